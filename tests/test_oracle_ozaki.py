@@ -1,0 +1,115 @@
+"""Pins of the oracle's split-precision (Ozaki-style) DD GEMM steps (no GPU).
+
+* exponents: e_i is the largest frexp exponent of row i's hi words (and f_j
+  of column j's), so every scaled |a'| < 1.
+* slicing: sum_s d_s 2^(-7s) equals a' truncated toward zero to 7S bits,
+  exactly (Fractions); every digit is an int8 in [-127, 127] with a's sign.
+* level sums: equal to numpy int64 matrix products of the digit planes,
+  summed over s + t = g (an independent library routine).
+* recombination: equals the exact level sum rounded greedily to DD.
+* end to end: |C - C_exact| <= 2^-100 |A||B| at S = 16 on row/column scaled
+  inputs, and the error falls as S grows.
+"""
+
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from exact import F, greedy, value
+from paper_1710_01839_gb300 import inputs as I
+
+
+def _frexp_exp(x: float) -> int:
+    return math.frexp(x)[1]
+
+
+def test_exponents_and_scaling():
+    A, B = I.dd_rowcol_scaled(9, 13, 7, seed=3)
+    e = oracle.ozaki_row_expo(A)
+    f = oracle.ozaki_col_expo(B)
+    for i in range(9):
+        assert e[i] == max(_frexp_exp(x) for x in A[0, i] if x != 0)
+        for k in range(13):
+            assert abs(value(A[:, i, k])) < Fraction(2) ** int(e[i])
+    for j in range(7):
+        assert f[j] == max(_frexp_exp(x) for x in B[0, :, j] if x != 0)
+
+
+@pytest.mark.parametrize("S", [1, 3, 8, 16])
+def test_digits_are_exact_truncation(S):
+    A, _ = I.dd_rowcol_scaled(6, 10, 4, seed=4)
+    A[:, 2, 3] = 0.0          # a zero element
+    A[:, 4, :] = 0.0          # an all-zero row
+    e = oracle.ozaki_row_expo(A)
+    D = oracle.ozaki_slice(A, e, S, by_col=False)
+    assert D.dtype == np.int8
+    assert np.abs(D.astype(np.int64)).max() <= 127
+    for i in range(6):
+        for k in range(10):
+            a = value(A[:, i, k]) * Fraction(2) ** -int(e[i])
+            scaled = a * (1 << (7 * S))
+            trunc = (abs(scaled.numerator) // scaled.denominator) * (1 if a >= 0 else -1)
+            got = sum(int(D[s, i, k]) << (7 * (S - 1 - s)) for s in range(S))
+            assert got == trunc
+            if a > 0:
+                assert (D[:, i, k] >= 0).all()
+            if a < 0:
+                assert (D[:, i, k] <= 0).all()
+
+
+def test_level_sums_match_numpy_integer_products():
+    S = 5
+    A, B = I.dd_rowcol_scaled(7, 12, 5, seed=5)
+    e, f = oracle.ozaki_row_expo(A), oracle.ozaki_col_expo(B)
+    DA = oracle.ozaki_slice(A, e, S, by_col=False)
+    DB = oracle.ozaki_slice(B, f, S, by_col=True)
+    L = oracle.ozaki_levels(DA, DB, S)
+    want = np.zeros_like(L)
+    for s in range(1, S + 1):
+        for t in range(1, S + 2 - s):
+            want[s + t] += DA[s - 1].astype(np.int64) @ DB[t - 1].astype(np.int64)
+    assert np.array_equal(L, want)
+
+
+def test_recombination_is_exact_then_rounded():
+    S = 6
+    A, B = I.dd_rowcol_scaled(5, 8, 4, seed=6)
+    e, f = oracle.ozaki_row_expo(A), oracle.ozaki_col_expo(B)
+    DA = oracle.ozaki_slice(A, e, S, by_col=False)
+    DB = oracle.ozaki_slice(B, f, S, by_col=True)
+    L = oracle.ozaki_levels(DA, DB, S)
+    C = oracle.ozaki_recombine(L, e, f, S)
+    for i in range(5):
+        for j in range(4):
+            x = sum((Fraction(int(L[g, i, j])) * Fraction(2) ** (int(e[i]) + int(f[j]) - 7 * g)
+                     for g in range(2, S + 2)), Fraction(0))
+            assert C[:, i, j].tolist() == greedy(x, 2)
+    assert np.array_equal(C, oracle.ozaki_gemm(A, B, S))
+
+
+def _max_rel_err(A, B, C):
+    m, n = C.shape[1], C.shape[2]
+    ii, jj = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    err, absab = oracle.exact_check(A, B, C, ii.ravel(), jj.ravel())
+    return float(np.max(err / absab))
+
+
+def test_end_to_end_error_bound_and_monotone_in_slices():
+    A, B = I.dd_rowcol_scaled(24, 40, 20, seed=7)
+    errs = {}
+    for S in (8, 12, 14, 16, 18):
+        errs[S] = _max_rel_err(A, B, oracle.ozaki_gemm(A, B, S))
+    assert errs[16] <= 2.0**-100
+    assert errs[18] <= errs[16] <= errs[14] <= errs[12] <= errs[8]
+    assert errs[8] > 2.0**-100   # too few slices really does lose accuracy
+
+
+def test_exact_on_integers():
+    a = I.int_matrix(6, 9, 8, -100, 100)
+    b = I.int_matrix(9, 5, 9, -100, 100)
+    C = oracle.ozaki_gemm(I.ints_to_dd(a), I.ints_to_dd(b), 4)
+    assert np.array_equal(C[0], (a @ b).astype(np.float64))
+    assert not C[1].any()
