@@ -1,0 +1,116 @@
+/*
+ * mpgemm — multiple-precision dense real matrix multiplication C := AB on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The operation is the paper's: Kouya, "Tuning Technique for Multiple
+ * Precision Dense Matrix Multiplication using Prediction of Computational
+ * Time" (arXiv:1710.01839), Section 2: C := AB with A in R^{m x l},
+ * B in R^{l x n}, c_ij = sum_{k=1..l} a_ik b_kj (Eq 1), computed by the
+ * simple algorithm (Eq 1), the block algorithm with block size n_min (Eq 2)
+ * or Strassen's recursion P1..P7 (Eq 3), in double-double (DD), quad-double
+ * (QD) or p-bit multi-limb binary floating point (the MPFR stand-in of
+ * Section 4.2).
+ *
+ * Conventions shared by every entry point:
+ *   - All matrix pointers are DEVICE pointers owned by the caller.  The
+ *     library never frees them.  C must not overlap A or B (MPGEMM_EINVAL).
+ *   - Layout: row-major planes.  DD: 2 planes [hi | lo] of rows*cols doubles
+ *     (value hi + lo, |lo| <= ulp(hi)/2).  QD: 4 planes x0..x3 (value
+ *     x0 + x1 + x2 + x3, non-overlapping).  Multi-limb with p = prec_bits
+ *     = 32 w: (2 + w) planes of rows*cols uint32 words: [exponent (int32) |
+ *     flags (bit0 sign, bit1 zero) | limb 0 (least significant) .. limb w-1],
+ *     value (-1)^sign * M * 2^(exponent - p), M = sum limb_i 2^(32 i) in
+ *     [2^(p-1), 2^p); zero has M = 0, exponent 0, flags bit1 set.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream).  Argument errors are returned at once and nothing is
+ *     launched.  Errors found on the device (multi-limb exponent overflow, a
+ *     bounded wait that gave up) set a per-device status word that
+ *     mpgemm_stream_status() reads.
+ *   - Return value: MPGEMM_OK (0) or a negative mpgemm_status.
+ *   - m, l, n may be 0 (nothing to do, C untouched when m*n == 0; C = 0 when
+ *     l == 0).
+ */
+#ifndef MPGEMM_H
+#define MPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MPGEMM_SIMPLE = 0,    /* Eq 1: one output per thread, k ascending, no staging        */
+    MPGEMM_BLOCK = 1,     /* Eq 2: n_min-blocked, shared-memory staged, register tiled    */
+    MPGEMM_STRASSEN = 2,  /* Eq 3: strassen_depth levels of P1..P7, leaves = block(n_min) */
+    MPGEMM_AUTO = 3       /* algorithm, n_min and depth from the tuner / cost model       */
+} mpgemm_algo;
+
+typedef enum {
+    MPGEMM_OK = 0,
+    MPGEMM_EINVAL = -1,       /* bad argument (negative size, NULL, overlap, bad n_min)   */
+    MPGEMM_EUNSUPPORTED = -2, /* valid but not supported (odd size at a Strassen level,   */
+                              /* precision not built)                                      */
+    MPGEMM_ECUDA = -3,        /* a CUDA call failed; mpgemm_last_cuda_error() has it       */
+    MPGEMM_EOVERFLOW = -4,    /* device: a multi-limb exponent left the int32 range        */
+    MPGEMM_ETIMEOUT = -5,     /* device: a bounded wait gave up                            */
+    MPGEMM_ENOMEM = -6        /* workspace allocation failed or is too small               */
+} mpgemm_status;
+
+typedef enum { MPGEMM_KIND_DD = 0, MPGEMM_KIND_QD = 1, MPGEMM_KIND_MP = 2 } mpgemm_kind;
+
+/* ---------------------------------------------------------------------------
+ * The GEMM (Section 2, Eqs 1-3).
+ *   algo           mpgemm_algo.
+ *   n_min          block size of Eq 2 (power of two, 16..256).  On the GPU it is
+ *                  the edge of the square C block one CTA computes when
+ *                  n_min <= the format's largest CTA tile (64 DD, 32 QD, 16 MP),
+ *                  and otherwise the edge of the super-tile of CTAs that run
+ *                  back to back (L2 blocking).  <= 0 selects the default.
+ *   strassen_depth levels of Eq 3 (0..4) for MPGEMM_STRASSEN; every dimension
+ *                  must be divisible by 2^depth (else MPGEMM_EUNSUPPORTED).
+ * Strassen needs workspace (mpgemm_workspace_size); it is taken from the
+ * buffer given to mpgemm_set_workspace, else allocated stream-ordered
+ * (cudaMallocAsync) and released on the same stream.
+ * ------------------------------------------------------------------------- */
+int mpgemm_dd(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int algo,
+              int n_min, int strassen_depth, void* stream);
+int mpgemm_qd(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int algo,
+              int n_min, int strassen_depth, void* stream);
+/* prec_bits = 32 w, w in {1, 2, 4, 8, 16, 32}.  Round to nearest, ties to
+   even, after every multiply and every add (c <- RN(c + RN(a b)), k
+   ascending); simple and block results are bit-identical to each other. */
+int mpgemm_mp(int64_t m, int64_t l, int64_t n, int prec_bits, const uint32_t* A, const uint32_t* B,
+              uint32_t* C, int algo, int n_min, int strassen_depth, void* stream);
+
+/* Bytes of workspace one call needs (0 for simple/block). */
+size_t mpgemm_workspace_size(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo,
+                             int strassen_depth);
+/* Give the library a device buffer to use as workspace for calls on this
+   device (NULL, 0 = allocate per call).  The caller keeps ownership and must
+   not free it while calls that may use it are in flight.  Calls on
+   different streams that share the buffer must be ordered by the caller. */
+int mpgemm_set_workspace(void* dev_ptr, size_t bytes);
+
+/* Synchronise `stream`, then read and clear the current device's status
+   word: MPGEMM_OK, MPGEMM_EOVERFLOW or MPGEMM_ETIMEOUT. */
+int mpgemm_stream_status(void* stream);
+const char* mpgemm_strerror(int status);
+/* The cudaError_t of the last MPGEMM_ECUDA on this host thread. */
+int mpgemm_last_cuda_error(void);
+/* Kernel timing for benchmarks: while enabled, every GEMM kernel launch (the
+   dominant kernel of each algorithm) is bracketed by CUDA events on its
+   stream.  mpgemm_profile_read synchronises on those events and returns the
+   summed device milliseconds and the number of launches since the last
+   read, then forgets them. */
+int mpgemm_profile(int enable);
+int mpgemm_profile_read(double* total_ms, int* launches);
+/* Library version as 10000*major + 100*minor + patch. */
+int mpgemm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPGEMM_H */

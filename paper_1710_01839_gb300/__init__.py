@@ -1,0 +1,119 @@
+"""Python binding of libmpgemm: multiple-precision dense GEMM C := AB on a
+GB300 (Kouya, arXiv:1710.01839, Section 2, Eqs 1-3).
+
+Argument marshalling only: every step runs in the CUDA library's kernels.
+If the compiled library is missing this module raises; there is no CPU
+fallback.  PyTorch supplies device memory and the current stream.
+
+Layouts (see include/mpgemm.h): DD tensors are float64 of shape (2, rows,
+cols) [hi, lo]; QD float64 (4, rows, cols); multi-limb uint32-compatible
+int32/uint32 tensors of shape (2 + w, rows, cols) with p = 32 w bits.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from ._lib import (ALGO, KIND, MpgemmError, check, lib, lib_path)  # noqa: F401
+
+__all__ = ["gemm_dd", "gemm_qd", "gemm_mp", "workspace_size", "set_workspace", "stream_status", "strerror",
+           "MpgemmError", "ALGO", "KIND", "lib", "lib_path"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _check_tensor(t, planes, dtypes, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    if t.dim() != 3 or t.shape[0] != planes:
+        raise ValueError(f"{name} must have shape ({planes}, rows, cols), got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _algo(a):
+    return ALGO[a] if isinstance(a, str) else int(a)
+
+
+def _ddqd(fn, planes, A, B, C, algo, n_min, depth, stream):
+    torch = _torch()
+    _check_tensor(A, planes, (torch.float64,), "A")
+    _check_tensor(B, planes, (torch.float64,), "B")
+    m, l = A.shape[1], A.shape[2]
+    if B.shape[1] != l:
+        raise ValueError("inner dimensions differ")
+    n = B.shape[2]
+    if C is None:
+        C = torch.empty((planes, m, n), dtype=torch.float64, device=A.device)
+    _check_tensor(C, planes, (torch.float64,), "C")
+    rc = fn(m, l, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+            _algo(algo), int(n_min), int(depth), _stream_ptr(stream))
+    check(rc)
+    return C
+
+
+def gemm_dd(A, B, C=None, algo="block", n_min=0, depth=0, stream=None):
+    """C := AB in double-double (mpgemm_dd)."""
+    return _ddqd(lib().mpgemm_dd, 2, A, B, C, algo, n_min, depth, stream)
+
+
+def gemm_qd(A, B, C=None, algo="block", n_min=0, depth=0, stream=None):
+    """C := AB in quad-double (mpgemm_qd)."""
+    return _ddqd(lib().mpgemm_qd, 4, A, B, C, algo, n_min, depth, stream)
+
+
+def gemm_mp(A, B, prec_bits, C=None, algo="block", n_min=0, depth=0, stream=None):
+    """C := AB in p-bit multi-limb floating point, p = prec_bits (mpgemm_mp)."""
+    torch = _torch()
+    w = prec_bits // 32
+    dt = (torch.int32, torch.uint32) if hasattr(torch, "uint32") else (torch.int32,)
+    _check_tensor(A, 2 + w, dt, "A")
+    _check_tensor(B, 2 + w, dt, "B")
+    m, l = A.shape[1], A.shape[2]
+    if B.shape[1] != l:
+        raise ValueError("inner dimensions differ")
+    n = B.shape[2]
+    if C is None:
+        C = torch.empty((2 + w, m, n), dtype=A.dtype, device=A.device)
+    _check_tensor(C, 2 + w, dt, "C")
+    rc = lib().mpgemm_mp(m, l, n, int(prec_bits), ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                         ctypes.c_void_p(C.data_ptr()), _algo(algo), int(n_min), int(depth), _stream_ptr(stream))
+    check(rc)
+    return C
+
+
+def workspace_size(kind, m, l, n, algo="strassen", depth=1, prec_bits=0):
+    k = KIND[kind] if isinstance(kind, str) else int(kind)
+    return int(lib().mpgemm_workspace_size(k, int(prec_bits), m, l, n, _algo(algo), int(depth)))
+
+
+def set_workspace(tensor=None):
+    """Hand the library a device buffer (a CUDA tensor) to use as workspace;
+    None reverts to per-call stream-ordered allocation.  Keep the tensor
+    alive while calls that may use it run."""
+    if tensor is None:
+        check(lib().mpgemm_set_workspace(None, 0))
+    else:
+        check(lib().mpgemm_set_workspace(ctypes.c_void_p(tensor.data_ptr()), tensor.numel() * tensor.element_size()))
+
+
+def stream_status(stream=None):
+    return int(lib().mpgemm_stream_status(_stream_ptr(stream)))
+
+
+def strerror(status):
+    return lib().mpgemm_strerror(int(status)).decode()

@@ -1,0 +1,71 @@
+"""ctypes declarations of libmpgemm's C ABI (include/mpgemm.h)."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libmpgemm.so")
+
+ALGO = {"simple": 0, "block": 1, "strassen": 2, "auto": 3}
+KIND = {"dd": 0, "qd": 1, "mp": 2}
+STATUS = {0: "MPGEMM_OK", -1: "MPGEMM_EINVAL", -2: "MPGEMM_EUNSUPPORTED", -3: "MPGEMM_ECUDA",
+          -4: "MPGEMM_EOVERFLOW", -5: "MPGEMM_ETIMEOUT", -6: "MPGEMM_ENOMEM"}
+
+
+class MpgemmError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+
+# name -> (restype, argtypes); every function the header declares
+SIGNATURES = {
+    "mpgemm_dd": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _I, _I, _P]),
+    "mpgemm_qd": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _I, _I, _P]),
+    "mpgemm_mp": (_I, [_I64, _I64, _I64, _I, _P, _P, _P, _I, _I, _I, _P]),
+    "mpgemm_workspace_size": (_SZ, [_I, _I, _I64, _I64, _I64, _I, _I]),
+    "mpgemm_set_workspace": (_I, [_P, _SZ]),
+    "mpgemm_stream_status": (_I, [_P]),
+    "mpgemm_strerror": (ctypes.c_char_p, [_I]),
+    "mpgemm_last_cuda_error": (_I, []),
+    "mpgemm_version": (_I, []),
+    "mpgemm_profile": (_I, [_I]),
+    "mpgemm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+}
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libmpgemm.so.  Raises if it was not built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                               f"g.build()'` (the CUDA library is required; there is no CPU path)")
+        L = ctypes.CDLL(_LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != 0:
+        extra = ""
+        if rc == -3:
+            extra = f"cudaError {lib().mpgemm_last_cuda_error()}"
+        raise MpgemmError(rc, lib().mpgemm_strerror(rc).decode() + (" " + extra if extra else ""))

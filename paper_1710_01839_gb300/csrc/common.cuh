@@ -1,0 +1,74 @@
+// Shared definitions of the multiple-precision GEMM library (device side).
+//
+// Matrix storage: row-major "planes".  A DD matrix is two contiguous arrays
+// [hi | lo] of rows*cols doubles, QD four planes, a p-bit multi-limb matrix
+// (2 + w) planes of uint32 words [exponent | flags | limb 0 .. limb w-1].
+// Internally every operand is addressed through a View: element (z, q, i, j)
+// (batch z, plane q, row i, column j) lives at p[z*bs + q*ps + i*ld + j], so
+// Strassen's quadrants and batched sub-problems need no copies.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mpgemm.h"
+
+namespace mpg {
+
+template <class T>
+struct View {
+    T* p;
+    int64_t ld;  // row stride (elements)
+    int64_t ps;  // plane stride (elements)
+    int64_t bs;  // batch stride (elements)
+    __host__ __device__ T* at(int64_t z, int q, int64_t i, int64_t j) const {
+        return p + z * bs + q * ps + i * ld + j;
+    }
+};
+
+template <class T>
+inline View<T> planes_view(T* p, int64_t rows, int64_t cols) {
+    View<T> v{p, cols, rows * cols, 0};
+    return v;
+}
+
+// Device-side status word (bits of MPGEMM_DEV_*), one per device, read and
+// cleared by mpgemm_stream_status().
+enum : unsigned {
+    DEV_EXP_OVERFLOW = 1u,   // a multi-limb exponent left the int32 range
+    DEV_TIMEOUT = 2u,        // a bounded wait in a persistent kernel gave up
+    DEV_BAD_DESC = 4u,       // a batched descriptor failed a device-side check
+};
+
+unsigned* device_status_ptr();   // address of this device's status word
+
+// Launch-shape helpers.
+__host__ __device__ inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Host-side error plumbing.
+#define MPG_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) {                              \
+            ::mpg::set_last_cuda_error(e_);                   \
+            return MPGEMM_ECUDA;                              \
+        }                                                     \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e);
+int check_launch();   // cudaGetLastError -> status
+
+// CTA raster order: with group size G (in tiles), consecutive CTA ids cover a
+// G x G super-tile of C before moving on (G = 1 is plain row-major order).
+__device__ __forceinline__ void raster(unsigned pid, unsigned tiles_m, unsigned tiles_n, unsigned G,
+                                       unsigned& tm, unsigned& tn) {
+    unsigned band = G * tiles_n;
+    unsigned gid = pid / band;
+    unsigned first = gid * G;
+    unsigned gm = tiles_m - first < G ? tiles_m - first : G;
+    unsigned r = pid - gid * band;
+    tm = first + r % gm;
+    tn = r / gm;
+}
+
+}  // namespace mpg

@@ -1,0 +1,190 @@
+// Multi-limb GEMM kernels (simple, Eq 1, and block, Eq 2) and the
+// elementwise add/sub used by Strassen (Eq 3), for p = 32 W bits.
+//
+// Both GEMM kernels keep the per-element operation sequence of Eq 1
+// (c = +0; for k = 1..l: c = RN(c + RN(a_ik b_kj))), so they are
+// bit-identical to each other and to the definition.  The work is on the
+// integer pipe (W^2 32x32->64 multiplies per product plus O(W) alignment and
+// rounding), one thread per output.
+#include "common.cuh"
+#include "kernels.h"
+#include "mp_arith.cuh"
+#include "profile.h"
+
+namespace mpg {
+
+template <int W>
+__device__ __forceinline__ void load_mp(MPV<W>& v, const uint32_t* p, int64_t ps) {
+    v.e = (int)p[0];
+    v.f = p[ps];
+#pragma unroll
+    for (int i = 0; i < W; i++) v.m[i] = p[(2 + i) * ps];
+}
+
+template <int W>
+__device__ __forceinline__ void store_mp(const MPV<W>& v, uint32_t* p, int64_t ps) {
+    p[0] = (uint32_t)v.e;
+    p[ps] = v.f;
+#pragma unroll
+    for (int i = 0; i < W; i++) p[(2 + i) * ps] = v.m[i];
+}
+
+template <int W>
+__device__ __forceinline__ void mp_mac(MPV<W>& c, const MPV<W>& a, const MPV<W>& b, unsigned& st) {
+    MPV<W> t;
+    mp_mul<W>(a, b, t, st);
+    MPV<W> s;
+    mp_add<W>(c, t, s, st);
+    c = s;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_mp_simple(int64_t m, int64_t l, int64_t n, View<const uint32_t> A,
+                                                   View<const uint32_t> B, View<uint32_t> C, unsigned* status) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    int64_t z = blockIdx.z;
+    if (i >= m || j >= n) return;
+    unsigned st = 0u;
+    MPV<W> c;
+    mp_set_zero(c, 0u);
+    for (int64_t k = 0; k < l; k++) {
+        MPV<W> a, b;
+        load_mp(a, A.at(z, 0, i, k), A.ps);
+        load_mp(b, B.at(z, 0, k, j), B.ps);
+        mp_mac(c, a, b, st);
+    }
+    store_mp(c, C.at(z, 0, i, j), C.ps);
+    if (st) atomicOr(status, st);
+}
+
+// CTA = 16 x 16 outputs, one per thread; A rows / B columns staged through
+// shared memory KT elements deep as [k][row][word]; CTA order follows the
+// super-tile raster with group G.
+template <int W, int KT>
+__global__ void __launch_bounds__(256) k_mp_block(int64_t m, int64_t l, int64_t n, View<const uint32_t> A,
+                                                  View<const uint32_t> B, View<uint32_t> C, unsigned G,
+                                                  unsigned* status) {
+    constexpr int BM = 16;
+    constexpr int E = 2 + W;
+    constexpr int WORDS = BM * KT * E;
+    __shared__ uint32_t As[KT][BM][E];
+    __shared__ uint32_t Bs[KT][BM][E];
+    const unsigned tiles_m = ceil_div(m, BM), tiles_n = ceil_div(n, BM);
+    unsigned tm, tn;
+    raster(blockIdx.x, tiles_m, tiles_n, G, tm, tn);
+    const int64_t z = blockIdx.y;
+    const int64_t i0 = (int64_t)tm * BM, j0 = (int64_t)tn * BM;
+    const int tid = threadIdx.x, ty = tid / BM, tx = tid % BM;
+    unsigned st = 0u;
+    MPV<W> c;
+    mp_set_zero(c, 0u);
+    for (int64_t k0 = 0; k0 < l; k0 += KT) {
+        for (int idx = tid; idx < WORDS; idx += 256) {
+            int q = idx / (BM * KT), rem = idx % (BM * KT);
+            int r = rem / KT, cc = rem % KT;          // A: row r, k = k0 + cc
+            int64_t i = i0 + r, k = k0 + cc;
+            uint32_t va = (i < m && k < l) ? __ldg(A.at(z, q, i, k)) : (q == 1 ? 2u : 0u);
+            As[cc][r][q] = va;
+            int rb = rem / BM, cb = rem % BM;         // B: k = k0 + rb, column cb
+            int64_t kb = k0 + rb, j = j0 + cb;
+            uint32_t vb = (kb < l && j < n) ? __ldg(B.at(z, q, kb, j)) : (q == 1 ? 2u : 0u);
+            Bs[rb][cb][q] = vb;
+        }
+        __syncthreads();
+        const int kmax = (l - k0) < KT ? (int)(l - k0) : KT;
+        for (int kk = 0; kk < kmax; kk++) {
+            MPV<W> a, b;
+            a.e = (int)As[kk][ty][0];
+            a.f = As[kk][ty][1];
+            b.e = (int)Bs[kk][tx][0];
+            b.f = Bs[kk][tx][1];
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                a.m[w] = As[kk][ty][2 + w];
+                b.m[w] = Bs[kk][tx][2 + w];
+            }
+            mp_mac(c, a, b, st);
+        }
+        __syncthreads();
+    }
+    int64_t i = i0 + ty, j = j0 + tx;
+    if (i < m && j < n) store_mp(c, C.at(z, 0, i, j), C.ps);
+    if (st) atomicOr(status, st);
+}
+
+template <int W>
+__global__ void k_mp_addsub(int64_t r, int64_t c, View<uint32_t> Z, View<const uint32_t> X, View<const uint32_t> Y,
+                            int sub, unsigned* status) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = (int64_t)blockIdx.y;
+    int64_t z = blockIdx.z;
+    if (j >= c) return;
+    unsigned st = 0u;
+    MPV<W> x, y, s;
+    load_mp(x, X.at(z, 0, i, j), X.ps);
+    load_mp(y, Y.at(z, 0, i, j), Y.ps);
+    if (sub) y.f ^= 1u;
+    mp_add<W>(x, y, s, st);
+    store_mp(s, Z.at(z, 0, i, j), Z.ps);
+    if (st) atomicOr(status, st);
+}
+
+template <int W>
+static int mp_gemm_w(int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const uint32_t> A,
+                     View<const uint32_t> B, View<uint32_t> C, int n_min, cudaStream_t s) {
+    unsigned* status = device_status_ptr();
+    if (!status) return MPGEMM_ECUDA;
+    ProfScope ps(s);
+    if (algo == MPGEMM_SIMPLE) {
+        dim3 blk(16, 16);
+        dim3 grd(ceil_div(n, 16), ceil_div(m, 16), (unsigned)batch);
+        k_mp_simple<W><<<grd, blk, 0, s>>>(m, l, n, A, B, C, status);
+    } else {
+        unsigned G = n_min > 16 ? (unsigned)(n_min / 16) : 1u;
+        dim3 grd(ceil_div(m, 16) * ceil_div(n, 16), (unsigned)batch);
+        constexpr int KT = W >= 16 ? 4 : 8;
+        k_mp_block<W, KT><<<grd, 256, 0, s>>>(m, l, n, A, B, C, G, status);
+    }
+    return check_launch();
+}
+
+int mp_gemm(int w, int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const uint32_t> A,
+            View<const uint32_t> B, View<uint32_t> C, int n_min, cudaStream_t s) {
+    if (m == 0 || n == 0 || batch == 0) return MPGEMM_OK;
+    switch (w) {
+        case 1: return mp_gemm_w<1>(algo, m, l, n, batch, A, B, C, n_min, s);
+        case 2: return mp_gemm_w<2>(algo, m, l, n, batch, A, B, C, n_min, s);
+        case 4: return mp_gemm_w<4>(algo, m, l, n, batch, A, B, C, n_min, s);
+        case 8: return mp_gemm_w<8>(algo, m, l, n, batch, A, B, C, n_min, s);
+        case 16: return mp_gemm_w<16>(algo, m, l, n, batch, A, B, C, n_min, s);
+        case 32: return mp_gemm_w<32>(algo, m, l, n, batch, A, B, C, n_min, s);
+        default: return MPGEMM_EUNSUPPORTED;
+    }
+}
+
+template <int W>
+static int mp_addsub_w(int64_t r, int64_t c, int64_t batch, View<uint32_t> Z, View<const uint32_t> X,
+                       View<const uint32_t> Y, int sub, cudaStream_t s) {
+    unsigned* status = device_status_ptr();
+    if (!status) return MPGEMM_ECUDA;
+    dim3 grd(ceil_div(c, 128), (unsigned)r, (unsigned)batch);
+    k_mp_addsub<W><<<grd, 128, 0, s>>>(r, c, Z, X, Y, sub, status);
+    return check_launch();
+}
+
+int mp_addsub(int w, int64_t r, int64_t c, int64_t batch, View<uint32_t> Z, View<const uint32_t> X,
+              View<const uint32_t> Y, int sub, cudaStream_t s) {
+    if (r == 0 || c == 0 || batch == 0) return MPGEMM_OK;
+    switch (w) {
+        case 1: return mp_addsub_w<1>(r, c, batch, Z, X, Y, sub, s);
+        case 2: return mp_addsub_w<2>(r, c, batch, Z, X, Y, sub, s);
+        case 4: return mp_addsub_w<4>(r, c, batch, Z, X, Y, sub, s);
+        case 8: return mp_addsub_w<8>(r, c, batch, Z, X, Y, sub, s);
+        case 16: return mp_addsub_w<16>(r, c, batch, Z, X, Y, sub, s);
+        case 32: return mp_addsub_w<32>(r, c, batch, Z, X, Y, sub, s);
+        default: return MPGEMM_EUNSUPPORTED;
+    }
+}
+
+}  // namespace mpg

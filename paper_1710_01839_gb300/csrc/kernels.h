@@ -1,0 +1,27 @@
+// Internal launch interfaces between the C-ABI layer and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mpg {
+
+// DD / QD simple (Eq 1) or block (Eq 2) over `batch` independent problems
+// (grid.z / grid.y); kind = MPGEMM_KIND_DD or MPGEMM_KIND_QD.
+int ddqd_gemm(int kind, int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const double> A,
+              View<const double> B, View<double> C, int n_min, cudaStream_t s);
+
+// Multi-limb simple / block, w limbs per mantissa.
+int mp_gemm(int w, int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const uint32_t> A,
+            View<const uint32_t> B, View<uint32_t> C, int n_min, cudaStream_t s);
+
+// Elementwise z = x + y (sub: x - y) in a format over a batch of r x c matrices.
+int ddqd_addsub(int kind, int64_t r, int64_t c, int64_t batch, View<double> Z, View<const double> X,
+                View<const double> Y, int sub, cudaStream_t s);
+int mp_addsub(int w, int64_t r, int64_t c, int64_t batch, View<uint32_t> Z, View<const uint32_t> X,
+              View<const uint32_t> Y, int sub, cudaStream_t s);
+
+}  // namespace mpg

@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle and with the
+exact product.
+
+Bars (written into each test):
+  DD      |C - C_exact| <= 4 l 2^-104 |A||B| elementwise (and within twice
+          that of the oracle, which meets the same bound)
+  QD      |C - C_exact| <= 4 l 2^-208 |A||B|
+  MP      bit-identical to the oracle (simple and block keep k ascending)
+  Strassen on integer matrices: bit-identical to the simple algorithm
+  DD Strassen: |C - C_exact| <= 2^-96 l max|A| max|B|
+Sizes span several tiles with ragged tails; the bench's full-size launch
+configurations are checked on sampled entries.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import DD_BOUND, QD_BOUND, bound_ratio, dev, host, sample_indices
+from paper_1710_01839_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+mpg = pytest.importorskip("paper_1710_01839_gb300")
+
+
+def _full(m, n):
+    ii, jj = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    return ii.ravel().astype(np.int64), jj.ravel().astype(np.int64)
+
+
+# ---------------------------------------------------------------- DD
+
+@pytest.mark.parametrize("algo,n_min", [("simple", 0), ("block", 16), ("block", 32), ("block", 64),
+                                        ("block", 128), ("block", 256)])
+def test_dd_ragged(algo, n_min):
+    m, l, n = 131, 97, 77
+    A, B = I.dd_random(m, l, 101, 20), I.dd_random(l, n, 102, 20)
+    C = host(mpg.gemm_dd(dev(A), dev(B), algo=algo, n_min=n_min))
+    ii, jj = _full(m, n)
+    assert bound_ratio(A, B, C, ii, jj, DD_BOUND) <= 1.0
+    Co = oracle.dd_gemm(A, B)
+    err, absab = oracle.exact_check(A, B, Co, ii, jj)
+    diff = np.abs((C[0] - Co[0]) + (C[1] - Co[1])).ravel()
+    assert np.all(diff <= 2 * DD_BOUND * l * absab)
+
+
+@pytest.mark.parametrize("algo", ["simple", "block"])
+def test_dd_small_config_full(algo):
+    # 128^3, hi ~ U[-1,1], lo = hi 2^-53 u: every entry against the exact product
+    n = 128
+    A, B = I.dd_random(n, n, I.seed_for(0)), I.dd_random(n, n, I.seed_for(0, 1))
+    C = host(mpg.gemm_dd(dev(A), dev(B), algo=algo))
+    ii, jj = _full(n, n)
+    assert bound_ratio(A, B, C, ii, jj, DD_BOUND) <= 1.0
+
+
+@pytest.mark.parametrize("n,n_min", [(1024, 32), (1024, 64), (2048, 64), (2048, 128)])
+def test_dd_large_config_sampled(n, n_min):
+    A = I.dd_random(n, n, I.seed_for(1), exp_spread=20)
+    B = I.dd_random(n, n, I.seed_for(1, 1), exp_spread=20)
+    C = host(mpg.gemm_dd(dev(A), dev(B), algo="block", n_min=n_min))
+    ii, jj = sample_indices(n, n, 512, seed=n + n_min)
+    assert bound_ratio(A, B, C, ii, jj, DD_BOUND) <= 1.0
+
+
+def test_dd_worst_case_positive_inputs():
+    # all terms positive: partial sums grow monotonically, the accumulator's
+    # hardest case for the deferred renormalisation
+    n = 512
+    A, B = np.abs(I.dd_random(n, n, 7)), np.abs(I.dd_random(n, n, 8))
+    A[1] = np.abs(A[1]) * 0.5
+    C = host(mpg.gemm_dd(dev(A), dev(B), algo="block", n_min=64))
+    ii, jj = sample_indices(n, n, 256, seed=3)
+    assert bound_ratio(A, B, C, ii, jj, DD_BOUND) <= 1.0
+
+
+# ---------------------------------------------------------------- QD
+
+@pytest.mark.parametrize("algo,n_min", [("simple", 0), ("block", 16), ("block", 32), ("block", 128)])
+def test_qd_ragged(algo, n_min):
+    m, l, n = 67, 53, 45
+    A, B = I.qd_random(m, l, 103, 20), I.qd_random(l, n, 104, 20)
+    C = host(mpg.gemm_qd(dev(A), dev(B), algo=algo, n_min=n_min))
+    ii, jj = _full(m, n)
+    assert bound_ratio(A, B, C, ii, jj, QD_BOUND) <= 1.0
+
+
+@pytest.mark.parametrize("n", [1024])
+def test_qd_large_config_sampled(n):
+    A = I.qd_random(n, n, I.seed_for(1, 2), exp_spread=20)
+    B = I.qd_random(n, n, I.seed_for(1, 3), exp_spread=20)
+    C = host(mpg.gemm_qd(dev(A), dev(B), algo="block", n_min=32))
+    ii, jj = sample_indices(n, n, 256, seed=n)
+    assert bound_ratio(A, B, C, ii, jj, QD_BOUND) <= 1.0
+
+
+# ---------------------------------------------------------------- multi-limb
+
+@pytest.mark.parametrize("w", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("algo", ["simple", "block"])
+def test_mp_ragged_bit_exact(w, algo):
+    m, l, n = 37, 29, 23
+    A, B = I.mp_random(m, l, w, 200 + w), I.mp_random(l, n, w, 300 + w)
+    C = host(mpg.gemm_mp(dev(A), dev(B), 32 * w, algo=algo, n_min=32), mp=True)
+    Co = oracle.mp_gemm(A, B, prec_bits=32 * w)
+    assert np.array_equal(C, Co)
+    assert mpg.stream_status() == 0
+
+
+@pytest.mark.parametrize("w,n", [(4, 256), (8, 256), (16, 256), (32, 256), (4, 512)])
+def test_mp_large_config_sampled_rows(w, n):
+    A = I.mp_random(n, n, w, I.seed_for(2, w))
+    B = I.mp_random(n, n, w, I.seed_for(2, 100 + w))
+    C = host(mpg.gemm_mp(dev(A), dev(B), 32 * w, algo="block", n_min=16), mp=True)
+    for r0 in (0, n // 2, n - 1):
+        Co = oracle.mp_gemm(A, B, prec_bits=32 * w, rows=(r0, r0 + 1))
+        assert np.array_equal(C[:, r0], Co[:, r0]), r0
+
+
+def test_mp_cancellation_and_zeros():
+    # rows of A that are negatives of each other, zero entries, equal exponents
+    w = 4
+    m, l, n = 8, 16, 8
+    A = I.mp_random(m, l, w, 400, emin=-2, emax=2)
+    B = I.mp_random(l, n, w, 401, emin=-2, emax=2)
+    A[:, 1] = A[:, 0]
+    A[1, 1] ^= 1                       # row 1 = -row 0
+    A[:, 2, 3] = 0
+    A[1, 2, 3] = 2                     # a zero (M = 0, e = 0, zero flag)
+    B[:, 5, :] = B[:, 4, :]
+    B[1, 5, :] ^= 1                    # two rows of B cancel in every product sum
+    C = host(mpg.gemm_mp(dev(A), dev(B), 128, algo="block"), mp=True)
+    assert np.array_equal(C, oracle.mp_gemm(A, B, prec_bits=128))
+
+
+# ---------------------------------------------------------------- Strassen
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("fmt", ["dd", "qd", "mp128"])
+def test_strassen_integers_bit_exact(fmt, depth):
+    m, l, n = 64, 48, 40
+    a, b = I.int_matrix(m, l, 500 + depth), I.int_matrix(l, n, 600 + depth)
+    if fmt == "dd":
+        C = host(mpg.gemm_dd(dev(I.ints_to_dd(a)), dev(I.ints_to_dd(b)), algo="strassen", n_min=16, depth=depth))
+        want = I.ints_to_dd(a @ b)
+    elif fmt == "qd":
+        C = host(mpg.gemm_qd(dev(I.ints_to_qd(a)), dev(I.ints_to_qd(b)), algo="strassen", n_min=16, depth=depth))
+        want = I.ints_to_qd(a @ b)
+    else:
+        C = host(mpg.gemm_mp(dev(I.ints_to_mp(a, 4)), dev(I.ints_to_mp(b, 4)), 128, algo="strassen", n_min=16,
+                             depth=depth), mp=True)
+        want = I.ints_to_mp(a @ b, 4)
+    assert np.array_equal(C, want)
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_dd_strassen_bound(depth):
+    n = 256
+    A, B = I.dd_random(n, n, 700), I.dd_random(n, n, 701)
+    C = host(mpg.gemm_dd(dev(A), dev(B), algo="strassen", n_min=32, depth=depth))
+    ii, jj = sample_indices(n, n, 400, seed=depth)
+    err, _ = oracle.exact_check(A, B, C, ii, jj)
+    amax = np.max(np.abs(A[0] + A[1]))
+    bmax = np.max(np.abs(B[0] + B[1]))
+    assert np.max(err) <= 2.0**-96 * n * amax * bmax
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+def test_qd_strassen_bound(depth):
+    n = 64
+    A, B = I.qd_random(n, n, 702), I.qd_random(n, n, 703)
+    C = host(mpg.gemm_qd(dev(A), dev(B), algo="strassen", n_min=16, depth=depth))
+    ii, jj = _full(n, n)
+    err, _ = oracle.exact_check(A, B, C, ii, jj)
+    amax = np.max(np.abs(A[0]))
+    bmax = np.max(np.abs(B[0]))
+    assert np.max(err) <= 2.0**-200 * n * amax * bmax
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+def test_mp_strassen_bit_exact_vs_oracle(depth):
+    w, n = 4, 32
+    A, B = I.mp_random(n, n, w, 710 + depth), I.mp_random(n, n, w, 720 + depth)
+    C = host(mpg.gemm_mp(dev(A), dev(B), 128, algo="strassen", n_min=8, depth=depth), mp=True)
+    Co = oracle.mp_gemm(A, B, prec_bits=128, algo="strassen", n_min=8, depth=depth)
+    assert np.array_equal(C, Co)
+
+
+def test_strassen_with_caller_workspace():
+    import torch
+    n = 128
+    A, B = I.dd_random(n, n, 730), I.dd_random(n, n, 731)
+    ref = host(mpg.gemm_dd(dev(A), dev(B), algo="strassen", n_min=32, depth=2))
+    ws = torch.empty(mpg.workspace_size("dd", n, n, n, algo="strassen", depth=2), dtype=torch.uint8, device="cuda")
+    mpg.set_workspace(ws)
+    try:
+        got = host(mpg.gemm_dd(dev(A), dev(B), algo="strassen", n_min=32, depth=2))
+        small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+        mpg.set_workspace(small)
+        with pytest.raises(mpg.MpgemmError):
+            mpg.gemm_dd(dev(A), dev(B), algo="strassen", n_min=32, depth=2)
+    finally:
+        mpg.set_workspace(None)
+    assert np.array_equal(ref, got)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_edge_cases_and_errors():
+    import torch
+    # empty inner dimension: C = 0
+    A = dev(np.zeros((2, 5, 0)))
+    B = dev(np.zeros((2, 0, 4)))
+    C = host(mpg.gemm_dd(A, B))
+    assert C.shape == (2, 5, 4) and not C.any()
+    Am = dev(np.zeros((6, 3, 0), dtype=np.uint32))
+    Bm = dev(np.zeros((6, 0, 2), dtype=np.uint32))
+    Cm = host(mpg.gemm_mp(Am, Bm, 128), mp=True)
+    assert (Cm[1] == 2).all() and not Cm[0].any() and not Cm[2:].any()
+    # empty output
+    C = mpg.gemm_dd(dev(np.zeros((2, 0, 3))), dev(np.zeros((2, 3, 4))))
+    assert C.shape == (2, 0, 4)
+    # 1 x 1 x 1
+    a = np.array([[[0.5]], [[2.0**-60]]])
+    b = np.array([[[3.0]], [[0.0]]])
+    c = host(mpg.gemm_dd(dev(a), dev(b), algo="simple"))
+    assert c[0, 0, 0] + c[1, 0, 0] == 1.5 + 3 * 2.0**-60 and c[0, 0, 0] == 1.5
+    # argument errors come back as status codes, nothing launched
+    Ad, Bd = dev(I.dd_random(8, 8, 1)), dev(I.dd_random(8, 8, 2))
+    with pytest.raises(mpg.MpgemmError) as e:
+        mpg.gemm_dd(Ad, Bd, n_min=48)
+    assert e.value.status == -1
+    with pytest.raises(mpg.MpgemmError) as e:
+        mpg.gemm_dd(Ad, Bd, C=Ad)               # C overlaps A
+    assert e.value.status == -1
+    with pytest.raises(mpg.MpgemmError) as e:
+        mpg.gemm_dd(dev(I.dd_random(6, 6, 1)), dev(I.dd_random(6, 6, 2)), algo="strassen", depth=2)
+    assert e.value.status == -2
+    L = mpg.lib()
+    assert L.mpgemm_dd(-1, 1, 1, None, None, None, 1, 0, 0, None) == -1
+    assert L.mpgemm_mp(2, 2, 2, 96, None, None, None, 1, 0, 0, None) == -2
+    assert mpg.stream_status() == 0
+
+
+def test_paper_matrices_dd_closed_form():
+    # Section 4's matrices: c_ij = sqrt(15) n(n-1)(3i+n-2)/6 for every j
+    n = 256
+    A, B = I.paper_matrices(n, "dd")
+    C = host(mpg.gemm_dd(dev(A), dev(B), algo="block", n_min=64))
+    from fractions import Fraction
+    import math
+    r15 = Fraction(math.isqrt(15 << 600), 1 << 300)
+    for i in (1, 2, n // 2, n):
+        truth = r15 * I.paper_closed_form(n, i)
+        for j in (0, n // 3, n - 1):
+            got = Fraction(C[0, i - 1, j]) + Fraction(C[1, i - 1, j])
+            assert abs(got - truth) <= (4 * n + 3) * Fraction(2) ** -104 * truth
