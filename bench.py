@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""Benchmark of the multiple-precision GEMM C := AB on GB300.
+
+One step = one C := AB at the large square configuration (DD by default,
+m = l = n = 2048, entries hi ~ U[-1,1], lo = hi 2^-53 u, both words scaled
+by 2^k, k ~ U{-20..20}) through the library's C ABI with the algorithm and
+block size the tuner picked (the paper's Section 3 procedure: predict the
+block algorithm's time for each n_min from a reduced-row run, then time
+simple / block(best n_min) / Strassen and keep the fastest).  The tuning
+itself runs once before the timed region and is reported, not timed.
+
+Printed: one JSON line (rank 0).  `value` is whole-job effective GFLOP/s,
+2 m n l / t (Strassen credited with the same nominal count), from CUDA
+events on the launching stream with inputs resident in HBM and L2 flushed
+between steps; `e2e` is the same metric with host->device copies of A and B
+and the device->host copy of C inside the timed region.  `roofline` is the
+dominant kernel's FP64-pipe utilisation; `cpu_baseline` is the oracle on
+the host cores over a bounded row sample.
+
+  python bench.py [--gpus N --steps K --warmup W] [--fmt dd|qd] [--n 2048]
+  python bench.py --impl reference ...   (the oracle on the host cores)
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DD/QD GEMM GFLOP/s (2mnl/t) & roofline %; Ozaki vs plain DD at ≤2^-100 rel err"
+# FP64-pipe operations per multiply-accumulate of the kernels (see ddqd.cuh;
+# TwoSum costs 3 FP64 operations there, its operand ordering runs on the
+# integer pipe):
+#   DD: DMUL + 3 DFMA + TwoSum (3) + 2 DADD = 9, plus a 3-op TwoSum every 8 steps
+#   QD: 72 per step plus a 15-op renormalisation every 4 steps
+FP64_OPS_PER_MAC = {"dd": 9.0 + 3.0 / 8.0, "qd": 72.0 + 15.0 / 4.0}
+# FP64 pipe: 2 operations / clock / SM (measured 1.91 DFMA/clk/SM at 2.07 GHz by
+# a dependent-chain-free DFMA loop) x 152 SMs x 2070 MHz maximum SM clock.
+FP64_PEAK_GOPS = 2 * 152 * 2.070
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mpgemm", choices=["mpgemm", "reference"])
+    ap.add_argument("--fmt", default="dd", choices=["dd", "qd"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--algo", default="tuned", choices=["tuned", "simple", "block", "strassen"])
+    ap.add_argument("--n_min", type=int, default=64)
+    ap.add_argument("--depth", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the split-precision comparison")
+    ap.add_argument("--ozaki-n", type=int, default=4096)
+    ap.add_argument("--ozaki-slices", type=int, default=16)
+    return ap.parse_args()
+
+
+# mma.sync m16n8k32 s8 throughput measured on this machine's GB300 by a loop of
+# independent register-operand mma.sync instructions on all SMs (no tcgen05
+# integer MMA exists on sm_103a).
+INT8_MMA_PEAK_TOPS = 151.2
+
+
+def split_precision_extra(args, stream):
+    """Ozaki-style split-precision DD GEMM against the plain DD kernels on the
+    same DD inputs (m = l = n = ozaki_n, A's rows scaled by 2^r_i and B's
+    columns by 2^c_j, r, c ~ U{-16..16}).  Accuracy (<= 2^-100 |A||B|) is
+    asserted by the parity tests, not here."""
+    import ctypes
+    import torch
+    import paper_1710_01839_gb300 as mpg
+    from paper_1710_01839_gb300 import inputs as I
+    n, S = args.ozaki_n, args.ozaki_slices
+    A, B = I.dd_rowcol_scaled(n, n, n, seed=I.seed_for(3))
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    Cd = torch.empty_like(Ad)
+    L = mpg.lib()
+    sp = ctypes.c_void_p(int(stream.cuda_stream))
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    def oz():
+        rc = L.mpgemm_dd_ozaki(n, n, n, p(Ad), p(Bd), p(Cd), S, sp)
+        if rc:
+            raise RuntimeError(mpg.strerror(rc))
+
+    def timed(fn, steps):
+        fn()
+        torch.cuda.synchronize()
+        L.mpgemm_profile(1)
+        L.mpgemm_profile_read(None, None)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, kl = ctypes.c_double(), ctypes.c_int()
+        L.mpgemm_profile_read(ctypes.byref(kms), ctypes.byref(kl))
+        L.mpgemm_profile(0)
+        return e0.elapsed_time(e1) / steps, kms.value / max(kl.value, 1)
+
+    flops = 2.0 * n ** 3
+    oz_ms, oz_kms = timed(oz, 3)
+    pairs = S * (S + 1) // 2
+    lp = (n + 63) // 64 * 64
+    int_ops = 2.0 * n * n * lp * pairs
+    out = {"workload": f"DD m=l=n={n}, rows/cols scaled 2^U{{-16..16}}, S={S} int8 slices",
+           "ozaki_gflops": flops / (oz_ms * 1e-3) / 1e9, "ozaki_ms": oz_ms,
+           "roofline": {"bound": "tensor", "unit": "TOPS (int8 mma.sync)",
+                        "achieved": int_ops / (oz_kms * 1e-3) / 1e12, "peak": INT8_MMA_PEAK_TOPS,
+                        "frac": int_ops / (oz_kms * 1e-3) / 1e12 / INT8_MMA_PEAK_TOPS,
+                        "kernel": f"k_ozaki_levels, {pairs} slice pairs x 2 n^2 l int8 ops", "kernel_ms": oz_kms,
+                        "kernel_share": oz_kms / oz_ms}}
+    for name, algo, nm, d in (("plain_dd_block", "block", 64, 0), ("plain_dd_strassen3", "strassen", 32, 3)):
+        ms, _ = timed(lambda: mpg.gemm_dd(Ad, Bd, Cd, algo=algo, n_min=nm, depth=d), 1)
+        out[name + "_gflops"] = flops / (ms * 1e-3) / 1e9
+        out[name + "_ms"] = ms
+    out["speedup_vs_best_plain_dd"] = min(out["plain_dd_block_ms"], out["plain_dd_strassen3_ms"]) / oz_ms
+    return out
+
+
+# ---------------------------------------------------------------- helpers
+
+def inputs_for(fmt, n, rank=0):
+    from paper_1710_01839_gb300 import inputs as I
+    gen = I.dd_random if fmt == "dd" else I.qd_random
+    A = gen(n, n, I.seed_for(1, 10 * rank), exp_spread=20)
+    B = gen(n, n, I.seed_for(1, 10 * rank + 1), exp_spread=20)
+    return A, B
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(fmt, A, B, algo, n_min, budget_s):
+    """The oracle (as it stands) on the host cores over a row sample of the
+    same workload: rate = 2 * rows * n * l / t."""
+    import oracle
+    m, l, n = A.shape[1], A.shape[2], B.shape[2]
+    run = oracle.dd_gemm if fmt == "dd" else oracle.qd_gemm
+    cores = oracle.threads()
+    oalgo = "block" if algo in ("block", "strassen", "tuned") else "simple"
+    rows = max(1, cores)
+    t0 = time.perf_counter()
+    run(A, B, algo=oalgo, n_min=n_min, rows=(0, rows))
+    dt = time.perf_counter() - t0
+    # grow the sample to about `budget_s` seconds in total
+    if dt < budget_s / 4:
+        more = int(rows * (budget_s * 0.75) / max(dt, 1e-3))
+        more = max(rows, min(more - more % max(cores, 1), m - rows))
+        t0 = time.perf_counter()
+        run(A, B, algo=oalgo, n_min=n_min, rows=(rows, rows + more))
+        dt = time.perf_counter() - t0
+        rows = more
+    gflops = 2.0 * rows * n * l / dt / 1e9
+    return {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{rows} of {m} rows of C ({fmt.upper()} {oalgo} algorithm, k ascending), {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    A, B = inputs_for(args.fmt, args.n)
+    m, l, n = args.n, args.n, args.n
+    run = oracle.dd_gemm if args.fmt == "dd" else oracle.qd_gemm
+    cores = oracle.threads()
+    per_step_rows = max(cores, 1)
+    # size each step to about (cpu-seconds / 4) seconds
+    t0 = time.perf_counter()
+    run(A, B, algo="block", n_min=args.n_min, rows=(0, per_step_rows))
+    dt = time.perf_counter() - t0
+    target = max(1.0, args.cpu_seconds / 4)
+    per_step_rows = int(min(m, max(per_step_rows, per_step_rows * target / max(dt, 1e-3))))
+    for _ in range(args.warmup and 1):
+        pass
+    times = []
+    for s in range(args.steps):
+        r0 = (s * per_step_rows) % max(1, m - per_step_rows + 1)
+        t0 = time.perf_counter()
+        run(A, B, algo="block", n_min=args.n_min, rows=(r0, r0 + per_step_rows))
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = 2.0 * per_step_rows * n * l * len(times) / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.fmt.upper()} square GEMM m=l=n={args.n}, exponent spread 2^[-20,20]",
+                       "fmt": args.fmt, "n": args.n, "algo": "block", "n_min": args.n_min},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step_rows} rows of C per step (of {m}), block algorithm"},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1710_01839_gb300 as mpg
+    from paper_1710_01839_gb300 import tuner
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    fmt, n = args.fmt, args.n
+    m = l = n
+    A, B = inputs_for(fmt, n, rank)
+    planes = A.shape[0]
+    Ad = torch.from_numpy(A).cuda()
+    Bd = torch.from_numpy(B).cuda()
+    Cd = torch.empty((planes, m, n), dtype=torch.float64, device="cuda")
+    gemm = mpg.gemm_dd if fmt == "dd" else mpg.gemm_qd
+
+    # -------- selection (Section 3): untimed
+    t_tune = 0.0
+    tune_info = None
+    if args.algo == "tuned":
+        t0 = time.perf_counter()
+        choice, tune_info = tuner.tune(fmt, Ad, Bd, Cd)
+        t_tune = time.perf_counter() - t0
+        algo, n_min, depth = choice["algo"], choice["n_min"], choice["depth"]
+    else:
+        algo, n_min, depth = args.algo, args.n_min, args.depth if args.algo == "strassen" else 0
+
+    def step():
+        gemm(Ad, Bd, Cd, algo=algo, n_min=n_min, depth=depth)
+
+    launches_per_step = 1 if algo in ("simple", "block") else 3 * depth + 1
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    L = mpg.lib()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # -------- timed region (device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    L.mpgemm_profile(1)
+    import ctypes
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    kms = ctypes.c_double(0.0)
+    kl = ctypes.c_int(0)
+    L.mpgemm_profile_read(ctypes.byref(kms), ctypes.byref(kl))
+    L.mpgemm_profile(0)
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    status = mpg.stream_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status}: {mpg.strerror(status)}")
+    t_max = tot_ms
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    flops_step = 2.0 * m * n * l
+    value = world * flops_step * args.steps / (t_max * 1e-3) / 1e9
+
+    # -------- dominant kernel roofline (FP64 pipe)
+    leaf = n >> depth if algo == "strassen" else n
+    leaf_count = 7 ** depth if algo == "strassen" else 1
+    macs_per_launch = leaf_count * float(leaf) ** 3
+    k_avg_ms = kms.value / max(kl.value, 1)
+    achieved = macs_per_launch * FP64_OPS_PER_MAC[fmt] / (k_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "unit": "Gop/s (FP64 pipe)", "achieved": achieved, "peak": FP64_PEAK_GOPS,
+                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
+                "kernel": f"{fmt} {'leaf ' if algo == 'strassen' else ''}{'simple' if algo == 'simple' else 'block'}"
+                          f" GEMM, {macs_per_launch:.3g} MACs x {FP64_OPS_PER_MAC[fmt]} FP64 ops per launch",
+                "kernel_ms": k_avg_ms, "kernel_share_of_step": kms.value / tot_ms if tot_ms else None,
+                "peak_note": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"}
+
+    # -------- end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(A).pin_memory()
+        Bh = torch.from_numpy(B).pin_memory()
+        Ch = torch.empty((planes, m, n), dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            Ad.copy_(Ah, non_blocking=True)
+            Bd.copy_(Bh, non_blocking=True)
+            step()
+            Ch.copy_(Cd, non_blocking=True)
+        torch.cuda.synchronize()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev2[i][0].record(stream)
+            Ad.copy_(Ah, non_blocking=True)
+            Bd.copy_(Bh, non_blocking=True)
+            step()
+            Ch.copy_(Cd, non_blocking=True)
+            ev2[i][1].record(stream)
+        torch.cuda.synchronize()
+        e_ms = sum(a.elapsed_time(b) for a, b in ev2)
+        if dist:
+            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * flops_step * args.steps / (e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(planes * m * n * 8),
+               "ms_per_step": e_ms / args.steps}
+
+    extras = None
+    if not args.no_extras and fmt == "dd":
+        extras = split_precision_extra(args, stream)
+
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_baseline(fmt, A, B, algo, n_min if n_min > 0 else 64, args.cpu_seconds)
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{fmt.upper()} square GEMM m=l=n={n}, hi~U[-1,1], lo=hi*2^-53*u, "
+                                   f"exponent spread 2^[-20,20]", "fmt": fmt, "n": n, "algo": algo,
+                       "n_min": n_min, "strassen_depth": depth, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}", "tuning_s": round(t_tune, 3)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
+    if tune_info is not None:
+        line["tuning"] = tune_info
+    if extras is not None:
+        line["split_precision"] = extras
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -84,6 +84,39 @@ int mpgemm_qd(int64_t m, int64_t l, int64_t n, const double* A, const double* B,
 int mpgemm_mp(int64_t m, int64_t l, int64_t n, int prec_bits, const uint32_t* A, const uint32_t* B,
               uint32_t* C, int algo, int n_min, int strassen_depth, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Split-precision DD GEMM on the INT8 tensor path (an Ozaki-style scheme; the
+ * paper has no counterpart, it is an extension of its DD GEMM):
+ *   1. e_i = largest frexp exponent of row i of A's hi plane, f_j of column j
+ *      of B's hi plane;
+ *   2. every element, scaled by 2^-e_i (A) or 2^-f_j (B), is truncated toward
+ *      zero to 7 S bits and split into S signed base-128 digits (int8);
+ *   3. level sums L_g = sum_{s+t=g} D_s^A D_t^B for g = 2..S+1, exact in int32
+ *      (int8 x int8 tensor-core products);
+ *   4. c_ij = (RN(x), RN(x - RN(x))) with x = 2^(e_i+f_j) sum_g L_g 2^-7g,
+ *      summed exactly.
+ * num_slices S in 1..18 (0 = 16).  Error: |C - AB| <= about
+ * 2 l 2^-7S max|a'| max|b'| 2^(e_i+f_j) plus the final DD rounding; S = 16
+ * gives <= 2^-100 |A||B| for entries within a few binades of their row /
+ * column maximum.  Limits: S * 127^2 * l < 2^31, m and n <= 65535.
+ * Workspace: mpgemm_ozaki_workspace_size() bytes, from the buffer set with
+ * mpgemm_set_workspace or allocated stream-ordered.
+ * ------------------------------------------------------------------------- */
+int mpgemm_dd_ozaki(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int num_slices,
+                    void* stream);
+size_t mpgemm_ozaki_workspace_size(int64_t m, int64_t l, int64_t n, int num_slices);
+int mpgemm_ozaki_slices_default(void);
+/* Steps 1-2 alone: digits of a DD matrix X (rows x cols planes).  by_col = 0:
+   row scaling, digits as S planes of rows x lp int8 (lp = cols rounded up to
+   64, zero padded); by_col = 1: column scaling, digits transposed as S planes
+   of cols x lp (lp = rows rounded up to 64).  expo receives the exponents. */
+int mpgemm_ozaki_split(int by_col, int64_t rows, int64_t cols, const double* X, int num_slices, int* expo,
+                       signed char* digits, void* stream);
+/* Step 3 alone: levels = S planes (g = 2..S+1) of m x n int32 from digit
+   planes laid out as mpgemm_ozaki_split writes them. */
+int mpgemm_ozaki_levels(int64_t m, int64_t l, int64_t n, int num_slices, const signed char* DA,
+                        const signed char* DB, int* levels, void* stream);
+
 /* Bytes of workspace one call needs (0 for simple/block). */
 size_t mpgemm_workspace_size(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo,
                              int strassen_depth);
@@ -92,6 +125,56 @@ size_t mpgemm_workspace_size(int kind, int prec_bits, int64_t m, int64_t l, int6
    not free it while calls that may use it are in flight.  Calls on
    different streams that share the buffer must be ordered by the caller. */
 int mpgemm_set_workspace(void* dev_ptr, size_t bytes);
+
+/* ---------------------------------------------------------------------------
+ * Tuning (Section 3).  mpgemm_tune runs the paper's procedure on the given
+ * operands (device pointers in the format of `kind`; C is overwritten):
+ *   1. for each n_min in {16, 32, 64, 128, 256} time the block algorithm on
+ *      the first r rows of A against all of B, r = mpgemm_sample_rows(),
+ *      and predict the full time by scaling T_sample with the ratio of
+ *      per-SM rounds of CTAs, ceil(CTAs(m) / SMs) / ceil(CTAs(r) / SMs)
+ *      (the paper's m / r when both runs are whole rounds);
+ *   2. keep the n_min with the smallest prediction;
+ *   3. time simple, block(n_min) and Strassen depths 1..3 (leaves at n_min)
+ *      and report the fastest.
+ * Timings are medians of 3 event-timed runs (1 with MPGEMM_TUNE_QUICK).
+ * With MPGEMM_TUNE_REMEMBER the choice is stored for this (kind, prec_bits,
+ * m, l, n) and used by MPGEMM_AUTO.  Synchronous; returns MPGEMM_OK or an
+ * error status.
+ * ------------------------------------------------------------------------- */
+enum {
+    MPGEMM_TUNE_VERIFY = 1,       /* also time the full block GEMM for every n_min */
+    MPGEMM_TUNE_REMEMBER = 2,     /* store the choice for MPGEMM_AUTO               */
+    MPGEMM_TUNE_SKIP_SIMPLE = 4,  /* do not time the simple algorithm               */
+    MPGEMM_TUNE_QUICK = 8         /* one timed run per configuration                */
+};
+typedef struct {
+    int algo, n_min, depth;      /* the choice                                    */
+    double best_ms;              /* its measured time                             */
+    int n_cand;                  /* candidates below                              */
+    int cand_n_min[8];
+    int64_t cand_rows[8];        /* rows r of the sample run                      */
+    double cand_sample_ms[8];    /* T_sample                                      */
+    double cand_pred_ms[8];      /* T_sample * m / r                              */
+    double cand_full_ms[8];      /* measured full time (NaN without VERIFY)       */
+    double simple_ms, block_ms;  /* NaN when not run                              */
+    double strassen_ms[4];       /* [d], d = 1..3; NaN when not run               */
+    double tuning_ms;            /* wall time of this call                        */
+} mpgemm_tune_report;
+int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const void* A, const void* B, void* C,
+                int flags, void* stream, mpgemm_tune_report* report);
+/* Forget every remembered choice. */
+int mpgemm_tune_forget(void);
+/* The (algo, n_min, depth) MPGEMM_AUTO would use for this problem. */
+int mpgemm_auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int* algo, int* n_min,
+                       int* depth);
+/* The paper's prediction (Fig. 1): full time = sampled time * m / rows. */
+double mpgemm_predict_time(double t_sample, int64_t m, int64_t rows);
+/* Rows r of the sample run for block size n_min: at least 2 n_min (the
+   paper's tables give predicted = sampled * m / (2 n_min)), at least one full
+   wave of CTAs on `num_sms` SMs, a multiple of the CTA tile, at most m.
+   Host arithmetic only. */
+int64_t mpgemm_sample_rows(int kind, int64_t m, int64_t n, int n_min, int num_sms);
 
 /* Synchronise `stream`, then read and clear the current device's status
    word: MPGEMM_OK, MPGEMM_EOVERFLOW or MPGEMM_ETIMEOUT. */

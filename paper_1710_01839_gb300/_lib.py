@@ -39,6 +39,16 @@ SIGNATURES = {
     "mpgemm_last_cuda_error": (_I, []),
     "mpgemm_version": (_I, []),
     "mpgemm_profile": (_I, [_I]),
+    "mpgemm_dd_ozaki": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _P]),
+    "mpgemm_ozaki_workspace_size": (_SZ, [_I64, _I64, _I64, _I]),
+    "mpgemm_ozaki_slices_default": (_I, []),
+    "mpgemm_ozaki_split": (_I, [_I, _I64, _I64, _P, _I, _P, _P, _P]),
+    "mpgemm_ozaki_levels": (_I, [_I64, _I64, _I64, _I, _P, _P, _P, _P]),
+    "mpgemm_tune": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _I, _P, _P]),
+    "mpgemm_tune_forget": (_I, []),
+    "mpgemm_auto_choice": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P]),
+    "mpgemm_predict_time": (ctypes.c_double, [ctypes.c_double, _I64, _I64]),
+    "mpgemm_sample_rows": (_I64, [_I, _I64, _I64, _I, _I]),
     "mpgemm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
 }
 

@@ -4,11 +4,12 @@
 //
 // The multiply-accumulate of the GEMM (Eq 1's c <- c + a_ik b_kj) uses a
 // deferred-renormalisation accumulator instead of a full DD add per step:
-//   DD:  state (s, t).  p = RN(ah bh) and its exact error from one FMA, the
-//        two cross products folded into that error with two more FMAs, then
-//        (s, r) = TwoSum(s, p) and t <- t + (r + e).  Every DD_RENORM steps
-//        (s, t) = TwoSum(s, t).  12 FP64 operations per step (the library
-//        DD add + multiply pair costs 27).
+//   DD:  state (s, t).  p = RN(ah bh) and its exact error e from one FMA,
+//        the two cross products accumulated into t with two more FMAs, then
+//        (s, r) = TwoSum(s, p) and t <- t + (e + r).  Every DD_RENORM steps
+//        (s, t) = TwoSum(s, t).  9 FP64 operations per step with the
+//        exponent-ordered TwoSum below (the library DD add + multiply pair
+//        costs 27).
 //        Worst-case error after l steps: about (DD_RENORM + 3) l u^2 sum|a||b|
 //        plus O(u^2) per product, inside the required 16 l u^2 |A||B|
 //        (= 4 l 2^-104 |A||B|) for DD_RENORM = 8.
@@ -34,13 +35,19 @@ namespace mpg {
 
 // ---------------------------------------------------------------- EFTs
 
-// Knuth's TwoSum: s = RN(a + b), e = a + b - s exactly.
+// TwoSum: s = RN(a + b), e = a + b - s exactly, for any a, b.  Computed as
+// Dekker's Fast2Sum after ordering the operands by their exponent fields,
+// compared on the integer pipe: it returns exactly what Knuth's 6-operation
+// TwoSum returns (both are error-free), with 3 FP64 operations instead of 6.
+// On GB300 the FP64 pipe (2 operations / clock / SM) is the bottleneck and
+// the issue slots for the integer compare and selects are otherwise idle.
 __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
-    double x = __dadd_rn(a, b);
-    double bv = __dsub_rn(x, a);
-    double av = __dsub_rn(x, bv);
-    e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
-    s = x;
+    const int ea = __double2hiint(a) & 0x7ff00000, eb = __double2hiint(b) & 0x7ff00000;
+    const bool sw = eb > ea;
+    const double x = sw ? b : a, y = sw ? a : b;
+    const double r = __dadd_rn(x, y);
+    e = __dsub_rn(y, __dsub_rn(r, x));
+    s = r;
 }
 
 // Dekker's Fast2Sum (exact when exponent(a) >= exponent(b)).
@@ -64,12 +71,12 @@ __device__ __forceinline__ void dd_zero(DDAcc& c) {
 __device__ __forceinline__ void dd_mac(DDAcc& c, double ah, double al, double bh, double bl) {
     double p = __dmul_rn(ah, bh);
     double e = __fma_rn(ah, bh, -p);   // exact error of p
-    e = __fma_rn(ah, bl, e);
-    e = __fma_rn(al, bh, e);
+    double t = __fma_rn(ah, bl, c.t);   // cross products straight into the low part
+    t = __fma_rn(al, bh, t);
     double s, r;
     two_sum(c.s, p, s, r);
     c.s = s;
-    c.t = __dadd_rn(c.t, __dadd_rn(r, e));
+    c.t = __dadd_rn(t, __dadd_rn(e, r));
 }
 
 __device__ __forceinline__ void dd_renorm(DDAcc& c) {

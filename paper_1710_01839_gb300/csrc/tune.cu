@@ -1,19 +1,252 @@
-// Selection of algorithm, block size n_min and Strassen depth for
-// MPGEMM_AUTO (the paper's tuning step, Section 3).
+// The tuning procedure of the paper's Section 3, on the GPU:
+//   1. for every candidate block size n_min, time the block algorithm on A's
+//      first r rows against the whole of B and predict the full time as
+//      T_sample * m / r (Fig. 1; the paper's tables imply r = 2 n_min);
+//   2. keep the n_min with the smallest prediction;
+//   3. time the simple algorithm, the block algorithm with that n_min and
+//      Strassen (depths 1..3, leaves at that n_min) and pick the fastest.
+// GPU adaptation of step 1: a reduced-row launch must still fill the machine,
+// so r is at least the rows that give one full wave of CTAs (same per-CTA
+// work as the full run), rounded up to the CTA tile; and the scale factor
+// m / r becomes the ratio of per-SM rounds of CTAs (full run / sample), which
+// equals m / r when both are whole rounds and also covers the partly filled
+// last round.
+//
+// Choices can be remembered per problem shape; MPGEMM_AUTO then uses them,
+// else the cost model if one is installed, else a fixed default.
+#include <algorithm>
+#include <cstring>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "common.cuh"
+#include "kernels.h"
+#include "strassen.h"
 #include "tune.h"
 
 namespace mpg {
 
+using Key = std::tuple<int, int, int64_t, int64_t, int64_t>;
+static std::mutex g_tmu;
+static std::map<Key, Choice> g_table;
+
+// Installed cost model (mlp.cu); returns false when none is installed.
+bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, Choice* out);
+
 int auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, Choice* out) {
-    (void)prec_bits;
-    (void)m;
-    (void)l;
-    (void)n;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        auto it = g_table.find(Key(kind, prec_bits, m, l, n));
+        if (it != g_table.end()) {
+            *out = it->second;
+            return MPGEMM_OK;
+        }
+    }
+    if (cost_model_choice(kind, prec_bits, m, l, n, out)) return MPGEMM_OK;
     out->algo = MPGEMM_BLOCK;
     out->n_min = default_n_min(kind);
     out->depth = 0;
     return MPGEMM_OK;
 }
 
+// CTA tile edge used by the block kernel for a given n_min (mirrors the
+// launch selection in gemm_ddqd.cu / gemm_mp.cu).
+int block_tile(int kind, int n_min) {
+    if (kind == MPGEMM_KIND_DD) return n_min <= 16 ? 16 : n_min <= 32 ? 32 : 64;
+    if (kind == MPGEMM_KIND_QD) return n_min <= 16 ? 16 : 32;
+    return 16;
+}
+
+// Resident CTAs per SM assumed for a full wave (measured occupancy of the
+// block kernels: 256-thread CTAs; DD 64-tiles use ~180 registers per thread).
+static int ctas_per_sm(int kind, int tile) {
+    if (kind == MPGEMM_KIND_DD) return tile == 64 ? 1 : tile == 32 ? 3 : 4;
+    if (kind == MPGEMM_KIND_QD) return tile == 32 ? 2 : 3;
+    return 2;
+}
+
+// Per-SM rounds of CTAs for `rows` rows of C: the block kernels are bound
+// by one pipe per SM (FP64 for DD/QD, integer for multi-limb), so an SM's
+// co-resident CTAs share it and the run time follows the largest number of
+// CTAs any SM receives, ceil(CTAs / SMs).
+static double rounds(int kind, int64_t rows, int64_t n, int n_min, int sms) {
+    int tile = block_tile(kind, n_min);
+    int64_t ctas = ((rows + tile - 1) / tile) * ((n + tile - 1) / tile);
+    return (double)((ctas + sms - 1) / sms);
+}
+
+int64_t sample_rows_rule(int64_t m, int n_min, int64_t wave_rows, int tile) {
+    int64_t r = 2 * (int64_t)n_min;
+    if (r < wave_rows) r = wave_rows;
+    if (tile > 0) r = (r + tile - 1) / tile * tile;
+    if (r > m) r = m;
+    return r;
+}
+
+namespace {
+
+struct Problem {
+    int kind, prec_bits;
+    int64_t m, l, n;
+    const void* A;
+    const void* B;
+    void* C;
+    cudaStream_t s;
+};
+
+int run_once(const Problem& P, int algo, int n_min, int depth, int64_t rows) {
+    if (P.kind == MPGEMM_KIND_MP) {
+        int w = P.prec_bits / 32;
+        View<const uint32_t> a{(const uint32_t*)P.A, P.l, P.m * P.l, 0};
+        View<const uint32_t> b = planes_view((const uint32_t*)P.B, P.l, P.n);
+        View<uint32_t> c{(uint32_t*)P.C, P.n, P.m * P.n, 0};
+        if (algo == MPGEMM_STRASSEN) return strassen_mp(w, P.m, P.l, P.n, a, b, c, n_min, depth, P.s);
+        return mp_gemm(w, algo, rows, P.l, P.n, 1, a, b, c, n_min, P.s);
+    }
+    View<const double> a{(const double*)P.A, P.l, P.m * P.l, 0};
+    View<const double> b = planes_view((const double*)P.B, P.l, P.n);
+    View<double> c{(double*)P.C, P.n, P.m * P.n, 0};
+    if (algo == MPGEMM_STRASSEN) return strassen_ddqd(P.kind, P.m, P.l, P.n, a, b, c, n_min, depth, P.s);
+    return ddqd_gemm(P.kind, algo, rows, P.l, P.n, 1, a, b, c, n_min, P.s);
+}
+
+// Median of `reps` event-timed runs after one warm-up, in ms.
+int time_it(const Problem& P, int algo, int n_min, int depth, int64_t rows, int reps, double* ms) {
+    cudaEvent_t e0, e1;
+    MPG_CUDA(cudaEventCreate(&e0));
+    MPG_CUDA(cudaEventCreate(&e1));
+    int rc = run_once(P, algo, n_min, depth, rows);
+    std::vector<double> t;
+    for (int i = 0; i < reps && rc == MPGEMM_OK; i++) {
+        cudaEventRecord(e0, P.s);
+        rc = run_once(P, algo, n_min, depth, rows);
+        cudaEventRecord(e1, P.s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = MPGEMM_ECUDA;
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        t.push_back(f);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    std::sort(t.begin(), t.end());
+    *ms = t.empty() ? 0.0 : t[t.size() / 2];
+    return MPGEMM_OK;
+}
+
+}  // namespace
+
 }  // namespace mpg
+
+using namespace mpg;
+
+extern "C" {
+
+double mpgemm_predict_time(double t_sample, int64_t m, int64_t rows) {
+    if (rows <= 0) return NAN;
+    return t_sample * (double)m / (double)rows;
+}
+
+int64_t mpgemm_sample_rows(int kind, int64_t m, int64_t n, int n_min, int num_sms) {
+    int tile = block_tile(kind, n_min);
+    int64_t tiles_n = (n + tile - 1) / tile;
+    int64_t wave_ctas = (int64_t)num_sms * ctas_per_sm(kind, tile);
+    int64_t wave_rows = tiles_n > 0 ? (wave_ctas + tiles_n - 1) / tiles_n * tile : tile;
+    return sample_rows_rule(m, n_min, wave_rows, tile);
+}
+
+int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const void* A, const void* B, void* C,
+                int flags, void* stream, mpgemm_tune_report* rep) {
+    if (!rep || m <= 0 || l <= 0 || n <= 0 || !A || !B || !C) return MPGEMM_EINVAL;
+    if (kind < MPGEMM_KIND_DD || kind > MPGEMM_KIND_MP) return MPGEMM_EINVAL;
+    if (kind == MPGEMM_KIND_MP && (prec_bits <= 0 || prec_bits % 32)) return MPGEMM_EINVAL;
+    auto t_start = std::chrono::steady_clock::now();
+    Problem P{kind, kind == MPGEMM_KIND_MP ? prec_bits : 0, m, l, n, A, B, C, (cudaStream_t)stream};
+    int dev = 0, sms = 0;
+    MPG_CUDA(cudaGetDevice(&dev));
+    MPG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int reps = (flags & MPGEMM_TUNE_QUICK) ? 1 : 3;
+    memset(rep, 0, sizeof *rep);
+    static const int cands[] = {16, 32, 64, 128, 256};
+    int best = -1;
+    double best_pred = 0;
+    for (int c = 0; c < 5; c++) {
+        int nm = cands[c];
+        int64_t r = mpgemm_sample_rows(kind, m, n, nm, sms);
+        double ms = 0;
+        int rc = time_it(P, MPGEMM_BLOCK, nm, 0, r, reps, &ms);
+        if (rc) return rc;
+        rep->cand_n_min[c] = nm;
+        rep->cand_rows[c] = r;
+        rep->cand_sample_ms[c] = ms;
+        rep->cand_pred_ms[c] = ms * rounds(kind, m, n, nm, sms) / rounds(kind, r, n, nm, sms);
+        rep->cand_full_ms[c] = NAN;
+        if (flags & MPGEMM_TUNE_VERIFY) {
+            rc = time_it(P, MPGEMM_BLOCK, nm, 0, m, reps, &rep->cand_full_ms[c]);
+            if (rc) return rc;
+        }
+        if (best < 0 || rep->cand_pred_ms[c] < best_pred) {
+            best = c;
+            best_pred = rep->cand_pred_ms[c];
+        }
+    }
+    rep->n_cand = 5;
+    const int nm = cands[best];
+    int rc;
+    rep->simple_ms = NAN;
+    if (!(flags & MPGEMM_TUNE_SKIP_SIMPLE)) {
+        rc = time_it(P, MPGEMM_SIMPLE, nm, 0, m, reps, &rep->simple_ms);
+        if (rc) return rc;
+    }
+    rc = time_it(P, MPGEMM_BLOCK, nm, 0, m, reps, &rep->block_ms);
+    if (rc) return rc;
+    Choice ch{MPGEMM_BLOCK, nm, 0};
+    double best_ms = rep->block_ms;
+    if (!std::isnan(rep->simple_ms) && rep->simple_ms < best_ms) {
+        ch = Choice{MPGEMM_SIMPLE, nm, 0};
+        best_ms = rep->simple_ms;
+    }
+    for (int d = 1; d <= 3; d++) {
+        rep->strassen_ms[d] = NAN;
+        int64_t q = (int64_t)1 << d;
+        if (m % q || l % q || n % q || (m >> d) < 16 || (n >> d) < 16 || (l >> d) < 16) continue;
+        rc = time_it(P, MPGEMM_STRASSEN, nm, d, m, reps, &rep->strassen_ms[d]);
+        if (rc) return rc;
+        if (rep->strassen_ms[d] < best_ms) {
+            ch = Choice{MPGEMM_STRASSEN, nm, d};
+            best_ms = rep->strassen_ms[d];
+        }
+    }
+    rep->algo = ch.algo;
+    rep->n_min = ch.n_min;
+    rep->depth = ch.depth;
+    rep->best_ms = best_ms;
+    if (flags & MPGEMM_TUNE_REMEMBER) {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        g_table[Key(kind, P.prec_bits, m, l, n)] = ch;
+    }
+    rep->tuning_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    return MPGEMM_OK;
+}
+
+int mpgemm_tune_forget(void) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_table.clear();
+    return MPGEMM_OK;
+}
+
+int mpgemm_auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int* algo, int* n_min, int* depth) {
+    Choice c;
+    int rc = auto_choice(kind, prec_bits, m, l, n, &c);
+    if (rc) return rc;
+    if (algo) *algo = c.algo;
+    if (n_min) *n_min = c.n_min;
+    if (depth) *depth = c.depth;
+    return MPGEMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+"""The tuning step (Section 3) through the C ABI: mpgemm_tune."""
+
+from __future__ import annotations
+
+import ctypes
+import math
+
+from ._lib import KIND, check, lib
+
+ALGO_NAME = {0: "simple", 1: "block", 2: "strassen", 3: "auto"}
+VERIFY, REMEMBER, SKIP_SIMPLE, QUICK = 1, 2, 4, 8
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("n_min", ctypes.c_int), ("depth", ctypes.c_int),
+                ("best_ms", ctypes.c_double), ("n_cand", ctypes.c_int),
+                ("cand_n_min", ctypes.c_int * 8), ("cand_rows", ctypes.c_int64 * 8),
+                ("cand_sample_ms", ctypes.c_double * 8), ("cand_pred_ms", ctypes.c_double * 8),
+                ("cand_full_ms", ctypes.c_double * 8), ("simple_ms", ctypes.c_double),
+                ("block_ms", ctypes.c_double), ("strassen_ms", ctypes.c_double * 4),
+                ("tuning_ms", ctypes.c_double)]
+
+
+def _nan(x):
+    return None if x is None or (isinstance(x, float) and math.isnan(x)) else x
+
+
+def report_dict(r: TuneReport):
+    cands = []
+    for i in range(r.n_cand):
+        full = _nan(r.cand_full_ms[i])
+        pred = r.cand_pred_ms[i]
+        cands.append({"n_min": r.cand_n_min[i], "rows": r.cand_rows[i], "sample_ms": r.cand_sample_ms[i],
+                      "pred_ms": pred, "full_ms": full,
+                      "rel_diff": (abs(pred - full) / full) if full else None})
+    return {"algo": ALGO_NAME[r.algo], "n_min": r.n_min, "depth": r.depth, "best_ms": r.best_ms,
+            "candidates": cands, "simple_ms": _nan(r.simple_ms), "block_ms": r.block_ms,
+            "strassen_ms": {d: _nan(r.strassen_ms[d]) for d in (1, 2, 3)}, "tuning_ms": r.tuning_ms}
+
+
+def tune(fmt, A, B, C, flags=REMEMBER, prec_bits=0, stream=None):
+    """Run mpgemm_tune on device tensors; returns (choice dict, report dict)."""
+    import torch
+    kind = KIND["mp" if fmt.startswith("mp") else fmt]
+    m, l = A.shape[1], A.shape[2]
+    n = B.shape[2]
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    rep = TuneReport()
+    rc = lib().mpgemm_tune(kind, int(prec_bits), m, l, n, ctypes.c_void_p(A.data_ptr()),
+                           ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()), int(flags),
+                           ctypes.c_void_p(int(stream.cuda_stream)), ctypes.byref(rep))
+    check(rc)
+    d = report_dict(rep)
+    return {"algo": d["algo"], "n_min": d["n_min"], "depth": d["depth"]}, d
+
+
+def predict_time(t_sample, m, rows):
+    return float(lib().mpgemm_predict_time(float(t_sample), int(m), int(rows)))
+
+
+def sample_rows(fmt, m, n, n_min, num_sms=152):
+    return int(lib().mpgemm_sample_rows(KIND[fmt], int(m), int(n), int(n_min), int(num_sms)))
