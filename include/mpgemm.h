@@ -117,6 +117,34 @@ int mpgemm_ozaki_split(int by_col, int64_t rows, int64_t cols, const double* X, 
 int mpgemm_ozaki_levels(int64_t m, int64_t l, int64_t n, int num_slices, const signed char* DA,
                         const signed char* DB, int* levels, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * DD Strassen that allocates nothing.  The paper has no counterpart.  It is
+ * for callers that cannot allocate device memory while they run: for
+ * example a service whose device memory is all handed to its own pool
+ * allocator at start-up, after which nothing else may allocate, or a
+ * latency-critical loop that cannot afford an allocation's possible
+ * device-wide synchronisation or its failure.  It computes what
+ * mpgemm_dd(m, l, n, A, B, C, MPGEMM_STRASSEN, n_min, strassen_depth, stream)
+ * computes, with the same kernels, but its workspace is a fixed 32 MiB
+ * scratch array inside the library (device memory that every GPU which loads
+ * the library holds until the process exits), and it calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The caller still passes A, B and C.
+ *   - strassen_depth must be 1..4 (MPGEMM_EINVAL otherwise); every other
+ *     argument is checked as in mpgemm_dd.
+ *   - A problem whose Strassen workspace (mpgemm_workspace_size) is larger
+ *     than 32 MiB is refused with MPGEMM_ENOMEM before anything is launched.
+ *   - The first call on a device finds the scratch array's device address
+ *     (one cudaGetSymbolAddress, made with that device current); make that
+ *     first call before any stream capture.
+ *   - All calls share the one scratch array.  Calls whose kernels may overlap
+ *     on the GPU (different streams with no ordering between them) race on it
+ *     and corrupt each other's results: order them on one stream or with
+ *     events.  No part of the scratch needs clearing between calls: every
+ *     element a call reads was written earlier in the same call.
+ * ------------------------------------------------------------------------- */
+int mpgemm_dd_strassen_noalloc(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C,
+                               int n_min, int strassen_depth, void* stream);
+
 /* Bytes of workspace one call needs (0 for simple/block). */
 size_t mpgemm_workspace_size(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo,
                              int strassen_depth);

@@ -39,6 +39,7 @@ SIGNATURES = {
     "mpgemm_last_cuda_error": (_I, []),
     "mpgemm_version": (_I, []),
     "mpgemm_profile": (_I, [_I]),
+    "mpgemm_dd_strassen_noalloc": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _I, _P]),
     "mpgemm_dd_ozaki": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _P]),
     "mpgemm_ozaki_workspace_size": (_SZ, [_I64, _I64, _I64, _I]),
     "mpgemm_ozaki_slices_default": (_I, []),
