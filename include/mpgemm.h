@@ -145,6 +145,83 @@ int mpgemm_ozaki_levels(int64_t m, int64_t l, int64_t n, int num_slices, const s
 int mpgemm_dd_strassen_noalloc(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C,
                                int n_min, int strassen_depth, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched GEMMs of uneven sizes and mixed precisions in one persistent launch
+ * (an extension; the paper runs one GEMM at a time).  Each descriptor is one
+ * C := AB with its own sizes, format and device pointers (layouts as above).
+ *   kind        MPGEMM_KIND_DD, MPGEMM_KIND_QD, or MPGEMM_KIND_MP with
+ *               prec_bits = 256 (the only multi-limb width of the batched
+ *               kernel)
+ *   tile        edge of the C tile one CTA computes: 16 or 32 for DD / QD
+ *               (0 = the cost model's choice when one is installed, else
+ *               32), always 16 for multi-limb
+ * mpgemm_batched_plan validates the descriptors, builds the table of work
+ * items (one per C tile, heaviest first) and copies it to the device
+ * (cudaMalloc + synchronous copies: plan outside hot loops).  The plan keeps
+ * the pointers; the caller keeps the matrices alive.
+ * mpgemm_batched_run resets the plan's work counter and launches the
+ * persistent kernel on `stream` (one CTA per resident slot; CTAs take work
+ * items from an atomic counter and never wait for each other).  Runs of the
+ * same plan must not overlap (they share the counter).
+ * mpgemm_batched_run_graph does the same through a CUDA graph captured on the
+ * plan's first call (on a stream of the plan's own) and replayed afterwards.
+ * mpgemm_batched_sequential runs the same descriptors as one ordinary launch
+ * per GEMM (block algorithm, n_min = tile): the baseline.
+ * Results are bit-identical to mpgemm_dd / mpgemm_qd / mpgemm_mp with
+ * MPGEMM_BLOCK and n_min = tile.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int kind;
+    int prec_bits;
+    int64_t m, l, n;
+    const void* A;
+    const void* B;
+    void* C;
+    int tile;
+    int reserved;
+} mpgemm_desc;
+typedef struct mpgemm_plan_s* mpgemm_plan;
+int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* plan);
+int mpgemm_batched_run(mpgemm_plan plan, void* stream);
+int mpgemm_batched_run_graph(mpgemm_plan plan, void* stream);
+int mpgemm_batched_destroy(mpgemm_plan plan);
+/* Work items, persistent grid size and the tile chosen for each descriptor. */
+int mpgemm_batched_info(mpgemm_plan plan, int* work_items, int* grid, int* tiles, int tiles_len);
+int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * FP32 MLP cost model (an extension standing in for the paper's time
+ * prediction, Section 3): log(time) of a configuration (m, l, n, format,
+ * precision bits, algorithm, tile, Strassen depth) from 16 features through
+ * two hidden layers of 64 ReLU units, trained with Adam by hand-written
+ * kernels on timings the library measures itself.  Once trained (or loaded)
+ * it is installed for the process: MPGEMM_AUTO then picks, for shapes it has
+ * not tuned, the candidate (simple, block tile 16/32/64, Strassen depth 1..3
+ * with those tiles) of least predicted time, and batched plans use it for
+ * tile = 0.  mpgemm_tune (measured) remains available and wins when it has
+ * a remembered choice.
+ *   mpgemm_cost_features   feature vector (mpgemm_cost_num_features floats)
+ *   mpgemm_cost_collect    time `count` random configurations (shapes
+ *                          log-uniform in [16, max_dim], formats DD / QD /
+ *                          256-bit, valid algorithms); host output arrays;
+ *                          synchronous; allocates its own operand buffers
+ *   mpgemm_cost_train      train a new model (epochs x count/128 Adam steps,
+ *                          lr 2e-3) and install it; optional per-epoch loss
+ *   mpgemm_cost_predict    predicted milliseconds for host feature vectors
+ *   mpgemm_cost_save/load  binary model file; mpgemm_cost_clear uninstalls
+ * ------------------------------------------------------------------------- */
+int mpgemm_cost_num_features(void);
+int mpgemm_cost_features(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo, int tile, int depth,
+                         float* out);
+int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* features, float* times_ms,
+                        void* stream);
+int mpgemm_cost_train(const float* features, const float* times_ms, int count, int epochs, unsigned long long seed,
+                      float* loss_per_epoch);
+int mpgemm_cost_predict(const float* features, int count, float* out_ms);
+int mpgemm_cost_save(const char* path);
+int mpgemm_cost_load(const char* path);
+int mpgemm_cost_clear(void);
+
 /* Bytes of workspace one call needs (0 for simple/block). */
 size_t mpgemm_workspace_size(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo,
                              int strassen_depth);

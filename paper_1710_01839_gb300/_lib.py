@@ -39,6 +39,20 @@ SIGNATURES = {
     "mpgemm_last_cuda_error": (_I, []),
     "mpgemm_version": (_I, []),
     "mpgemm_profile": (_I, [_I]),
+    "mpgemm_cost_num_features": (_I, []),
+    "mpgemm_cost_features": (_I, [_I, _I, _I64, _I64, _I64, _I, _I, _I, _P]),
+    "mpgemm_cost_collect": (_I, [_I, ctypes.c_ulonglong, _I, _P, _P, _P]),
+    "mpgemm_cost_train": (_I, [_P, _P, _I, _I, ctypes.c_ulonglong, _P]),
+    "mpgemm_cost_predict": (_I, [_P, _I, _P]),
+    "mpgemm_cost_save": (_I, [ctypes.c_char_p]),
+    "mpgemm_cost_load": (_I, [ctypes.c_char_p]),
+    "mpgemm_cost_clear": (_I, []),
+    "mpgemm_batched_plan": (_I, [_P, _I, _P]),
+    "mpgemm_batched_run": (_I, [_P, _P]),
+    "mpgemm_batched_run_graph": (_I, [_P, _P]),
+    "mpgemm_batched_destroy": (_I, [_P]),
+    "mpgemm_batched_info": (_I, [_P, _P, _P, _P, _I]),
+    "mpgemm_batched_sequential": (_I, [_P, _I, _P]),
     "mpgemm_dd_strassen_noalloc": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _I, _P]),
     "mpgemm_dd_ozaki": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _P]),
     "mpgemm_ozaki_workspace_size": (_SZ, [_I64, _I64, _I64, _I]),

@@ -1,0 +1,65 @@
+"""Batched uneven mixed-precision GEMMs through the C ABI
+(mpgemm_batched_plan / _run / _run_graph / _sequential)."""
+
+from __future__ import annotations
+
+import ctypes
+
+from ._lib import KIND, check, lib
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("prec_bits", ctypes.c_int), ("m", ctypes.c_int64),
+                ("l", ctypes.c_int64), ("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("tile", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(int(s.cuda_stream))
+
+
+def make_descs(problems, tiles=None):
+    """problems: list of (fmt, A, B, C) with device tensors; fmt in
+    {'dd', 'qd', 'mp256'}.  tiles: optional list of tile edges."""
+    arr = (Desc * len(problems))()
+    for i, (fmt, A, B, C) in enumerate(problems):
+        kind = KIND["mp" if fmt.startswith("mp") else fmt]
+        arr[i] = Desc(kind, 256 if kind == 2 else 0, A.shape[1], A.shape[2], B.shape[2], A.data_ptr(), B.data_ptr(),
+                      C.data_ptr(), 0 if tiles is None else int(tiles[i]), 0)
+    return arr
+
+
+class Plan:
+    def __init__(self, descs):
+        self.descs = descs
+        self.h = ctypes.c_void_p()
+        check(lib().mpgemm_batched_plan(descs, len(descs), ctypes.byref(self.h)))
+
+    def run(self, stream=None):
+        check(lib().mpgemm_batched_run(self.h, _stream(stream)))
+
+    def run_graph(self, stream=None):
+        check(lib().mpgemm_batched_run_graph(self.h, _stream(stream)))
+
+    def info(self):
+        w, g = ctypes.c_int(), ctypes.c_int()
+        t = (ctypes.c_int * len(self.descs))()
+        check(lib().mpgemm_batched_info(self.h, ctypes.byref(w), ctypes.byref(g), t, len(self.descs)))
+        return {"work_items": w.value, "grid": g.value, "tiles": list(t)}
+
+    def close(self):
+        if self.h:
+            lib().mpgemm_batched_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sequential(descs, stream=None):
+    check(lib().mpgemm_batched_sequential(descs, len(descs), _stream(stream)))

@@ -27,7 +27,7 @@ struct View {
 };
 
 template <class T>
-inline View<T> planes_view(T* p, int64_t rows, int64_t cols) {
+__host__ __device__ inline View<T> planes_view(T* p, int64_t rows, int64_t cols) {
     View<T> v{p, cols, rows * cols, 0};
     return v;
 }

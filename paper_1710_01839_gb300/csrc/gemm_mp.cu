@@ -9,34 +9,10 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "mp_arith.cuh"
+#include "tiles.cuh"
 #include "profile.h"
 
 namespace mpg {
-
-template <int W>
-__device__ __forceinline__ void load_mp(MPV<W>& v, const uint32_t* p, int64_t ps) {
-    v.e = (int)p[0];
-    v.f = p[ps];
-#pragma unroll
-    for (int i = 0; i < W; i++) v.m[i] = p[(2 + i) * ps];
-}
-
-template <int W>
-__device__ __forceinline__ void store_mp(const MPV<W>& v, uint32_t* p, int64_t ps) {
-    p[0] = (uint32_t)v.e;
-    p[ps] = v.f;
-#pragma unroll
-    for (int i = 0; i < W; i++) p[(2 + i) * ps] = v.m[i];
-}
-
-template <int W>
-__device__ __forceinline__ void mp_mac(MPV<W>& c, const MPV<W>& a, const MPV<W>& b, unsigned& st) {
-    MPV<W> t;
-    mp_mul<W>(a, b, t, st);
-    MPV<W> s;
-    mp_add<W>(c, t, s, st);
-    c = s;
-}
 
 template <int W>
 __global__ void __launch_bounds__(256) k_mp_simple(int64_t m, int64_t l, int64_t n, View<const uint32_t> A,
@@ -58,58 +34,19 @@ __global__ void __launch_bounds__(256) k_mp_simple(int64_t m, int64_t l, int64_t
     if (st) atomicOr(status, st);
 }
 
-// CTA = 16 x 16 outputs, one per thread; A rows / B columns staged through
-// shared memory KT elements deep as [k][row][word]; CTA order follows the
-// super-tile raster with group G.
+// CTA = 16 x 16 outputs (mp_block_tile); CTA order follows the super-tile
+// raster with group G.
 template <int W, int KT>
 __global__ void __launch_bounds__(256) k_mp_block(int64_t m, int64_t l, int64_t n, View<const uint32_t> A,
                                                   View<const uint32_t> B, View<uint32_t> C, unsigned G,
                                                   unsigned* status) {
     constexpr int BM = 16;
-    constexpr int E = 2 + W;
-    constexpr int WORDS = BM * KT * E;
-    __shared__ uint32_t As[KT][BM][E];
-    __shared__ uint32_t Bs[KT][BM][E];
+    __shared__ uint32_t sm[2 * KT * BM * (2 + W)];
     const unsigned tiles_m = ceil_div(m, BM), tiles_n = ceil_div(n, BM);
     unsigned tm, tn;
     raster(blockIdx.x, tiles_m, tiles_n, G, tm, tn);
-    const int64_t z = blockIdx.y;
-    const int64_t i0 = (int64_t)tm * BM, j0 = (int64_t)tn * BM;
-    const int tid = threadIdx.x, ty = tid / BM, tx = tid % BM;
     unsigned st = 0u;
-    MPV<W> c;
-    mp_set_zero(c, 0u);
-    for (int64_t k0 = 0; k0 < l; k0 += KT) {
-        for (int idx = tid; idx < WORDS; idx += 256) {
-            int q = idx / (BM * KT), rem = idx % (BM * KT);
-            int r = rem / KT, cc = rem % KT;          // A: row r, k = k0 + cc
-            int64_t i = i0 + r, k = k0 + cc;
-            uint32_t va = (i < m && k < l) ? __ldg(A.at(z, q, i, k)) : (q == 1 ? 2u : 0u);
-            As[cc][r][q] = va;
-            int rb = rem / BM, cb = rem % BM;         // B: k = k0 + rb, column cb
-            int64_t kb = k0 + rb, j = j0 + cb;
-            uint32_t vb = (kb < l && j < n) ? __ldg(B.at(z, q, kb, j)) : (q == 1 ? 2u : 0u);
-            Bs[rb][cb][q] = vb;
-        }
-        __syncthreads();
-        const int kmax = (l - k0) < KT ? (int)(l - k0) : KT;
-        for (int kk = 0; kk < kmax; kk++) {
-            MPV<W> a, b;
-            a.e = (int)As[kk][ty][0];
-            a.f = As[kk][ty][1];
-            b.e = (int)Bs[kk][tx][0];
-            b.f = Bs[kk][tx][1];
-#pragma unroll
-            for (int w = 0; w < W; w++) {
-                a.m[w] = As[kk][ty][2 + w];
-                b.m[w] = Bs[kk][tx][2 + w];
-            }
-            mp_mac(c, a, b, st);
-        }
-        __syncthreads();
-    }
-    int64_t i = i0 + ty, j = j0 + tx;
-    if (i < m && j < n) store_mp(c, C.at(z, 0, i, j), C.ps);
+    mp_block_tile<W, KT>(m, l, n, A, B, C, blockIdx.y, (int64_t)tm * BM, (int64_t)tn * BM, sm, st);
     if (st) atomicOr(status, st);
 }
 

@@ -1,0 +1,222 @@
+// Device building blocks shared by the GEMM kernels and the batched
+// persistent kernel: the DD / QD element formats and one CTA's block of C.
+#pragma once
+
+#include "common.cuh"
+#include "ddqd.cuh"
+#include "mp_arith.cuh"
+
+namespace mpg {
+
+struct DDFmt {
+    static constexpr int P = 2;
+    static constexpr int R = DD_RENORM;
+    using Acc = DDAcc;
+    __device__ static void zero(Acc& c) { dd_zero(c); }
+    __device__ static void mac(Acc& c, const double* a, const double* b) { dd_mac(c, a[0], a[1], b[0], b[1]); }
+    __device__ static void renorm(Acc& c) { dd_renorm(c); }
+    __device__ static void finish(Acc& c, double* out) {
+        double h, l;
+        two_sum(c.s, c.t, h, l);
+        out[0] = h;
+        out[1] = l;
+    }
+};
+
+struct QDFmt {
+    static constexpr int P = 4;
+    static constexpr int R = QD_RENORM;
+    using Acc = QDAcc;
+    __device__ static void zero(Acc& c) { qd_zero(c); }
+    __device__ static void mac(Acc& c, const double* a, const double* b) { qd_mac(c, a, b); }
+    __device__ static void renorm(Acc& c) { qd_renorm(c); }
+    __device__ static void finish(Acc& c, double* out) {
+        qd_finish(c);
+        out[0] = c.s0;
+        out[1] = c.s1;
+        out[2] = c.s2;
+        out[3] = c.s3;
+    }
+};
+
+// One BM x BM block of C (rows i0.., columns j0.., batch z) computed by the
+// calling CTA (NT = (BM/RM)^2 threads): each thread an RM x RM register tile
+// (rows ty + r*TPD, columns tx + c*TPD); K advances in panels of KT staged
+// through shared memory `sm` (2 * KT * BM * P doubles) as [k][row][plane],
+// the next panel's global loads issued before the current panel's arithmetic.
+template <class Fmt, int BM, int RM, int KT>
+__device__ __forceinline__ void ddqd_block_tile(int64_t m, int64_t l, int64_t n, const View<const double>& A,
+                                                const View<const double>& B, const View<double>& C, int64_t z,
+                                                int64_t i0, int64_t j0, double* sm) {
+    constexpr int P = Fmt::P;
+    constexpr int TPD = BM / RM;
+    constexpr int NT = TPD * TPD;
+    constexpr int LD = (BM * KT) / NT;   // elements per thread per panel and operand
+    static_assert((BM * KT) % NT == 0, "panel must split evenly over the threads");
+    static_assert(KT % Fmt::R == 0, "renormalisation period must divide the panel depth");
+    auto As = reinterpret_cast<double (*)[BM][P]>(sm);
+    auto Bs = reinterpret_cast<double (*)[BM][P]>(sm + KT * BM * P);
+    const int tid = threadIdx.x;
+    const int ty = tid / TPD, tx = tid % TPD;
+
+    typename Fmt::Acc acc[RM][RM];
+#pragma unroll
+    for (int r = 0; r < RM; r++)
+#pragma unroll
+        for (int c = 0; c < RM; c++) Fmt::zero(acc[r][c]);
+
+    double ra[LD][P], rb[LD][P];
+    auto gload = [&](int64_t k0) {
+#pragma unroll
+        for (int v = 0; v < LD; v++) {
+            int idx = tid + v * NT;
+            int r = idx / KT, c = idx % KT;          // A panel: BM rows x KT
+            int64_t i = i0 + r, k = k0 + c;
+            bool ok = i < m && k < l;
+#pragma unroll
+            for (int q = 0; q < P; q++) ra[v][q] = ok ? __ldg(A.at(z, q, i, k)) : 0.0;
+            int rr = idx / BM, cc = idx % BM;        // B panel: KT rows x BM
+            int64_t kb = k0 + rr, j = j0 + cc;
+            bool okb = kb < l && j < n;
+#pragma unroll
+            for (int q = 0; q < P; q++) rb[v][q] = okb ? __ldg(B.at(z, q, kb, j)) : 0.0;
+        }
+    };
+    auto sstore = [&]() {
+#pragma unroll
+        for (int v = 0; v < LD; v++) {
+            int idx = tid + v * NT;
+            int r = idx / KT, c = idx % KT;
+            int rr = idx / BM, cc = idx % BM;
+#pragma unroll
+            for (int q = 0; q < P; q++) {
+                As[c][r][q] = ra[v][q];
+                Bs[rr][cc][q] = rb[v][q];
+            }
+        }
+    };
+
+    gload(0);
+    sstore();
+    __syncthreads();
+    for (int64_t k0 = 0; k0 < l; k0 += KT) {
+        const bool more = k0 + KT < l;
+        if (more) gload(k0 + KT);
+#pragma unroll
+        for (int kk = 0; kk < KT; kk++) {
+            double a[RM][P], b[RM][P];
+#pragma unroll
+            for (int r = 0; r < RM; r++)
+#pragma unroll
+                for (int q = 0; q < P; q++) a[r][q] = As[kk][ty + r * TPD][q];
+#pragma unroll
+            for (int c = 0; c < RM; c++)
+#pragma unroll
+                for (int q = 0; q < P; q++) b[c][q] = Bs[kk][tx + c * TPD][q];
+#pragma unroll
+            for (int r = 0; r < RM; r++)
+#pragma unroll
+                for (int c = 0; c < RM; c++) Fmt::mac(acc[r][c], a[r], b[c]);
+            if ((kk + 1) % Fmt::R == 0) {
+#pragma unroll
+                for (int r = 0; r < RM; r++)
+#pragma unroll
+                    for (int c = 0; c < RM; c++) Fmt::renorm(acc[r][c]);
+            }
+        }
+        __syncthreads();
+        if (more) {
+            sstore();
+            __syncthreads();
+        }
+    }
+
+#pragma unroll
+    for (int r = 0; r < RM; r++)
+#pragma unroll
+        for (int c = 0; c < RM; c++) {
+            int64_t i = i0 + ty + r * TPD, j = j0 + tx + c * TPD;
+            double out[P];
+            Fmt::finish(acc[r][c], out);
+            if (i < m && j < n) {
+#pragma unroll
+                for (int q = 0; q < P; q++) *C.at(z, q, i, j) = out[q];
+            }
+        }
+}
+
+template <int W>
+__device__ __forceinline__ void load_mp(MPV<W>& v, const uint32_t* p, int64_t ps) {
+    v.e = (int)p[0];
+    v.f = p[ps];
+#pragma unroll
+    for (int i = 0; i < W; i++) v.m[i] = p[(2 + i) * ps];
+}
+
+template <int W>
+__device__ __forceinline__ void store_mp(const MPV<W>& v, uint32_t* p, int64_t ps) {
+    p[0] = (uint32_t)v.e;
+    p[ps] = v.f;
+#pragma unroll
+    for (int i = 0; i < W; i++) p[(2 + i) * ps] = v.m[i];
+}
+
+template <int W>
+__device__ __forceinline__ void mp_mac(MPV<W>& c, const MPV<W>& a, const MPV<W>& b, unsigned& st) {
+    MPV<W> t;
+    mp_mul<W>(a, b, t, st);
+    MPV<W> s;
+    mp_add<W>(c, t, s, st);
+    c = s;
+}
+
+// One 16 x 16 block of C (one output per thread, 256 threads) with A rows and
+// B columns staged KT elements deep through shared memory `sm`
+// (2 * KT * 16 * (2 + W) words) as [k][row][word]; device-side flags are
+// ORed into `st`.
+template <int W, int KT>
+__device__ __forceinline__ void mp_block_tile(int64_t m, int64_t l, int64_t n, const View<const uint32_t>& A,
+                                              const View<const uint32_t>& B, const View<uint32_t>& C, int64_t z,
+                                              int64_t i0, int64_t j0, uint32_t* sm, unsigned& st) {
+    constexpr int BM = 16;
+    constexpr int E = 2 + W;
+    constexpr int WORDS = BM * KT * E;
+    auto As = reinterpret_cast<uint32_t (*)[BM][E]>(sm);
+    auto Bs = reinterpret_cast<uint32_t (*)[BM][E]>(sm + KT * BM * E);
+    const int tid = threadIdx.x, ty = tid / BM, tx = tid % BM;
+    MPV<W> c;
+    mp_set_zero(c, 0u);
+    for (int64_t k0 = 0; k0 < l; k0 += KT) {
+        for (int idx = tid; idx < WORDS; idx += 256) {
+            int q = idx / (BM * KT), rem = idx % (BM * KT);
+            int r = rem / KT, cc = rem % KT;          // A: row r, k = k0 + cc
+            int64_t i = i0 + r, k = k0 + cc;
+            uint32_t va = (i < m && k < l) ? __ldg(A.at(z, q, i, k)) : (q == 1 ? 2u : 0u);
+            As[cc][r][q] = va;
+            int rb = rem / BM, cb = rem % BM;         // B: k = k0 + rb, column cb
+            int64_t kb = k0 + rb, j = j0 + cb;
+            uint32_t vb = (kb < l && j < n) ? __ldg(B.at(z, q, kb, j)) : (q == 1 ? 2u : 0u);
+            Bs[rb][cb][q] = vb;
+        }
+        __syncthreads();
+        const int kmax = (l - k0) < KT ? (int)(l - k0) : KT;
+        for (int kk = 0; kk < kmax; kk++) {
+            MPV<W> a, b;
+            a.e = (int)As[kk][ty][0];
+            a.f = As[kk][ty][1];
+            b.e = (int)Bs[kk][tx][0];
+            b.f = Bs[kk][tx][1];
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                a.m[w] = As[kk][ty][2 + w];
+                b.m[w] = Bs[kk][tx][2 + w];
+            }
+            mp_mac(c, a, b, st);
+        }
+        __syncthreads();
+    }
+    int64_t i = i0 + ty, j = j0 + tx;
+    if (i < m && j < n) store_mp(c, C.at(z, 0, i, j), C.ps);
+}
+
+}  // namespace mpg
