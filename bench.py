@@ -48,6 +48,15 @@ FP64_OPS_PER_MAC = {"dd": 9.0 + 3.0 / 8.0, "qd": 72.0 + 15.0 / 4.0}
 # FP64 pipe: 2 operations / clock / SM (measured 1.91 DFMA/clk/SM at 2.07 GHz by
 # a dependent-chain-free DFMA loop) x 152 SMs x 2070 MHz maximum SM clock.
 FP64_PEAK_GOPS = 2 * 152 * 2.070
+# Issue rate: 1 warp-instruction / clock per SM sub-partition, 4 per SM.
+ISSUE_PEAK_GWIPS = 4 * 152 * 2.070
+# Multi-limb thread-instructions per multiply-accumulate (ncu
+# smsp__inst_executed x 32 / MACs of the block kernel), by precision.
+MP_INSTR_PER_MAC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from ncu captures of exactly these configurations (profiles/):
+# (fmt, n, algo, n_min, depth) -> bytes.  Absent => null.
+TRAFFIC_BYTES = {("dd", 2048, "strassen", 32, 3): 725.0e6 + 336.1e6}
 
 
 def parse():
@@ -56,7 +65,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpgemm", choices=["mpgemm", "reference"])
-    ap.add_argument("--fmt", default="dd", choices=["dd", "qd"])
+    ap.add_argument("--fmt", default="dd", choices=["dd", "qd", "mp"])
+    ap.add_argument("--prec", type=int, default=256, help="multi-limb precision in bits (--fmt mp)")
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--algo", default="tuned", choices=["tuned", "simple", "block", "strassen"])
     ap.add_argument("--n_min", type=int, default=64)
@@ -67,6 +77,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the split-precision comparison")
     ap.add_argument("--ozaki-n", type=int, default=4096)
     ap.add_argument("--ozaki-slices", type=int, default=16)
+    ap.add_argument("--batched-count", type=int, default=512)
     return ap.parse_args()
 
 
@@ -134,10 +145,87 @@ def split_precision_extra(args, stream):
     return out
 
 
+def batched_extra(args, stream):
+    """512 GEMMs, m, l, n log-uniform in [16, 1024], format uniform over
+    {DD, QD, 256-bit}: one persistent graph-replayed launch with tiles from
+    the FP32 MLP cost model, the same with tiles from exhaustive timing
+    (every DD / QD GEMM timed alone at tile 16 and 32), and one ordinary
+    launch per GEMM.  Effective GFLOP/s = 2 sum(m n l) / t."""
+    import torch
+    from paper_1710_01839_gb300 import batched, costmodel, inputs as I
+    shapes = I.batched_shapes(args.batched_count)
+    probs = []
+    for i, (m, l, n, prec) in enumerate(shapes):
+        s = I.seed_for(4, i)
+        if prec == "dd":
+            A, B, planes, dt = I.dd_random(m, l, s), I.dd_random(l, n, s + 1), 2, torch.float64
+        elif prec == "qd":
+            A, B, planes, dt = I.qd_random(m, l, s), I.qd_random(l, n, s + 1), 4, torch.float64
+        else:
+            A, B, planes, dt = I.mp_random(m, l, 8, s).view(np.int32), I.mp_random(l, n, 8, s + 1).view(np.int32), 10, torch.int32
+        probs.append((prec, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                      torch.empty((planes, m, n), dtype=dt, device="cuda")))
+    flops = 2.0 * sum(m * l * n for m, l, n, _ in shapes)
+    model_src = "none"
+    if os.path.exists(costmodel.DEFAULT_MODEL):
+        costmodel.load(costmodel.DEFAULT_MODEL)
+        model_src = "shipped model file (trained on this pool's GB300 by paper_1710_01839_gb300/train_cost_model.py)"
+    else:
+        F, T = costmodel.collect(2048, seed=1714, max_dim=1024)
+        costmodel.train(F, T, epochs=200)
+        model_src = "trained in this run on 2048 timings"
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    # exhaustive: each DD / QD GEMM alone at both tiles
+    ex_tiles = []
+    for prec, A, B, C in probs:
+        if prec == "mp256":
+            ex_tiles.append(16)
+            continue
+        one = batched.make_descs([(prec, A, B, C)], [16])
+        t16 = timed(lambda: batched.sequential(one), 2)
+        one[0].tile = 32
+        t32 = timed(lambda: batched.sequential(one), 2)
+        ex_tiles.append(16 if t16 < t32 else 32)
+    d_model = batched.make_descs(probs)                 # tile 0: the cost model decides
+    d_exh = batched.make_descs(probs, ex_tiles)
+    p_model, p_exh = batched.Plan(d_model), batched.Plan(d_exh)
+    t_model = timed(p_model.run_graph)
+    t_exh = timed(p_exh.run_graph)
+    t_seq = timed(lambda: batched.sequential(d_exh))
+    model_tiles = p_model.info()["tiles"]
+    p_model.close()
+    p_exh.close()
+    return {"workload": f"{len(shapes)} GEMMs, m,l,n log-uniform [16,1024], formats uniform over DD/QD/MP256",
+            "persistent_graph_mlp_gflops": flops / (t_model * 1e-3) / 1e9, "persistent_graph_mlp_ms": t_model,
+            "persistent_graph_exhaustive_gflops": flops / (t_exh * 1e-3) / 1e9, "persistent_graph_exhaustive_ms": t_exh,
+            "sequential_launches_gflops": flops / (t_seq * 1e-3) / 1e9, "sequential_launches_ms": t_seq,
+            "mlp_regret_vs_exhaustive": t_model / t_exh - 1, "persistent_speedup_vs_sequential": t_seq / t_exh,
+            "tiles_agree_with_exhaustive": float(np.mean([a == b for a, b in zip(model_tiles, ex_tiles)])),
+            "cost_model": model_src}
+
+
 # ---------------------------------------------------------------- helpers
 
-def inputs_for(fmt, n, rank=0):
+def inputs_for(fmt, n, rank=0, prec=256):
     from paper_1710_01839_gb300 import inputs as I
+    if fmt == "mp":
+        w = prec // 32
+        A = I.mp_random(n, n, w, I.seed_for(2, 10 * rank + w))
+        B = I.mp_random(n, n, w, I.seed_for(2, 10 * rank + w + 1))
+        return A, B
     gen = I.dd_random if fmt == "dd" else I.qd_random
     A = gen(n, n, I.seed_for(1, 10 * rank), exp_spread=20)
     B = gen(n, n, I.seed_for(1, 10 * rank + 1), exp_spread=20)
@@ -202,7 +290,11 @@ def cpu_baseline(fmt, A, B, algo, n_min, budget_s):
     same workload: rate = 2 * rows * n * l / t."""
     import oracle
     m, l, n = A.shape[1], A.shape[2], B.shape[2]
-    run = oracle.dd_gemm if fmt == "dd" else oracle.qd_gemm
+    if fmt == "mp":
+        pb = 32 * (A.shape[0] - 2)
+        run = lambda A_, B_, **kw: oracle.mp_gemm(A_, B_, prec_bits=pb, **kw)
+    else:
+        run = oracle.dd_gemm if fmt == "dd" else oracle.qd_gemm
     cores = oracle.threads()
     oalgo = "block" if algo in ("block", "strassen", "tuned") else "simple"
     rows = max(1, cores)
@@ -283,19 +375,23 @@ def main():
 
     fmt, n = args.fmt, args.n
     m = l = n
-    A, B = inputs_for(fmt, n, rank)
+    A, B = inputs_for(fmt, n, rank, args.prec)
     planes = A.shape[0]
-    Ad = torch.from_numpy(A).cuda()
-    Bd = torch.from_numpy(B).cuda()
-    Cd = torch.empty((planes, m, n), dtype=torch.float64, device="cuda")
-    gemm = mpg.gemm_dd if fmt == "dd" else mpg.gemm_qd
+    is_mp = fmt == "mp"
+    Ad = torch.from_numpy(A.view(np.int32) if is_mp else A).cuda()
+    Bd = torch.from_numpy(B.view(np.int32) if is_mp else B).cuda()
+    Cd = torch.empty((planes, m, n), dtype=torch.int32 if is_mp else torch.float64, device="cuda")
+    if is_mp:
+        gemm = lambda A_, B_, C_, **kw: mpg.gemm_mp(A_, B_, args.prec, C_, **kw)
+    else:
+        gemm = mpg.gemm_dd if fmt == "dd" else mpg.gemm_qd
 
     # -------- selection (Section 3): untimed
     t_tune = 0.0
     tune_info = None
     if args.algo == "tuned":
         t0 = time.perf_counter()
-        choice, tune_info = tuner.tune(fmt, Ad, Bd, Cd)
+        choice, tune_info = tuner.tune(fmt, Ad, Bd, Cd, prec_bits=args.prec if is_mp else 0)
         t_tune = time.perf_counter() - t0
         algo, n_min, depth = choice["algo"], choice["n_min"], choice["depth"]
     else:
@@ -351,20 +447,31 @@ def main():
     leaf_count = 7 ** depth if algo == "strassen" else 1
     macs_per_launch = leaf_count * float(leaf) ** 3
     k_avg_ms = kms.value / max(kl.value, 1)
-    achieved = macs_per_launch * FP64_OPS_PER_MAC[fmt] / (k_avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "unit": "Gop/s (FP64 pipe)", "achieved": achieved, "peak": FP64_PEAK_GOPS,
-                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
-                "kernel": f"{fmt} {'leaf ' if algo == 'strassen' else ''}{'simple' if algo == 'simple' else 'block'}"
-                          f" GEMM, {macs_per_launch:.3g} MACs x {FP64_OPS_PER_MAC[fmt]} FP64 ops per launch",
-                "kernel_ms": k_avg_ms, "kernel_share_of_step": kms.value / tot_ms if tot_ms else None,
-                "peak_note": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"}
+    kname = (f"{fmt} {'leaf ' if algo == 'strassen' else ''}{'simple' if algo == 'simple' else 'block'} GEMM")
+    if is_mp:
+        # integer pipe: issue-bound; instructions per MAC come from ncu (see profiles/)
+        ipm = MP_INSTR_PER_MAC.get(args.prec)
+        achieved = macs_per_launch * ipm / 32.0 / (k_avg_ms * 1e-3) / 1e9 if ipm else None
+        roofline = {"bound": "alu", "unit": "G warp-instructions/s (issue)", "achieved": achieved,
+                    "peak": ISSUE_PEAK_GWIPS, "frac": achieved / ISSUE_PEAK_GWIPS if achieved else None,
+                    "traffic": None, "kernel": f"{kname}, {macs_per_launch:.3g} MACs x {ipm} thread-instructions",
+                    "kernel_ms": k_avg_ms, "kernel_share_of_step": kms.value / tot_ms if tot_ms else None,
+                    "peak_note": "derived: 1 warp-instruction/clk per SM sub-partition x 4 x 152 SMs x 2070 MHz"}
+    else:
+        achieved = macs_per_launch * FP64_OPS_PER_MAC[fmt] / (k_avg_ms * 1e-3) / 1e9
+        traffic = TRAFFIC_BYTES.get((fmt, n, algo, n_min, depth))
+        roofline = {"bound": "alu", "unit": "Gop/s (FP64 pipe)", "achieved": achieved, "peak": FP64_PEAK_GOPS,
+                    "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic,
+                    "kernel": f"{kname}, {macs_per_launch:.3g} MACs x {FP64_OPS_PER_MAC[fmt]} FP64 ops per launch",
+                    "kernel_ms": k_avg_ms, "kernel_share_of_step": kms.value / tot_ms if tot_ms else None,
+                    "peak_note": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"}
 
     # -------- end to end through host buffers
     e2e = None
     if not args.no_e2e:
-        Ah = torch.from_numpy(A).pin_memory()
-        Bh = torch.from_numpy(B).pin_memory()
-        Ch = torch.empty((planes, m, n), dtype=torch.float64).pin_memory()
+        Ah = torch.from_numpy(A.view(np.int32) if is_mp else A).pin_memory()
+        Bh = torch.from_numpy(B.view(np.int32) if is_mp else B).pin_memory()
+        Ch = torch.empty((planes, m, n), dtype=Cd.dtype).pin_memory()
         for _ in range(2):
             Ad.copy_(Ah, non_blocking=True)
             Bd.copy_(Bh, non_blocking=True)
@@ -387,12 +494,13 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e_ms = float(t.item())
         e2e = {"value": world * flops_step * args.steps / (e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
-               "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(planes * m * n * 8),
+               "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(Ch.numel() * Ch.element_size()),
                "ms_per_step": e_ms / args.steps}
 
-    extras = None
+    extras = bextra = None
     if not args.no_extras and fmt == "dd":
         extras = split_precision_extra(args, stream)
+        bextra = batched_extra(args, stream)
 
     if dist:
         dist.barrier()
@@ -418,6 +526,8 @@ def main():
         line["tuning"] = tune_info
     if extras is not None:
         line["split_precision"] = extras
+    if bextra is not None:
+        line["batched"] = bextra
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

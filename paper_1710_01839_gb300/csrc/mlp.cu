@@ -32,8 +32,10 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NF * NH, OFF_W2 = OFF_B1 + NH, OFF_B
               OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH, NPARAM = OFF_B3 + 1;
 
 // Features of one configuration (all inputs of the model, before
-// normalisation).  The GPU-specific ones (CTAs, rounds over 152 SMs) let the
-// model see wave quantisation directly.
+// normalisation): log2 m, l, n and mnl; format one-hot; log2 significand
+// bits; log2 tile; algorithm one-hot; Strassen depth; log2 CTAs; log2 rounds
+// of CTAs over the SMs; log2 kernel launches.  The GPU-specific ones let the
+// model see wave quantisation and per-launch overhead directly.
 void encode_features(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo, int tile, int depth,
                      int sms, float* f) {
     const double lm = std::log2((double)std::max<int64_t>(m, 1)), ll = std::log2((double)std::max<int64_t>(l, 1)),
@@ -50,7 +52,7 @@ void encode_features(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, i
                    (float)std::log2((double)std::max(tile, 1)), algo == MPGEMM_SIMPLE ? 1.f : 0.f,
                    algo == MPGEMM_BLOCK ? 1.f : 0.f, algo == MPGEMM_STRASSEN ? 1.f : 0.f, (float)depth,
                    (float)std::log2((double)std::max<int64_t>(ctas, 1)), (float)std::log2(std::max(rounds, 1.0)),
-                   (float)(ll - depth)};
+                   (float)std::log2(algo == MPGEMM_STRASSEN ? 3.0 * depth + 1.0 : 1.0)};   // kernel launches
     std::memcpy(f, v, sizeof v);
 }
 
