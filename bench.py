@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--ozaki-n", type=int, default=4096)
     ap.add_argument("--ozaki-slices", type=int, default=16)
     ap.add_argument("--batched-count", type=int, default=512)
+    ap.add_argument("--ozaki-fp8-slices", type=int, default=22)
     return ap.parse_args()
 
 
@@ -85,6 +86,8 @@ def parse():
 # independent register-operand mma.sync instructions on all SMs (no tcgen05
 # integer MMA exists on sm_103a).
 INT8_MMA_PEAK_TOPS = 151.2
+# mma.sync m16n8k32 e4m3 -> f32 throughput measured the same way.
+E4M3_MMA_PEAK_TFLOPS = 2192.0
 
 
 def split_precision_extra(args, stream):
@@ -142,6 +145,25 @@ def split_precision_extra(args, stream):
         out[name + "_gflops"] = flops / (ms * 1e-3) / 1e9
         out[name + "_ms"] = ms
     out["speedup_vs_best_plain_dd"] = min(out["plain_dd_block_ms"], out["plain_dd_strassen3_ms"]) / oz_ms
+    # FP8 digits: balanced base-32, e4m3 mma.sync with exact f32 accumulation
+    S8 = args.ozaki_fp8_slices
+
+    def oz8():
+        rc = L.mpgemm_dd_ozaki_ex(n, n, n, p(Ad), p(Bd), p(Cd), S8, 1, sp)
+        if rc:
+            raise RuntimeError(mpg.strerror(rc))
+
+    f8_ms, f8_kms = timed(oz8, 3)
+    pairs8 = S8 * (S8 + 1) // 2
+    f8_flops = 2.0 * n * n * lp * pairs8
+    out["fp8"] = {"slices": S8, "gflops": flops / (f8_ms * 1e-3) / 1e9, "ms": f8_ms,
+                  "speedup_vs_int8": oz_ms / f8_ms,
+                  "speedup_vs_best_plain_dd": min(out["plain_dd_block_ms"], out["plain_dd_strassen3_ms"]) / f8_ms,
+                  "roofline": {"bound": "tensor", "unit": "TFLOP/s (e4m3 mma.sync)",
+                               "achieved": f8_flops / (f8_kms * 1e-3) / 1e12, "peak": E4M3_MMA_PEAK_TFLOPS,
+                               "frac": f8_flops / (f8_kms * 1e-3) / 1e12 / E4M3_MMA_PEAK_TFLOPS,
+                               "kernel": f"k_ozaki_levels<fp8>, {pairs8} slice pairs x 2 n^2 l",
+                               "kernel_ms": f8_kms, "kernel_share": f8_kms / f8_ms}}
     return out
 
 
@@ -218,6 +240,22 @@ def batched_extra(args, stream):
 
 
 # ---------------------------------------------------------------- helpers
+
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (replicas: every rank times its own GEMMs)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, flops_per_step, steps, t_max_ms):
+    """Whole-job effective GFLOP/s: all ranks' nominal 2mnl work over the
+    slowest rank's time."""
+    return world * flops_per_step * steps / (t_max_ms * 1e-3) / 1e9
+
 
 def inputs_for(fmt, n, rank=0, prec=256):
     from paper_1710_01839_gb300 import inputs as I
@@ -391,7 +429,8 @@ def main():
     tune_info = None
     if args.algo == "tuned":
         t0 = time.perf_counter()
-        choice, tune_info = tuner.tune(fmt, Ad, Bd, Cd, prec_bits=args.prec if is_mp else 0)
+        choice, tune_info = tuner.tune(fmt, Ad, Bd, Cd, flags=tuner.REMEMBER | tuner.VERIFY,
+                                       prec_bits=args.prec if is_mp else 0)
         t_tune = time.perf_counter() - t0
         algo, n_min, depth = choice["algo"], choice["n_min"], choice["depth"]
     else:
@@ -434,13 +473,9 @@ def main():
     status = mpg.stream_status()
     if status != 0:
         raise RuntimeError(f"device status {status}: {mpg.strerror(status)}")
-    t_max = tot_ms
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(tot_ms, dist, "cuda")
     flops_step = 2.0 * m * n * l
-    value = world * flops_step * args.steps / (t_max * 1e-3) / 1e9
+    value = whole_job_rate(world, flops_step, args.steps, t_max)
 
     # -------- dominant kernel roofline (FP64 pipe)
     leaf = n >> depth if algo == "strassen" else n
@@ -489,11 +524,8 @@ def main():
             ev2[i][1].record(stream)
         torch.cuda.synchronize()
         e_ms = sum(a.elapsed_time(b) for a, b in ev2)
-        if dist:
-            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * flops_step * args.steps / (e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+        e_ms = max_over_ranks(e_ms, dist, "cuda")
+        e2e = {"value": whole_job_rate(world, flops_step, args.steps, e_ms), "unit": "GFLOP/s",
                "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(Ch.numel() * Ch.element_size()),
                "ms_per_step": e_ms / args.steps}
 

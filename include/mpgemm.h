@@ -116,6 +116,26 @@ int mpgemm_ozaki_split(int by_col, int64_t rows, int64_t cols, const double* X, 
    planes laid out as mpgemm_ozaki_split writes them. */
 int mpgemm_ozaki_levels(int64_t m, int64_t l, int64_t n, int num_slices, const signed char* DA,
                         const signed char* DB, int* levels, void* stream);
+/* The same scheme with a choice of digits (digit_kind):
+ *   MPGEMM_DIGITS_INT8 (0): base-128 digits in [-127, 127] as int8, products
+ *     on mma.sync s8 (what mpgemm_dd_ozaki does; S <= 18, default 16);
+ *   MPGEMM_DIGITS_E4M3 (1): each element scaled by 2^-(e_i+1) (one bit of
+ *     headroom) is truncated toward zero to 5 S bits and written in balanced
+ *     base-32 digits (every digit in [-16, 16], exact in FP8 e4m3), stored as
+ *     e4m3 codes; products on mma.sync e4m3 with f32 accumulation, exact
+ *     because every partial sum of one slice pair is an integer below 256 l
+ *     <= 2^24 (l <= 65536), moved to int32 after each pair; S <= 24, default
+ *     22 (<= 2^-100 |A||B| on the same inputs as 16 int8 slices).
+ * c_ij = RN_DD(2^(e_i + f_j + 2 h) sum_g L_g 2^(-b g)), b = 7, h = 0 (int8)
+ * or b = 5, h = 1 (e4m3).  mpgemm_ozaki_split_ex writes 1-byte digits (int8
+ * or e4m3 codes) in the layout described for mpgemm_ozaki_split. */
+enum { MPGEMM_DIGITS_INT8 = 0, MPGEMM_DIGITS_E4M3 = 1 };
+int mpgemm_dd_ozaki_ex(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C,
+                       int num_slices, int digit_kind, void* stream);
+int mpgemm_ozaki_split_ex(int digit_kind, int by_col, int64_t rows, int64_t cols, const double* X, int num_slices,
+                          int* expo, void* digits, void* stream);
+int mpgemm_ozaki_levels_ex(int digit_kind, int64_t m, int64_t l, int64_t n, int num_slices, const void* DA,
+                           const void* DB, int* levels, void* stream);
 
 /* ---------------------------------------------------------------------------
  * DD Strassen that allocates nothing.  The paper has no counterpart.  It is

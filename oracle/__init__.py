@@ -85,6 +85,10 @@ def _declare(L):
     L.or_ozaki_recombine.argtypes = [_I64, _I64, _I, _P, _P, _P, _P]
     L.or_ozaki_gemm.argtypes = [_I64, _I64, _I64, _P, _P, _P, _I]
     L.or_ozaki_gemm.restype = _I
+    L.or_ozaki_slice_b32.argtypes = [_I, _I64, _I64, _P, _P, _I, _P]
+    L.or_ozaki_recombine_bits.argtypes = [_I64, _I64, _I, _I, _I, _P, _P, _P, _P]
+    L.or_ozaki_gemm_b32.argtypes = [_I64, _I64, _I64, _P, _P, _P, _I]
+    L.or_ozaki_gemm_b32.restype = _I
 
 
 def _ptr(a: np.ndarray):
@@ -278,4 +282,31 @@ def ozaki_gemm(A, B, S):
     m, l, n = A.shape[1], A.shape[2], B.shape[2]
     C = np.zeros((2, m, n))
     lib().or_ozaki_gemm(m, l, n, _ptr(A), _ptr(B), _ptr(C), S)
+    return C
+
+
+def ozaki_slice_b32(X, expo, S, by_col):
+    """Balanced base-32 digits (|d| <= 16, FP8 e4m3-exact), S planes."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    expo = np.ascontiguousarray(expo, dtype=np.int32)
+    D = np.zeros((S, X.shape[1], X.shape[2]), dtype=np.int8)
+    lib().or_ozaki_slice_b32(1 if by_col else 0, X.shape[1], X.shape[2], _ptr(X), _ptr(expo), S, _ptr(D))
+    return D
+
+
+def ozaki_recombine_bits(L, e, f, S, bits, head):
+    m, n = L.shape[1], L.shape[2]
+    C = np.zeros((2, m, n))
+    lib().or_ozaki_recombine_bits(m, n, S, bits, head, _ptr(np.ascontiguousarray(L)),
+                                  _ptr(np.ascontiguousarray(e, dtype=np.int32)),
+                                  _ptr(np.ascontiguousarray(f, dtype=np.int32)), _ptr(C))
+    return C
+
+
+def ozaki_gemm_b32(A, B, S):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    m, l, n = A.shape[1], A.shape[2], B.shape[2]
+    C = np.zeros((2, m, n))
+    lib().or_ozaki_gemm_b32(m, l, n, _ptr(A), _ptr(B), _ptr(C), S)
     return C

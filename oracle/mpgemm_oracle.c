@@ -981,6 +981,85 @@ OR_API void or_ozaki_recombine(int64_t m, int64_t n, int S, const int64_t *L, co
         }
 }
 
+/* Balanced base-32 digits (the FP8 variant of step 2): with one bit of
+   headroom, x = a 2^-(e+1) (|x| < 1/2) is truncated toward zero to 5S bits
+   by S base-32 truncation steps (d_s = trunc(32 x), x = 32 x - d_s, all
+   exact), then the digits of |x| are balanced from the least significant
+   up: a digit >= 16 becomes digit - 32 and carries 1 into the next more
+   significant digit; the most significant digit keeps its carry (it stays
+   <= 16 because |x| < 1/2).  Every digit lies in [-16, 16] (exact in FP8
+   e4m3) and sum_s d_s 32^(S-s) = trunc(x 2^(5S)). */
+static void ozaki_digits_b32(double hi, double lo, int e, int S, int8_t *d, int64_t stride) {
+    double xh = ldexp(hi, -(e + 1)), xl = ldexp(lo, -(e + 1));
+    int mag[64];
+    int neg = (xh < 0) || (xh == 0 && xl < 0);
+    if (S > 64) die("too many slices");
+    for (int s = 0; s < S; s++) {
+        double yh = ldexp(xh, 5), yl = ldexp(xl, 5);
+        double t = dd_trunc(yh, yl);
+        mag[s] = (int)fabs(t);
+        if (mag[s] > 31) die("base-32 digit out of range");
+        two_sum(yh - t, yl, &xh, &xl);
+    }
+    for (int s = S - 1; s >= 1; s--) {
+        if (mag[s] >= 16) {
+            mag[s] -= 32;
+            mag[s - 1] += 1;
+        }
+    }
+    if (mag[0] > 16) die("balanced top digit out of range");
+    for (int s = 0; s < S; s++) d[(int64_t)s * stride] = (int8_t)(neg ? -mag[s] : mag[s]);
+}
+
+OR_API void or_ozaki_slice_b32(int by_col, int64_t rows, int64_t cols, const double *X, const int32_t *expo, int S,
+                               int8_t *D) {
+    size_t N = (size_t)(rows * cols);
+    for (int64_t i = 0; i < rows; i++)
+        for (int64_t j = 0; j < cols; j++) {
+            size_t e = (size_t)(i * cols + j);
+            ozaki_digits_b32(X[e], X[N + e], by_col ? expo[j] : expo[i], S, D + e, (int64_t)N);
+        }
+}
+
+/* Step 4 for digits of `bits` bits with `head` bits of headroom per side:
+   c_ij = RN_DD(2^(e_i + f_j + 2 head) sum_g L_g 2^(-bits g)). */
+OR_API void or_ozaki_recombine_bits(int64_t m, int64_t n, int S, int bits, int head, const int64_t *L,
+                                    const int32_t *e, const int32_t *f, double *C) {
+    size_t NC = (size_t)(m * n);
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t j = 0; j < n; j++) {
+            wfx_t W;
+            double r[2];
+            wfx_zero(&W);
+            for (int g = 2; g <= S + 1; g++) {
+                int64_t v = L[(size_t)g * NC + (size_t)(i * n + j)];
+                if (v > (1LL << 53) || v < -(1LL << 53)) die("level sum beyond 2^53");
+                wfx_add_double(&W, ldexp((double)v, e[i] + f[j] + 2 * head - bits * g));
+            }
+            wfx_round_terms(&W, r, 2);
+            C[i * n + j] = r[0];
+            C[NC + (size_t)(i * n + j)] = r[1];
+        }
+}
+
+/* The FP8-digit pipeline (steps 1, 2 with balanced base-32 digits, 3, 4). */
+OR_API int or_ozaki_gemm_b32(int64_t m, int64_t l, int64_t n, const double *A, const double *B, double *C, int S) {
+    int32_t *e = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int32_t *f = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int8_t *DA = (int8_t *)malloc((size_t)(m * l * S) + 1);
+    int8_t *DB = (int8_t *)malloc((size_t)(l * n * S) + 1);
+    int64_t *L = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m * n) * (size_t)(2 * S + 1) + 8);
+    if (!e || !f || !DA || !DB || !L) die("out of host memory");
+    or_ozaki_row_expo(m, l, A, e);
+    or_ozaki_col_expo(l, n, B, f);
+    or_ozaki_slice_b32(0, m, l, A, e, S, DA);
+    or_ozaki_slice_b32(1, l, n, B, f, S, DB);
+    or_ozaki_levels(m, l, n, S, DA, DB, L);
+    or_ozaki_recombine_bits(m, n, S, 5, 1, L, e, f, C);
+    free(e); free(f); free(DA); free(DB); free(L);
+    return 0;
+}
+
 /* The whole split-precision pipeline (steps 1-4) for small sizes. */
 OR_API int or_ozaki_gemm(int64_t m, int64_t l, int64_t n, const double *A, const double *B, double *C, int S) {
     int32_t *e = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));

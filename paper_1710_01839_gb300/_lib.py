@@ -55,6 +55,9 @@ SIGNATURES = {
     "mpgemm_batched_sequential": (_I, [_P, _I, _P]),
     "mpgemm_dd_strassen_noalloc": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _I, _P]),
     "mpgemm_dd_ozaki": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _P]),
+    "mpgemm_dd_ozaki_ex": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _I, _P]),
+    "mpgemm_ozaki_split_ex": (_I, [_I, _I, _I64, _I64, _P, _I, _P, _P, _P]),
+    "mpgemm_ozaki_levels_ex": (_I, [_I, _I64, _I64, _I64, _I, _P, _P, _P, _P]),
     "mpgemm_ozaki_workspace_size": (_SZ, [_I64, _I64, _I64, _I]),
     "mpgemm_ozaki_slices_default": (_I, []),
     "mpgemm_ozaki_split": (_I, [_I, _I64, _I64, _P, _I, _P, _P, _P]),

@@ -130,6 +130,80 @@ __device__ __forceinline__ void dd_digits(double hi, double lo, int e, int S, si
     }
 }
 
+// FP8 e4m3 code of a small integer |v| <= 16 (exact: at most 4 significant bits).
+__device__ __forceinline__ unsigned char e4m3_of_int(int v) {
+    unsigned s = v < 0 ? 0x80u : 0u;
+    int a = v < 0 ? -v : v;
+    if (a == 0) return (unsigned char)s;
+    int e = 31 - __clz(a);                             // floor(log2 a), 0..4
+    unsigned mant = (unsigned)((a << 3) >> e) & 7u;    // (a / 2^e - 1) * 8
+    return (unsigned char)(s | ((unsigned)(e + 7) << 3) | mant);
+}
+
+// Balanced base-32 digits (FP8 variant): T = trunc((hi + lo) 2^(5S - e - 1))
+// (one bit of headroom, |T| < 2^(5S-1)), written from the least significant
+// digit up with digits >= 16 replaced by digit - 32 and a carry into the next
+// one; the top digit keeps its carry (<= 16).  Stored as e4m3 codes.
+__device__ __forceinline__ void dd_digits_b32(double hi, double lo, int e, int S, unsigned char* d, int64_t stride) {
+    const int sc = 5 * S - e - 1;
+    double H = ldexp(hi, sc), L = ldexp(lo, sc);
+    double tH = trunc(H);
+    double corr = 0.0;
+    if (tH == H) {
+        if (H > 0.0 && L < 0.0) corr = floor(L);
+        else if (H < 0.0 && L > 0.0) corr = ceil(L);
+        else corr = trunc(L);
+    }
+    unsigned long long th, tl, ch, cl;
+    dbl_int_to_u128(tH, th, tl);
+    dbl_int_to_u128(corr, ch, cl);
+    bool neg;
+    add_s128(th, tl, tH < 0.0, ch, cl, corr < 0.0, neg);
+    int carry = 0;
+    for (int s = S - 1; s >= 0; s--) {
+        int sh = 5 * (S - 1 - s);
+        unsigned long long v = sh >= 64 ? (th >> (sh - 64)) : (sh == 0 ? tl : ((tl >> sh) | (th << (64 - sh))));
+        int dig = (int)(v & 31ull) + carry;
+        carry = 0;
+        if (s > 0 && dig >= 16) {
+            dig -= 32;
+            carry = 1;
+        }
+        d[(int64_t)s * stride] = e4m3_of_int(neg ? -dig : dig);
+    }
+}
+
+// A (m x l, row scale e): digits into S planes of m x lp (K contiguous, zero padded).
+__global__ void k_slice_rows_f8(int64_t m, int64_t l, int64_t lp, const double* A, const int* e, int S,
+                                unsigned char* D) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = blockIdx.y;
+    if (k >= lp || i >= m) return;
+    unsigned char* out = D + i * lp + k;
+    const int64_t plane = m * lp;
+    if (k >= l) {
+        for (int s = 0; s < S; s++) out[s * plane] = 0;
+        return;
+    }
+    const int64_t idx = i * l + k;
+    dd_digits_b32(A[idx], A[m * l + idx], e[i], S, out, plane);
+}
+
+__global__ void k_slice_cols_f8(int64_t l, int64_t n, int64_t lp, const double* B, const int* f, int S,
+                                unsigned char* D) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t j = blockIdx.y;
+    if (k >= lp || j >= n) return;
+    unsigned char* out = D + j * lp + k;
+    const int64_t plane = n * lp;
+    if (k >= l) {
+        for (int s = 0; s < S; s++) out[s * plane] = 0;
+        return;
+    }
+    const int64_t idx = k * n + j;
+    dd_digits_b32(B[idx], B[l * n + idx], f[j], S, out, plane);
+}
+
 // A (m x l, row scale e): digits into S planes of m x lp (K contiguous, zero padded).
 __global__ void k_slice_rows(int64_t m, int64_t l, int64_t lp, const double* A, const int* e, int S, signed char* D) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,6 +258,15 @@ __device__ __forceinline__ void mma_s8(int (&c)[4], const unsigned (&a)[4], unsi
         : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
+// FP8 e4m3 x e4m3 -> f32: exact on the digit products (integers <= 256) as
+// long as every partial sum stays below 2^24 in magnitude.
+__device__ __forceinline__ void mma_e4m3(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 
 constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64, OZ_STAGES = 4, OZ_THREADS = 256;
 constexpr int OZ_STAGE_BYTES = (OZ_BM + OZ_BN) * OZ_BK;   // 16 KB
@@ -196,8 +279,12 @@ __device__ __forceinline__ int swz(int r, int c) { return r * OZ_BK + ((c ^ ((r 
 // One CTA = one 128 x 128 tile of one level g; levels are issued heaviest
 // first (level g concatenates g - 1 slice pairs along K).  8 warps as 2 x 4,
 // warp tile 64 x 32 = 4 x 4 mma tiles; 4-stage cp.async pipeline.
+// F8 = false: int8 digits, s32 accumulators.  F8 = true: e4m3 digit codes,
+// f32 accumulators emptied into s32 after every slice pair (a pair's sum is
+// at most 256 l < 2^24, so every f32 partial sum is an exact integer).
+template <bool F8>
 __global__ void __launch_bounds__(OZ_THREADS) k_ozaki_levels(int64_t m, int64_t n, int64_t lp, int S,
-                                                             const signed char* DA, const signed char* DB,
+                                                             const unsigned char* DA, const unsigned char* DB,
                                                              int* Lv, unsigned tiles_m, unsigned tiles_n) {
     extern __shared__ __align__(128) unsigned char smem[];
     const unsigned tiles = tiles_m * tiles_n;
@@ -214,8 +301,8 @@ __global__ void __launch_bounds__(OZ_THREADS) k_ozaki_levels(int64_t m, int64_t 
     auto load = [&](int it, int stage) {
         int s = it / ksteps + 1;
         int64_t kb = (int64_t)(it % ksteps) * OZ_BK;
-        const signed char* Ab = DA + (int64_t)(s - 1) * planeA + kb;
-        const signed char* Bb = DB + (int64_t)(g - s - 1) * planeB + kb;
+        const unsigned char* Ab = DA + (int64_t)(s - 1) * planeA + kb;
+        const unsigned char* Bb = DB + (int64_t)(g - s - 1) * planeB + kb;
         unsigned char* sA = smem + stage * OZ_STAGE_BYTES;
         unsigned char* sB = sA + OZ_BM * OZ_BK;
 #pragma unroll
@@ -230,12 +317,21 @@ __global__ void __launch_bounds__(OZ_THREADS) k_ozaki_levels(int64_t m, int64_t 
     };
 
     int acc[4][4][4];
+    float facc[F8 ? 4 : 1][F8 ? 4 : 1][4];
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
         for (int b = 0; b < 4; b++)
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[a][b][c] = 0;
+    if constexpr (F8) {
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) facc[a][b][c] = 0.f;
+    }
 
 #pragma unroll
     for (int st = 0; st < OZ_STAGES - 1; st++) {
@@ -267,8 +363,25 @@ __global__ void __launch_bounds__(OZ_THREADS) k_ozaki_levels(int64_t m, int64_t 
 #pragma unroll
             for (int mi = 0; mi < 4; mi++)
 #pragma unroll
-                for (int ni = 0; ni < 4; ni++)
-                    mma_s8(acc[mi][ni], a[mi], b[ni >> 1][(ni & 1) * 2], b[ni >> 1][(ni & 1) * 2 + 1]);
+                for (int ni = 0; ni < 4; ni++) {
+                    if constexpr (F8)
+                        mma_e4m3(facc[mi][ni], a[mi], b[ni >> 1][(ni & 1) * 2], b[ni >> 1][(ni & 1) * 2 + 1]);
+                    else
+                        mma_s8(acc[mi][ni], a[mi], b[ni >> 1][(ni & 1) * 2], b[ni >> 1][(ni & 1) * 2 + 1]);
+                }
+        }
+        if constexpr (F8) {
+            if (it % ksteps == ksteps - 1) {   // end of a slice pair: move the exact f32 sums to s32
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+#pragma unroll
+                    for (int b = 0; b < 4; b++)
+#pragma unroll
+                        for (int c = 0; c < 4; c++) {
+                            acc[a][b][c] += __float2int_rn(facc[a][b][c]);
+                            facc[a][b][c] = 0.f;
+                        }
+            }
         }
     }
     cp_async_wait<0>();
@@ -373,16 +486,19 @@ __device__ __forceinline__ void neg192(unsigned long long (&v)[3]) {
     }
 }
 
-__global__ void k_recombine(int64_t m, int64_t n, int S, const int* Lv, const int* e, const int* f, double* C) {
+// bits = digit width (7 for int8, 5 for e4m3), head = headroom bits per side
+// (0 for int8, 1 for e4m3): x = 2^(e_i + f_j + 2 head) sum_g L_g 2^(-bits g).
+__global__ void k_recombine(int64_t m, int64_t n, int S, int bits, int head, const int* Lv, const int* e,
+                            const int* f, double* C) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = blockIdx.y;
     if (j >= n) return;
     const int64_t mn = m * n, idx = i * n + j;
     unsigned long long v[3] = {0ull, 0ull, 0ull};
-    for (int g = 2; g <= S + 1; g++) add_shifted(v, (long long)Lv[(int64_t)(g - 2) * mn + idx], 7 * (S + 1 - g));
+    for (int g = 2; g <= S + 1; g++) add_shifted(v, (long long)Lv[(int64_t)(g - 2) * mn + idx], bits * (S + 1 - g));
     bool neg = (long long)v[2] < 0;
     if (neg) neg192(v);
-    const int E = e[i] + f[j] - 7 * (S + 1);
+    const int E = e[i] + f[j] + 2 * head - bits * (S + 1);
     int p1;
     unsigned long long M1 = rn53(v, p1);
     double hi = ldexp((double)M1, p1 + E);
@@ -429,46 +545,62 @@ size_t ozaki_workspace_bytes(int64_t m, int64_t l, int64_t n, int S) {
            a256((size_t)S * (size_t)(n * lp)) + a256(sizeof(int) * (size_t)S * (size_t)(m * n));
 }
 
-int ozaki_split(int by_col, int64_t rows, int64_t cols, const double* X, int S, int* expo, signed char* D,
+// Digit kinds: 0 = int8 base-128 digits (7 bits, no headroom, S <= 18),
+//              1 = FP8 e4m3 balanced base-32 digits (5 bits, 1 bit headroom, S <= 24).
+static int digit_bits(int kind) { return kind == 1 ? 5 : 7; }
+static int digit_head(int kind) { return kind == 1 ? 1 : 0; }
+static int max_slices(int kind) { return kind == 1 ? 24 : 18; }
+
+int ozaki_split(int kind, int by_col, int64_t rows, int64_t cols, const double* X, int S, int* expo, void* D,
                 int64_t lp, cudaStream_t s) {
     if (!by_col) {
         k_row_expo<<<ceil_div(rows, 8), 256, 0, s>>>(rows, cols, X, expo);
         if (int rc = check_launch()) return rc;
         dim3 g(ceil_div(lp, 128), (unsigned)rows);
-        k_slice_rows<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, D);
+        if (kind == 1) k_slice_rows_f8<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (unsigned char*)D);
+        else k_slice_rows<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (signed char*)D);
     } else {
         k_col_expo<<<ceil_div(cols, 128), 128, 0, s>>>(rows, cols, X, expo);
         if (int rc = check_launch()) return rc;
         dim3 g(ceil_div(lp, 128), (unsigned)cols);
-        k_slice_cols<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, D);
+        if (kind == 1) k_slice_cols_f8<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (unsigned char*)D);
+        else k_slice_cols<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (signed char*)D);
     }
     return check_launch();
 }
 
-int ozaki_levels(int64_t m, int64_t n, int64_t lp, int S, const signed char* DA, const signed char* DB, int* Lv,
-                 cudaStream_t s) {
+template <bool F8>
+static int levels_launch(int64_t m, int64_t n, int64_t lp, int S, const void* DA, const void* DB, int* Lv,
+                         cudaStream_t s) {
     static bool attr_set[64];
     int dev = 0;
     MPG_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return MPGEMM_EUNSUPPORTED;
     if (!attr_set[dev]) {
-        MPG_CUDA(cudaFuncSetAttribute(k_ozaki_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+        MPG_CUDA(cudaFuncSetAttribute(k_ozaki_levels<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
         attr_set[dev] = true;
     }
     unsigned tm = ceil_div(m, OZ_BM), tn = ceil_div(n, OZ_BN);
     ProfScope ps(s);
-    k_ozaki_levels<<<tm * tn * (unsigned)S, OZ_THREADS, OZ_SMEM, s>>>(m, n, lp, S, DA, DB, Lv, tm, tn);
+    k_ozaki_levels<F8><<<tm * tn * (unsigned)S, OZ_THREADS, OZ_SMEM, s>>>(
+        m, n, lp, S, (const unsigned char*)DA, (const unsigned char*)DB, Lv, tm, tn);
     return check_launch();
 }
 
-int ozaki_recombine(int64_t m, int64_t n, int S, const int* Lv, const int* e, const int* f, double* C, cudaStream_t s) {
+int ozaki_levels(int kind, int64_t m, int64_t n, int64_t lp, int S, const void* DA, const void* DB, int* Lv,
+                 cudaStream_t s) {
+    return kind == 1 ? levels_launch<true>(m, n, lp, S, DA, DB, Lv, s) : levels_launch<false>(m, n, lp, S, DA, DB, Lv, s);
+}
+
+int ozaki_recombine(int kind, int64_t m, int64_t n, int S, const int* Lv, const int* e, const int* f, double* C,
+                    cudaStream_t s) {
     dim3 g(ceil_div(n, 128), (unsigned)m);
-    k_recombine<<<g, 128, 0, s>>>(m, n, S, Lv, e, f, C);
+    k_recombine<<<g, 128, 0, s>>>(m, n, S, digit_bits(kind), digit_head(kind), Lv, e, f, C);
     return check_launch();
 }
 
-int ozaki_gemm_ws(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int S, void* ws,
-                  size_t ws_bytes, cudaStream_t s) {
+int ozaki_gemm_ws(int kind, int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int S,
+                  void* ws, size_t ws_bytes, cudaStream_t s) {
     const int64_t lp = ozaki_padded_k(l);
     if (ws_bytes < ozaki_workspace_bytes(m, l, n, S)) return MPGEMM_ENOMEM;
     char* p = (char*)ws;
@@ -476,16 +608,16 @@ int ozaki_gemm_ws(int64_t m, int64_t l, int64_t n, const double* A, const double
     p += a256(sizeof(int) * (size_t)m);
     int* f = (int*)p;
     p += a256(sizeof(int) * (size_t)n);
-    signed char* DA = (signed char*)p;
+    void* DA = p;
     p += a256((size_t)S * (size_t)(m * lp));
-    signed char* DB = (signed char*)p;
+    void* DB = p;
     p += a256((size_t)S * (size_t)(n * lp));
     int* Lv = (int*)p;
     int rc;
-    if ((rc = ozaki_split(0, m, l, A, S, e, DA, lp, s))) return rc;
-    if ((rc = ozaki_split(1, l, n, B, S, f, DB, lp, s))) return rc;
-    if ((rc = ozaki_levels(m, n, lp, S, DA, DB, Lv, s))) return rc;
-    return ozaki_recombine(m, n, S, Lv, e, f, C, s);
+    if ((rc = ozaki_split(kind, 0, m, l, A, S, e, DA, lp, s))) return rc;
+    if ((rc = ozaki_split(kind, 1, l, n, B, S, f, DB, lp, s))) return rc;
+    if ((rc = ozaki_levels(kind, m, n, lp, S, DA, DB, Lv, s))) return rc;
+    return ozaki_recombine(kind, m, n, S, Lv, e, f, C, s);
 }
 
 }  // namespace mpg
@@ -498,17 +630,23 @@ int mpgemm_ozaki_slices_default(void) { return 16; }
 
 size_t mpgemm_ozaki_workspace_size(int64_t m, int64_t l, int64_t n, int num_slices) {
     if (m <= 0 || l <= 0 || n <= 0) return 0;
-    int S = num_slices <= 0 ? 16 : num_slices;
+    int S = num_slices <= 0 ? 24 : num_slices;   // covers either digit kind's default
     return ozaki_workspace_bytes(m, l, n, S);
 }
 
-int mpgemm_dd_ozaki(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int num_slices,
-                    void* stream) {
-    int S = num_slices <= 0 ? 16 : num_slices;
-    if (m < 0 || l < 0 || n < 0 || S < 1 || S > 18) return MPGEMM_EINVAL;
+int mpgemm_dd_ozaki_ex(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int num_slices,
+                       int digit_kind, void* stream) {
+    if (digit_kind != 0 && digit_kind != 1) return MPGEMM_EINVAL;
+    int S = num_slices <= 0 ? (digit_kind == 1 ? 22 : 16) : num_slices;
+    if (m < 0 || l < 0 || n < 0 || S < 1 || S > max_slices(digit_kind)) return MPGEMM_EINVAL;
     if ((m * l && !A) || (l * n && !B) || (m * n && !C)) return MPGEMM_EINVAL;
-    // every level sum must stay inside int32: (S) pairs * 127^2 * l < 2^31
-    if ((double)S * 16129.0 * (double)l >= 2147483648.0) return MPGEMM_EUNSUPPORTED;
+    if (digit_kind == 0) {
+        // every level sum must stay inside int32: S pairs * 127^2 * l < 2^31
+        if ((double)S * 16129.0 * (double)l >= 2147483648.0) return MPGEMM_EUNSUPPORTED;
+    } else {
+        // a pair's f32 sum must stay below 2^24 (256 l) and a level inside int32
+        if (l > 65536 || (double)S * 256.0 * (double)l >= 2147483648.0) return MPGEMM_EUNSUPPORTED;
+    }
     if (m > 65535 || n > 65535) return MPGEMM_EUNSUPPORTED;   // grid.y limits of the slice kernels
     cudaStream_t s = (cudaStream_t)stream;
     if (m == 0 || n == 0) return MPGEMM_OK;
@@ -521,26 +659,45 @@ int mpgemm_dd_ozaki(int64_t m, int64_t l, int64_t n, const double* A, const doub
     bool owned = false;
     int rc = workspace_get(bytes, s, &ws, &owned);
     if (rc) return rc;
-    rc = ozaki_gemm_ws(m, l, n, A, B, C, S, ws, bytes, s);
+    rc = ozaki_gemm_ws(digit_kind, m, l, n, A, B, C, S, ws, bytes, s);
     int rc2 = workspace_release(ws, owned, s);
     return rc ? rc : rc2;
 }
 
-int mpgemm_ozaki_split(int by_col, int64_t rows, int64_t cols, const double* X, int num_slices, int* expo,
-                       signed char* digits, void* stream) {
-    int S = num_slices <= 0 ? 16 : num_slices;
-    if (rows <= 0 || cols <= 0 || !X || !expo || !digits || S < 1 || S > 18) return MPGEMM_EINVAL;
+int mpgemm_dd_ozaki(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int num_slices,
+                    void* stream) {
+    return mpgemm_dd_ozaki_ex(m, l, n, A, B, C, num_slices, 0, stream);
+}
+
+int mpgemm_ozaki_split_ex(int digit_kind, int by_col, int64_t rows, int64_t cols, const double* X, int num_slices,
+                          int* expo, void* digits, void* stream) {
+    if (digit_kind != 0 && digit_kind != 1) return MPGEMM_EINVAL;
+    int S = num_slices <= 0 ? (digit_kind == 1 ? 22 : 16) : num_slices;
+    if (rows <= 0 || cols <= 0 || !X || !expo || !digits || S < 1 || S > max_slices(digit_kind)) return MPGEMM_EINVAL;
     if (rows > 65535 && !by_col) return MPGEMM_EUNSUPPORTED;
     if (cols > 65535 && by_col) return MPGEMM_EUNSUPPORTED;
     int64_t inner = by_col ? rows : cols;
-    return ozaki_split(by_col, rows, cols, X, S, expo, digits, ozaki_padded_k(inner), (cudaStream_t)stream);
+    return ozaki_split(digit_kind, by_col, rows, cols, X, S, expo, digits, ozaki_padded_k(inner), (cudaStream_t)stream);
+}
+
+int mpgemm_ozaki_split(int by_col, int64_t rows, int64_t cols, const double* X, int num_slices, int* expo,
+                       signed char* digits, void* stream) {
+    return mpgemm_ozaki_split_ex(0, by_col, rows, cols, X, num_slices, expo, digits, stream);
+}
+
+int mpgemm_ozaki_levels_ex(int digit_kind, int64_t m, int64_t l, int64_t n, int num_slices, const void* DA,
+                           const void* DB, int* levels, void* stream) {
+    if (digit_kind != 0 && digit_kind != 1) return MPGEMM_EINVAL;
+    int S = num_slices <= 0 ? (digit_kind == 1 ? 22 : 16) : num_slices;
+    if (m <= 0 || l <= 0 || n <= 0 || !DA || !DB || !levels || S < 1 || S > max_slices(digit_kind))
+        return MPGEMM_EINVAL;
+    if (digit_kind == 1 && l > 65536) return MPGEMM_EUNSUPPORTED;
+    return ozaki_levels(digit_kind, m, n, ozaki_padded_k(l), S, DA, DB, levels, (cudaStream_t)stream);
 }
 
 int mpgemm_ozaki_levels(int64_t m, int64_t l, int64_t n, int num_slices, const signed char* DA,
                         const signed char* DB, int* levels, void* stream) {
-    int S = num_slices <= 0 ? 16 : num_slices;
-    if (m <= 0 || l <= 0 || n <= 0 || !DA || !DB || !levels || S < 1 || S > 18) return MPGEMM_EINVAL;
-    return ozaki_levels(m, n, ozaki_padded_k(l), S, DA, DB, levels, (cudaStream_t)stream);
+    return mpgemm_ozaki_levels_ex(0, m, l, n, num_slices, DA, DB, levels, stream);
 }
 
 }  // extern "C"

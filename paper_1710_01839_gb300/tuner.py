@@ -33,9 +33,20 @@ def report_dict(r: TuneReport):
         cands.append({"n_min": r.cand_n_min[i], "rows": r.cand_rows[i], "sample_ms": r.cand_sample_ms[i],
                       "pred_ms": pred, "full_ms": full,
                       "rel_diff": (abs(pred - full) / full) if full else None})
-    return {"algo": ALGO_NAME[r.algo], "n_min": r.n_min, "depth": r.depth, "best_ms": r.best_ms,
-            "candidates": cands, "simple_ms": _nan(r.simple_ms), "block_ms": r.block_ms,
-            "strassen_ms": {d: _nan(r.strassen_ms[d]) for d in (1, 2, 3)}, "tuning_ms": r.tuning_ms}
+    out = {"algo": ALGO_NAME[r.algo], "n_min": r.n_min, "depth": r.depth, "best_ms": r.best_ms,
+           "candidates": cands, "simple_ms": _nan(r.simple_ms), "block_ms": r.block_ms,
+           "strassen_ms": {d: _nan(r.strassen_ms[d]) for d in (1, 2, 3)}, "tuning_ms": r.tuning_ms}
+    # Section 3's claim: tuning costs 1.6-2.3x more without the prediction.
+    # Device time of the procedure with the sampled runs vs. with full runs
+    # of the block algorithm for every n_min (the final timings are common).
+    if all(c["full_ms"] is not None for c in cands):
+        common = sum(v for v in [out["simple_ms"], out["block_ms"]] + list(out["strassen_ms"].values())
+                     if v is not None)
+        with_pred = sum(c["sample_ms"] for c in cands) + common
+        without = sum(c["full_ms"] for c in cands) + common
+        out["tuning_cost_ratio_without_prediction"] = without / with_pred
+        out["max_prediction_rel_diff"] = max(c["rel_diff"] for c in cands)
+    return out
 
 
 def tune(fmt, A, B, C, flags=REMEMBER, prec_bits=0, stream=None):

@@ -113,3 +113,51 @@ def test_exact_on_integers():
     C = oracle.ozaki_gemm(I.ints_to_dd(a), I.ints_to_dd(b), 4)
     assert np.array_equal(C[0], (a @ b).astype(np.float64))
     assert not C[1].any()
+
+
+# ---------------------------------------------------------------- balanced base-32 (FP8) digits
+
+@pytest.mark.parametrize("S", [1, 4, 22, 24])
+def test_b32_digits_are_exact_balanced_truncation(S):
+    A, _ = I.dd_rowcol_scaled(6, 10, 4, seed=14)
+    A[:, 2, 3] = 0.0
+    A[:, 4, :] = 0.0
+    e = oracle.ozaki_row_expo(A)
+    D = oracle.ozaki_slice_b32(A, e, S, by_col=False)
+    Di = D.astype(np.int64)
+    assert np.abs(Di).max() <= 16                       # every digit exact in FP8 e4m3
+    for i in range(6):
+        for k in range(10):
+            x = value(A[:, i, k]) * Fraction(2) ** -(int(e[i]) + 1)
+            assert abs(x) < Fraction(1, 2)
+            if x != 0:
+                # lower digits of |x| lie in [-16, 15] (balanced), the top one in [0, 16]
+                signed = Di[:, i, k] if x > 0 else -Di[:, i, k]
+                assert signed[1:].max(initial=-16) <= 15 and 0 <= signed[0] <= 16
+            scaled = x * (1 << (5 * S))
+            trunc = (abs(scaled.numerator) // scaled.denominator) * (1 if x >= 0 else -1)
+            got = sum(int(D[s, i, k]) * (32 ** (S - 1 - s)) for s in range(S))
+            assert got == trunc
+
+
+def test_b32_pipeline_recombination_and_bound():
+    S = 22
+    A, B = I.dd_rowcol_scaled(20, 36, 18, seed=15)
+    e, f = oracle.ozaki_row_expo(A), oracle.ozaki_col_expo(B)
+    DA = oracle.ozaki_slice_b32(A, e, S, False)
+    DB = oracle.ozaki_slice_b32(B, f, S, True)
+    L = oracle.ozaki_levels(DA, DB, S)
+    want = np.zeros_like(L)
+    for s in range(1, S + 1):
+        for t in range(1, S + 2 - s):
+            want[s + t] += DA[s - 1].astype(np.int64) @ DB[t - 1].astype(np.int64)
+    assert np.array_equal(L, want)
+    C = oracle.ozaki_recombine_bits(L, e, f, S, 5, 1)
+    for i in (0, 7, 19):
+        for j in (0, 17):
+            x = sum((Fraction(int(L[g, i, j])) * Fraction(2) ** (int(e[i]) + int(f[j]) + 2 - 5 * g)
+                     for g in range(2, S + 2)), Fraction(0))
+            assert C[:, i, j].tolist() == greedy(x, 2)
+    assert np.array_equal(C, oracle.ozaki_gemm_b32(A, B, S))
+    errs = {s: _max_rel_err(A, B, oracle.ozaki_gemm_b32(A, B, s)) for s in (12, 18, 22)}
+    assert errs[22] <= 2.0**-100 and errs[22] <= errs[18] <= errs[12]
