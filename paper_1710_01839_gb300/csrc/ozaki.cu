@@ -19,6 +19,7 @@
 #include "ozaki.h"
 #include "profile.h"
 #include "strassen.h"
+#include "tc_levels.h"
 
 namespace mpg {
 
@@ -537,7 +538,8 @@ __global__ void k_recombine(int64_t m, int64_t n, int S, int bits, int head, con
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-int64_t ozaki_padded_k(int64_t l) { return (l + OZ_BK - 1) / OZ_BK * OZ_BK; }
+// K padded to 128 bytes: a whole number of K blocks for both level kernels.
+int64_t ozaki_padded_k(int64_t l) { return (l + 127) / 128 * 128; }
 
 size_t ozaki_workspace_bytes(int64_t m, int64_t l, int64_t n, int S) {
     int64_t lp = ozaki_padded_k(l);
@@ -589,7 +591,8 @@ static int levels_launch(int64_t m, int64_t n, int64_t lp, int S, const void* DA
 
 int ozaki_levels(int kind, int64_t m, int64_t n, int64_t lp, int S, const void* DA, const void* DB, int* Lv,
                  cudaStream_t s) {
-    return kind == 1 ? levels_launch<true>(m, n, lp, S, DA, DB, Lv, s) : levels_launch<false>(m, n, lp, S, DA, DB, Lv, s);
+    // FP8 digits: tcgen05 (kind::f8f6f4) kernel; int8 digits: mma.sync s8 (no tcgen05 integer MMA on sm_103a)
+    return kind == 1 ? tc_levels(m, n, lp, S, DA, DB, Lv, s) : levels_launch<false>(m, n, lp, S, DA, DB, Lv, s);
 }
 
 int ozaki_recombine(int kind, int64_t m, int64_t n, int S, const int* Lv, const int* e, const int* f, double* C,

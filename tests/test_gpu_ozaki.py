@@ -22,7 +22,7 @@ def _p(t):
 
 
 def _lp(k):
-    return (k + 63) // 64 * 64
+    return (k + 127) // 128 * 128
 
 
 def _split(X, S, by_col):

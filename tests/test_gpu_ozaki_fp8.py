@@ -30,7 +30,7 @@ def _sp():
 
 
 def _lp(k):
-    return (k + 63) // 64 * 64
+    return (k + 127) // 128 * 128
 
 
 def decode_e4m3(codes: np.ndarray) -> np.ndarray:
