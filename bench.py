@@ -157,7 +157,7 @@ def split_precision_extra(args, stream):
         out[name + "_gflops"] = flops / (ms * 1e-3) / 1e9
         out[name + "_ms"] = ms
     out["speedup_vs_best_plain_dd"] = min(out["plain_dd_block_ms"], out["plain_dd_strassen3_ms"]) / oz_ms
-    # FP8 digits: balanced base-32, e4m3 mma.sync with exact f32 accumulation
+    # FP8 digits: balanced base-32, e4m3 tcgen05 MMAs with exact f32 accumulation in tensor memory
     S8 = args.ozaki_fp8_slices
 
     def oz8():

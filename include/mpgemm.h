@@ -108,8 +108,8 @@ size_t mpgemm_ozaki_workspace_size(int64_t m, int64_t l, int64_t n, int num_slic
 int mpgemm_ozaki_slices_default(void);
 /* Steps 1-2 alone: digits of a DD matrix X (rows x cols planes).  by_col = 0:
    row scaling, digits as S planes of rows x lp int8 (lp = cols rounded up to
-   64, zero padded); by_col = 1: column scaling, digits transposed as S planes
-   of cols x lp (lp = rows rounded up to 64).  expo receives the exponents. */
+   128, zero padded); by_col = 1: column scaling, digits transposed as S planes
+   of cols x lp (lp = rows rounded up to 128).  expo receives the exponents. */
 int mpgemm_ozaki_split(int by_col, int64_t rows, int64_t cols, const double* X, int num_slices, int* expo,
                        signed char* digits, void* stream);
 /* Step 3 alone: levels = S planes (g = 2..S+1) of m x n int32 from digit
@@ -122,10 +122,13 @@ int mpgemm_ozaki_levels(int64_t m, int64_t l, int64_t n, int num_slices, const s
  *   MPGEMM_DIGITS_E4M3 (1): each element scaled by 2^-(e_i+1) (one bit of
  *     headroom) is truncated toward zero to 5 S bits and written in balanced
  *     base-32 digits (every digit in [-16, 16], exact in FP8 e4m3), stored as
- *     e4m3 codes; products on mma.sync e4m3 with f32 accumulation, exact
- *     because every partial sum of one slice pair is an integer below 256 l
- *     <= 2^24 (l <= 65536), moved to int32 after each pair; S <= 24, default
- *     22 (<= 2^-100 |A||B| on the same inputs as 16 int8 slices).
+ *     e4m3 codes; products on the tcgen05 tensor cores (kind::f8f6f4) with
+ *     f32 accumulation in tensor memory, exact because every partial sum of
+ *     Q = floor(2^24 / (256 lp)) slice pairs is an integer below 2^24 (l <=
+ *     65536), moved to int32 after every Q pairs; S <= 24, default 22
+ *     (<= 2^-100 |A||B| on the same inputs as 16 int8 slices).  For
+ *     mpgemm_ozaki_levels_ex with e4m3 digits, DA and DB must be 16-byte
+ *     aligned (they are read through TMA tensor maps), else MPGEMM_EINVAL.
  * c_ij = RN_DD(2^(e_i + f_j + 2 h) sum_g L_g 2^(-b g)), b = 7, h = 0 (int8)
  * or b = 5, h = 1 (e4m3).  mpgemm_ozaki_split_ex writes 1-byte digits (int8
  * or e4m3 codes) in the layout described for mpgemm_ozaki_split. */

@@ -1,23 +1,40 @@
 // Level sums of the FP8-digit split-precision DD GEMM on the 5th-generation
 // tensor cores (tcgen05, kind::f8f6f4, e4m3 x e4m3 -> f32 in tensor memory).
 //
-// One CTA (128 threads) computes one 128 x 256 tile of C for one chunk of
-// one level: L_g = sum_{s in chunk} D_s^A (D_{g-s}^B)^T, the K dimension being
-// the concatenation of the chunk's slice pairs.  Operands are staged by
-// cp.async into shared memory in the K-major, 128-byte-swizzled layout the
-// tensor core reads through smem descriptors (4 stages of 128 bytes of K);
-// one thread issues the MMAs and tcgen05.commit signals a per-stage mbarrier
-// when a stage may be overwritten.  The f32 accumulator lives in tensor
-// memory (256 columns); a chunk holds at most Q pairs with Q * 256 * lp <=
-// 2^24, so every partial sum is an exact integer.  The epilogue reads the
-// accumulator with tcgen05.ld and stores (single-chunk levels) or atomically
-// adds (multi-chunk levels, into a zeroed buffer) the int32 level sums.
+// A job is one 128 x 256 tile of one level: L_g = sum_{s=1}^{g-1} D_s^A
+// (D_{g-s}^B)^T, the K dimension being the concatenation of the g - 1 slice
+// pairs.  The f32 accumulator is exact only while every partial sum stays
+// below 2^24, so a job runs as chunks of at most Q pairs (Q * 256 * lp <=
+// 2^24); each chunk's sum is converted to int32 and the chunks of a job are
+// added in registers-to-memory order by the same epilogue thread.
 //
-// Every wait is bounded; on a timeout the CTA records DEV_TIMEOUT in the
-// status word, skips its epilogue and still frees its tensor memory.
-#include <algorithm>
+// Persistent, warp-specialised CTA (one per SM, 192 threads):
+//   warp 0 (one lane)  TMA producer: 3-D tensor maps over the digit planes
+//                      ([S][rows][lp] bytes), 128-byte swizzle, one A box
+//                      (128 x 128 B) and one B box (256 x 128 B) per stage,
+//                      completion counted on the stage's `full` mbarrier;
+//   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (K = 32) per stage into
+//                      one of two 256-column TMEM accumulators, then
+//                      tcgen05.commit to the stage's `empty` mbarrier, and
+//                      after a chunk's last stage to the accumulator's
+//                      `tmem_full` mbarrier;
+//   warps 2-5          epilogue: tcgen05.ld of their 32-lane quarter,
+//                      exact f32 -> int32, store (first chunk) or add (later
+//                      chunks), then release the accumulator (`tmem_empty`).
+// With two accumulators the epilogue of one chunk overlaps the MMAs of the
+// next.  Jobs are ordered heaviest level first and dealt to CTAs in snake
+// order (round k: CTA c takes job k G + c, or k G + G - 1 - c for odd k), so
+// the per-CTA sums of pair counts differ by at most about one job.
+//
+// Every wait is bounded.  A role that gives up sets a shared abort flag and
+// DEV_TIMEOUT in the status word; the other roles leave their loops when
+// they see the flag.  Before the CTA exits the producer waits for its last
+// TMA copy into each stage and the MMA thread waits for all its MMAs, so no
+// asynchronous write is in flight when tensor memory is freed.
+#include <cuda.h>
+
 #include <cstdint>
-#include <vector>
+#include <mutex>
 
 #include "common.cuh"
 #include "profile.h"
@@ -25,245 +42,362 @@
 
 namespace mpg {
 
-constexpr int TC_M = 128, TC_N = 256, TC_BK = 128, TC_STAGES = 4, TC_THREADS = 128;
-constexpr int TC_STAGE_BYTES = (TC_M + TC_N) * TC_BK;          // 48 KB
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;      // + alignment slack
+constexpr int TC_M = 128, TC_N = 256, TC_BK = 128, TC_STAGES = 4, TC_THREADS = 192;
+constexpr int TC_A_BYTES = TC_M * TC_BK, TC_B_BYTES = TC_N * TC_BK;
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;          // 48 KB
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;      // + 1024-byte alignment slack
+constexpr int TC_TMEM_COLS = 2 * TC_N;                          // two accumulators
 constexpr uint32_t TC_IDESC = (1u << 4)                         // D: f32
                               | (0u << 7) | (0u << 10)          // A, B: e4m3
                               | ((uint32_t)(TC_N >> 3) << 17)   // N = 256
                               | ((uint32_t)(TC_M >> 4) << 24);  // M = 128
 constexpr uint32_t TC_SPIN = 1u << 24;
+constexpr uint64_t TC_WAIT_NS = 4000000000ull;   // 4 s
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart.
+// 1024 bytes apart (the layout a SWIZZLE_128B tensor map writes).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of parity `parity`; false after TC_SPIN polls or
+// TC_WAIT_NS nanoseconds, or when another role has raised the abort flag
+// (abort_flag == nullptr: teardown wait for asynchronous work already in
+// flight, which ignores the flag).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
+    uint64_t t0 = 0;
     for (uint32_t i = 0; i < TC_SPIN; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 255) == 255) {
+            if (abort_flag && *abort_flag) return false;
+            const uint64_t t = global_ns();
+            if (!t0) t0 = t;
+            else if (t - t0 > TC_WAIT_NS) return false;
+        }
     }
     return false;
 }
 
-// byte offset of 16-byte chunk c of row r inside a swizzled operand tile
-__device__ __forceinline__ uint32_t sw128(int r, int c) {
-    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) { return mbar_wait(bar, parity, nullptr); }
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
 }
 
-struct TcItem {
-    int tile, g, s0, s1;   // tile index, level, pairs s in [s0, s1)
+__device__ __forceinline__ void tc_fail(volatile int* abort_flag, unsigned* status) {
+    *abort_flag = 1;
+    atomicOr(status, DEV_TIMEOUT);
+}
+
+struct TcJob {
+    int g, row0, col0;
 };
 
+// Job j: levels from g = S + 1 (S pairs) down to g = 2, tiles row-major within a level.
+__device__ __forceinline__ TcJob tc_job(int j, int S, int tiles, int tiles_n) {
+    const int tile = j % tiles;
+    return TcJob{S + 1 - j / tiles, (tile / tiles_n) * TC_M, (tile % tiles_n) * TC_N};
+}
+
+// Index of this CTA's job in round k (snake order).
+__device__ __forceinline__ int tc_job_index(int k, int G, int c) { return k * G + ((k & 1) ? (G - 1 - c) : c); }
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_levels_tc(int64_t m, int64_t n, int64_t lp, const unsigned char* __restrict__ DA,
-                const unsigned char* __restrict__ DB, int* __restrict__ Lv, const TcItem* __restrict__ items,
-                const unsigned char* __restrict__ multi, unsigned tiles_n, unsigned* status) {
+    k_levels_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n,
+                int ksteps, int S, int Q, int tiles_n, int tiles, int vec, int* __restrict__ Lv, unsigned* status) {
     extern __shared__ unsigned char dsm[];
-    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tmem_full[2], tmem_empty[2], drain;
     __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
-    const TcItem it = items[blockIdx.x];
-    const int64_t row0 = (int64_t)(it.tile / tiles_n) * TC_M, col0 = (int64_t)(it.tile % tiles_n) * TC_N;
-    const int ksteps = (int)(lp / TC_BK);
-    const int total = (it.s1 - it.s0) * ksteps;
-    const int64_t planeA = m * lp, planeB = n * lp;
+    const int J = tiles * S, G = gridDim.x, cta = blockIdx.x;
+    const int rounds = (J + G - 1) / G;
 
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
-                     "r"(TC_N));
+                     "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; s++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mbar[s])));
+        for (int s = 0; s < TC_STAGES; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])));
+        }
+        for (int a = 0; a < 2; a++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&tmem_full[a])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&tmem_empty[a])), "r"(128));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&drain)));
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
 
-    // iteration q: pair s = s0 + q / ksteps, K block kb = (q % ksteps) * 128, into stage q % STAGES
-    auto load = [&](int q) {
-        const int s = it.s0 + q / ksteps;
-        const int64_t kb = (int64_t)(q % ksteps) * TC_BK;
-        const unsigned char* Ab = DA + (int64_t)(s - 1) * planeA + kb;
-        const unsigned char* Bb = DB + (int64_t)(it.g - s - 1) * planeB + kb;
-        unsigned char* sA = base + (q % TC_STAGES) * TC_STAGE_BYTES;
-        unsigned char* sB = sA + TC_M * TC_BK;
-#pragma unroll
-        for (int v = 0; v < (TC_M * 8) / TC_THREADS; v++) {
-            int c = tid + v * TC_THREADS, r = c >> 3, ch = c & 7;
-            int64_t gr = row0 + r;
-            bool ok = gr < m;
-            const void* src = ok ? (const void*)(Ab + gr * lp + ch * 16) : (const void*)DA;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(sA + sw128(r, ch))), "l"(src),
-                         "r"(ok ? 16 : 0));
-        }
-#pragma unroll
-        for (int v = 0; v < (TC_N * 8) / TC_THREADS; v++) {
-            int c = tid + v * TC_THREADS, r = c >> 3, ch = c & 7;
-            int64_t gc = col0 + r;
-            bool ok = gc < n;
-            const void* src = ok ? (const void*)(Bb + gc * lp + ch * 16) : (const void*)DB;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(sB + sw128(r, ch))), "l"(src),
-                         "r"(ok ? 16 : 0));
-        }
-    };
-
-    bool ok = true;
-#pragma unroll 1
-    for (int q = 0; q < TC_STAGES - 1; q++) {
-        if (q < total) load(q);
-        asm volatile("cp.async.commit_group;");
-    }
-#pragma unroll 1
-    for (int q = 0; q < total; q++) {
-        const int st = q % TC_STAGES;
-        asm volatile("cp.async.wait_group %0;" ::"n"(TC_STAGES - 2) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        ok = __syncthreads_and(ok);   // also makes a timeout seen by any thread a uniform exit
-        if (!ok) break;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a0 = su32(base + st * TC_STAGE_BYTES), b0 = a0 + TC_M * TC_BK;
-#pragma unroll
-            for (int j = 0; j < TC_BK / 32; j++) {
-                const uint64_t ad = smem_desc(a0 + 32 * j), bd = smem_desc(b0 + 32 * j);
-                const uint32_t acc = (q > 0 || j > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             su32(&mbar[st]))
-                         : "memory");
-        }
-        // refill the stage used by iteration q - 1 once its MMAs have read it
-        const int nx = q + TC_STAGES - 1;
-        if (nx < total) {
-            if (q >= 1) {
-                const int pq = q - 1;
-                if (!mbar_wait(su32(&mbar[pq % TC_STAGES]), (uint32_t)((pq / TC_STAGES) & 1))) ok = false;
-            }
-            if (ok) load(nx);
-        }
-        asm volatile("cp.async.commit_group;");
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    // the last commit covers every MMA issued before it
-    if (ok && total > 0) {
-        const int lq = total - 1;
-        if (!mbar_wait(su32(&mbar[lq % TC_STAGES]), (uint32_t)((lq / TC_STAGES) & 1))) ok = false;
-    }
-    // a CTA that timed out must not read or free tensor memory another thread's MMAs may still write
-    ok = __syncthreads_and(ok);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok && total > 0) {
-        int* out = Lv + (int64_t)(it.g - 2) * m * n;
-        const bool atomic = multi[it.g] != 0;
-        const int64_t r = row0 + warp * 32 + lane;
-#pragma unroll 1
-        for (int ch = 0; ch < TC_N / 32; ch++) {
-            uint32_t v[32];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (r < m) {
-                const int64_t c0 = col0 + ch * 32;
-#pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    if (c0 + i < n) {
-                        const int x = __float2int_rn(__uint_as_float(v[i]));
-                        if (atomic) atomicAdd(out + r * n + c0 + i, x);
-                        else out[r * n + c0 + i] = x;
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int k = 0; k < rounds && ok; k++) {
+                const int j = tc_job_index(k, G, cta);
+                if (j >= J) continue;
+                const TcJob jb = tc_job(j, S, tiles, tiles_n);
+                for (int s = 1; s < jb.g && ok; s++) {
+                    for (int kb = 0; kb < ksteps; kb++, it++) {
+                        const int st = (int)(it % TC_STAGES);
+                        if (!mbar_wait(su32(&empty[st]), ((it / TC_STAGES) & 1) ^ 1, &abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fb = su32(&full[st]);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                     "r"(TC_STAGE_BYTES)
+                                     : "memory");
+                        const uint32_t sA = su32(base + st * TC_STAGE_BYTES);
+                        tma_load_3d(sA, &tmA, kb * TC_BK, jb.row0, s - 1, fb);
+                        tma_load_3d(sA + TC_A_BYTES, &tmB, kb * TC_BK, jb.col0, jb.g - s - 1, fb);
                     }
                 }
             }
+            if (!ok) tc_fail(&abort_flag, status);
+            // the last copy issued into each stage has landed before the CTA may exit
+            for (uint32_t i = it > (uint32_t)TC_STAGES ? it - TC_STAGES : 0; i < it; i++)
+                if (!mbar_drain(su32(&full[i % TC_STAGES]), (i / TC_STAGES) & 1)) tc_fail(&abort_flag, status);
         }
-    } else if (!ok && tid == 0) {
-        atomicOr(status, DEV_TIMEOUT);
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, cc = 0;
+            bool ok = true, issued = false;
+            for (int k = 0; k < rounds && ok; k++) {
+                const int j = tc_job_index(k, G, cta);
+                if (j >= J) continue;
+                const int pairs = S - j / tiles;   // g - 1
+                for (int s0 = 1; s0 <= pairs && ok; s0 += Q, cc++) {
+                    const int np = (pairs - s0 + 1) < Q ? (pairs - s0 + 1) : Q;
+                    const uint32_t acc = cc & 1;
+                    if (!mbar_wait(su32(&tmem_empty[acc]), ((cc >> 1) & 1) ^ 1, &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t d = tmem + acc * TC_N;
+                    const int nst = np * ksteps;
+                    for (int q = 0; q < nst; q++, it++) {
+                        const int st = (int)(it % TC_STAGES);
+                        if (!mbar_wait(su32(&full[st]), (it / TC_STAGES) & 1, &abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint32_t a0 = su32(base + st * TC_STAGE_BYTES), b0 = a0 + TC_A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 32; kk++) {
+                            const uint64_t ad = smem_desc(a0 + 32 * kk), bd = smem_desc(b0 + 32 * kk);
+                            const uint32_t accum = (q > 0 || kk > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(accum));
+                        }
+                        issued = true;
+                        // the stage may be refilled once these MMAs have read it
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                su32(&empty[st]))
+                            : "memory");
+                    }
+                    if (!ok) break;
+                    // the chunk's sum is complete once every MMA issued so far has finished
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            su32(&tmem_full[acc]))
+                        : "memory");
+                }
+            }
+            if (!ok) tc_fail(&abort_flag, status);
+            if (issued) {
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&drain))
+                             : "memory");
+                if (!mbar_drain(su32(&drain), 0)) tc_fail(&abort_flag, status);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;   // tcgen05.ld reaches TMEM lanes 32 (warp % 4) .. + 31
+        uint32_t cc = 0;
+        bool ok = true;
+        for (int k = 0; k < rounds && ok; k++) {
+            const int j = tc_job_index(k, G, cta);
+            if (j >= J) continue;
+            const TcJob jb = tc_job(j, S, tiles, tiles_n);
+            const int pairs = jb.g - 1;
+            const int64_t r = (int64_t)jb.row0 + quarter * 32 + lane;
+            int* out = Lv + (int64_t)(jb.g - 2) * m * n + r * n;
+            for (int s0 = 1; s0 <= pairs; s0 += Q, cc++) {
+                const uint32_t acc = cc & 1;
+                const bool w = mbar_wait(su32(&tmem_full[acc]), (cc >> 1) & 1, &abort_flag);
+                if (!__all_sync(0xffffffffu, w)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const bool first = s0 == 1;
+#pragma unroll 1
+                for (int ch = 0; ch < TC_N / 32; ch++) {
+                    uint32_t v[32];
+                    const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + acc * TC_N + (uint32_t)(ch * 32);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                        : "r"(ta));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (r < m) {
+                        const int c0 = jb.col0 + ch * 32;
+                        int x[32];
+#pragma unroll
+                        for (int i = 0; i < 32; i++) x[i] = __float2int_rn(__uint_as_float(v[i]));
+                        if (vec && c0 + 32 <= n) {
+                            int4* o = (int4*)(out + c0);
+#pragma unroll
+                            for (int i = 0; i < 8; i++) {
+                                int4 t = make_int4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+                                if (!first) {
+                                    const int4 p = o[i];
+                                    t.x += p.x;
+                                    t.y += p.y;
+                                    t.z += p.z;
+                                    t.w += p.w;
+                                }
+                                o[i] = t;
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; i++)
+                                if (c0 + i < n) out[c0 + i] = first ? x[i] : out[c0 + i] + x[i];
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tmem_empty[acc])) : "memory");
+            }
+        }
+        if (!ok && lane == 0) tc_fail(&abort_flag, status);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+// ---------------------------------------------------------------- host side
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// [S][rows][lp] bytes, box = 128 bytes of K x box_rows rows x 1 plane,
+// 128-byte swizzle; rows past the end read as zero.
+static int digit_map(CUtensorMap* map, const void* D, int64_t rows, int64_t lp, int S, int box_rows) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return MPGEMM_ECUDA;
+    cuuint64_t dims[3] = {(cuuint64_t)lp, (cuuint64_t)rows, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)lp, (cuuint64_t)(rows * lp)};
+    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(D), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? MPGEMM_OK : MPGEMM_EINVAL;
 }
 
 int tc_levels(int64_t m, int64_t n, int64_t lp, int S, const void* DA, const void* DB, int* Lv, cudaStream_t s) {
-    if (lp % TC_BK) return MPGEMM_EINVAL;
-    unsigned* status = device_status_ptr();
-    if (!status) return MPGEMM_ECUDA;
+    if (lp <= 0 || lp % TC_BK || S < 1) return MPGEMM_EINVAL;
+    if (((uintptr_t)DA | (uintptr_t)DB) & 15) return MPGEMM_EINVAL;   // tensor-map base alignment
+    if (m > 65535 || n > 65535) return MPGEMM_EUNSUPPORTED;   // keeps job counts and offsets in int
     const int Q = (int)((int64_t)(1 << 24) / (256 * lp));   // pairs per chunk: Q * 256 * lp <= 2^24
     if (Q < 1) return MPGEMM_EUNSUPPORTED;
-    const unsigned tm = ceil_div(m, TC_M), tn = ceil_div(n, TC_N);
-    std::vector<TcItem> items;
-    std::vector<unsigned char> multi(S + 2, 0);
-    // heaviest work first: levels with the most pairs (chunks of up to Q pairs)
-    for (int g = S + 1; g >= 2; g--) {
-        const int pairs = g - 1;
-        if (pairs > Q) multi[g] = 1;
-        for (int s0 = 1; s0 <= pairs; s0 += Q) {
-            const int s1 = s0 + Q <= pairs + 1 ? s0 + Q : pairs + 1;
-            for (unsigned t = 0; t < tm * tn; t++) items.push_back(TcItem{(int)t, g, s0, s1});
-        }
-    }
-    // stable heaviest-first order: sort chunks by their pair count
-    std::stable_sort(items.begin(), items.end(),
-                     [](const TcItem& a, const TcItem& b) { return (a.s1 - a.s0) > (b.s1 - b.s0); });
-    bool any_multi = false;
-    for (int g = 2; g <= S + 1; g++) any_multi |= multi[g] != 0;
-    // the item table and the per-level flags travel in one stream-ordered allocation
-    const size_t ib = sizeof(TcItem) * items.size(), mb = multi.size();
-    void* dev = nullptr;
-    bool owned = false;
-    cudaError_t ae = cudaMallocAsync(&dev, ib + mb + 16, s);
-    if (ae != cudaSuccess) {
-        set_last_cuda_error(ae);
-        return MPGEMM_ENOMEM;
-    }
-    owned = true;
+    unsigned* status = device_status_ptr();
+    if (!status) return MPGEMM_ECUDA;
+    CUtensorMap mA, mB;
     int rc;
-    TcItem* d_items = (TcItem*)dev;
-    unsigned char* d_multi = (unsigned char*)dev + ((ib + 15) & ~(size_t)15);
-    MPG_CUDA(cudaMemcpyAsync(d_items, items.data(), ib, cudaMemcpyHostToDevice, s));
-    MPG_CUDA(cudaMemcpyAsync(d_multi, multi.data(), mb, cudaMemcpyHostToDevice, s));
-    if (any_multi) MPG_CUDA(cudaMemsetAsync(Lv, 0, sizeof(int) * (size_t)S * (size_t)(m * n), s));
+    if ((rc = digit_map(&mA, DA, m, lp, S, TC_M))) return rc;
+    if ((rc = digit_map(&mB, DB, n, lp, S, TC_N))) return rc;
+    static int sms[64];
     static bool attr_set[64];
     int devno = 0;
     MPG_CUDA(cudaGetDevice(&devno));
-    if (devno >= 0 && devno < 64 && !attr_set[devno]) {
+    if (devno < 0 || devno >= 64) return MPGEMM_EUNSUPPORTED;
+    if (!attr_set[devno]) {
         MPG_CUDA(cudaFuncSetAttribute(k_levels_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        MPG_CUDA(cudaDeviceGetAttribute(&sms[devno], cudaDevAttrMultiProcessorCount, devno));
         attr_set[devno] = true;
     }
+    const int tiles_m = (int)ceil_div(m, TC_M), tiles_n = (int)ceil_div(n, TC_N);
+    const int tiles = tiles_m * tiles_n;
+    const int64_t jobs = (int64_t)tiles * S;
+    const int grid = (int)(jobs < sms[devno] ? jobs : sms[devno]);
+    const int vec = ((uintptr_t)Lv % 16 == 0) && (n % 4 == 0);
     {
         ProfScope ps(s);
-        k_levels_tc<<<(unsigned)items.size(), TC_THREADS, TC_SMEM, s>>>(m, n, lp, (const unsigned char*)DA,
-                                                                       (const unsigned char*)DB, Lv, d_items, d_multi,
-                                                                       tn, status);
+        k_levels_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(mA, mB, (int)m, (int)n, (int)(lp / TC_BK), S, Q, tiles_n,
+                                                      tiles, vec, Lv, status);
     }
-    rc = check_launch();
-    if (owned) MPG_CUDA(cudaFreeAsync(dev, s));
-    return rc;
+    return check_launch();
 }
 
 }  // namespace mpg

@@ -74,7 +74,12 @@ def test_fp8_digits_bit_exact(S):
     assert np.array_equal(vb[:, :, :70], ob.transpose(0, 2, 1).astype(np.float64))
 
 
-@pytest.mark.parametrize("m,l,n,S", [(37, 70, 45, 6), (130, 200, 129, 22), (256, 192, 256, 24)])
+# (512, 16, 1024, 24): 384 tile-level jobs, so every CTA of the persistent
+# kernel runs several and cycles both tensor-memory accumulators;
+# (130, 4500, 24, 16) and (40, 3300, 30, 22): levels with more pairs than one
+# exact f32 chunk holds (Q = 2^16 / lp = 14 and 19), added chunk by chunk.
+@pytest.mark.parametrize("m,l,n,S", [(37, 70, 45, 6), (130, 200, 129, 22), (256, 192, 256, 24),
+                                     (512, 16, 1024, 24), (130, 4500, 24, 16), (40, 3300, 30, 22)])
 def test_fp8_levels_bit_exact(m, l, n, S):
     import torch
     A, B = I.dd_rowcol_scaled(m, l, n, seed=m + n + 1)
@@ -86,6 +91,16 @@ def test_fp8_levels_bit_exact(m, l, n, S):
     assert rc == 0
     Lo = oracle.ozaki_levels(oracle.ozaki_slice_b32(A, e, S, False), oracle.ozaki_slice_b32(B, f, S, True), S)
     assert np.array_equal(host(Lv).astype(np.int64), Lo[2:S + 2])
+
+
+def test_fp8_levels_reject_unaligned_digits():
+    import torch
+    DA = torch.zeros((2, 8, 128), dtype=torch.uint8, device="cuda")
+    DB = torch.zeros((2, 8, 128), dtype=torch.uint8, device="cuda")
+    Lv = torch.zeros((2, 8, 8), dtype=torch.int32, device="cuda")
+    rc = mpg.lib().mpgemm_ozaki_levels_ex(E4M3, 8, 100, 8, 2, ctypes.c_void_p(DA.data_ptr() + 1), _p(DB), _p(Lv),
+                                          _sp())
+    assert rc == -1
 
 
 def _ozaki_fp8(A, B, S):
