@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "ozaki.h"
+#include "ozaki_digits.cuh"
 #include "profile.h"
 #include "strassen.h"
 #include "tc_levels.h"
@@ -26,8 +27,8 @@ namespace mpg {
 // ---------------------------------------------------------------- step 1
 
 __device__ __forceinline__ int expo_of(double x) {
-    if (x == 0.0) return INT_MIN;
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    if ((b << 1) == 0ull) return INT_MIN;   // +-0 (integer test: no FP64 instruction)
     int E = (int)((b >> 52) & 0x7ff);
     if (E == 0) {   // subnormal: 0.m * 2^-1022, leading one of m decides
         unsigned long long mant = b & ((1ull << 52) - 1);
@@ -48,13 +49,32 @@ __global__ void k_row_expo(int64_t m, int64_t l, const double* hi, int* e) {
     if (lane == 0) e[row] = mx == INT_MIN ? 0 : mx;
 }
 
-// One thread per column, rows walked in order (coalesced across threads).
+// Column maxima in parallel over rows: a block covers 32 columns x
+// COLX_ROWS rows (a warp reads 32 consecutive doubles of one row) and
+// atomically raises f[j], pre-filled with COLX_EMPTY, which lies below every
+// finite frexp exponent (>= -1073) and above the INT_MIN of a zero element.
+constexpr int COLX_ROWS = 256;
+constexpr int COLX_EMPTY = (int)0x80808080;   // the byte fill 0x80
 __global__ void k_col_expo(int64_t l, int64_t n, const double* hi, int* f) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.y * COLX_ROWS;
     if (j >= n) return;
+    const int64_t k1 = k0 + COLX_ROWS < l ? k0 + COLX_ROWS : l;
     int mx = INT_MIN;
-    for (int64_t k = 0; k < l; k++) mx = max(mx, expo_of(hi[k * n + j]));
-    f[j] = mx == INT_MIN ? 0 : mx;
+#pragma unroll 4
+    for (int64_t k = k0 + threadIdx.y; k < k1; k += blockDim.y) mx = max(mx, expo_of(hi[k * n + j]));
+    __shared__ int red[8][32];
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        for (int y = 1; y < (int)blockDim.y; y++) mx = max(mx, red[y][threadIdx.x]);
+        if (mx != INT_MIN) atomicMax(f + j, mx);
+    }
+}
+// An all-zero column keeps the fill value: its exponent is 0.
+__global__ void k_expo_fix(int64_t n, int* f) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n && f[j] == COLX_EMPTY) f[j] = 0;
 }
 
 // ---------------------------------------------------------------- step 2
@@ -131,79 +151,112 @@ __device__ __forceinline__ void dd_digits(double hi, double lo, int e, int S, si
     }
 }
 
-// FP8 e4m3 code of a small integer |v| <= 16 (exact: at most 4 significant bits).
-__device__ __forceinline__ unsigned char e4m3_of_int(int v) {
-    unsigned s = v < 0 ? 0x80u : 0u;
-    int a = v < 0 ? -v : v;
-    if (a == 0) return (unsigned char)s;
-    int e = 31 - __clz(a);                             // floor(log2 a), 0..4
-    unsigned mant = (unsigned)((a << 3) >> e) & 7u;    // (a / 2^e - 1) * 8
-    return (unsigned char)(s | ((unsigned)(e + 7) << 3) | mant);
+// Two e4m3 codes of small integers in one instruction (exact for |v| <= 16):
+// the low byte holds a, the high byte b.
+__device__ __forceinline__ unsigned e4m3x2_of(int a, int b) {
+    unsigned short r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"((float)b), "f"((float)a));
+    return (unsigned)r;
 }
 
-// Balanced base-32 digits (FP8 variant): T = trunc((hi + lo) 2^(5S - e - 1))
-// (one bit of headroom, |T| < 2^(5S-1)), written from the least significant
-// digit up with digits >= 16 replaced by digit - 32 and a carry into the next
-// one; the top digit keeps its carry (<= 16).  Stored as e4m3 codes.
-__device__ __forceinline__ void dd_digits_b32(double hi, double lo, int e, int S, unsigned char* d, int64_t stride) {
-    const int sc = 5 * S - e - 1;
-    double H = ldexp(hi, sc), L = ldexp(lo, sc);
-    double tH = trunc(H);
-    double corr = 0.0;
-    if (tH == H) {
-        if (H > 0.0 && L < 0.0) corr = floor(L);
-        else if (H < 0.0 && L > 0.0) corr = ceil(L);
-        else corr = trunc(L);
-    }
-    unsigned long long th, tl, ch, cl;
-    dbl_int_to_u128(tH, th, tl);
-    dbl_int_to_u128(corr, ch, cl);
-    bool neg;
-    add_s128(th, tl, tH < 0.0, ch, cl, corr < 0.0, neg);
-    int carry = 0;
-    for (int s = S - 1; s >= 0; s--) {
-        int sh = 5 * (S - 1 - s);
-        unsigned long long v = sh >= 64 ? (th >> (sh - 64)) : (sh == 0 ? tl : ((tl >> sh) | (th << (64 - sh))));
-        int dig = (int)(v & 31ull) + carry;
-        carry = 0;
-        if (s > 0 && dig >= 16) {
-            dig -= 32;
-            carry = 1;
+template <int K>
+__device__ __forceinline__ int b32_digit(const B32& u, int S) {
+    const int d = b32_field<K>(u) - (K < S - 1 ? 16 : 0);
+    return u.neg ? -d : d;
+}
+
+// Digit k of four consecutive elements as four e4m3 codes (element 0 in the low byte).
+template <int K>
+__device__ __forceinline__ unsigned b32_word(const B32 (&u)[4], int S) {
+    return e4m3x2_of(b32_digit<K>(u[0], S), b32_digit<K>(u[1], S)) |
+           (e4m3x2_of(b32_digit<K>(u[2], S), b32_digit<K>(u[3], S)) << 16);
+}
+
+// Calls f(K, word) for K = 0 .. S-1 (S <= 24), K compile-time.
+template <int K, typename F>
+__device__ __forceinline__ void b32_words(const B32 (&u)[4], int S, F&& f) {
+    if constexpr (K < 24) {
+        if (K < S) {
+            f(K, b32_word<K>(u, S));
+            b32_words<K + 1>(u, S, f);
         }
-        d[(int64_t)s * stride] = e4m3_of_int(neg ? -dig : dig);
     }
 }
 
-// A (m x l, row scale e): digits into S planes of m x lp (K contiguous, zero padded).
+// A (m x l, row scale e): digits into S planes of m x lp.  One thread per
+// four consecutive K positions: 4-byte stores, a warp writes 128 contiguous
+// bytes of every plane.  Positions l <= k < lp are written as zero digits.
 __global__ void k_slice_rows_f8(int64_t m, int64_t l, int64_t lp, const double* A, const int* e, int S,
-                                unsigned char* D) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t i = blockIdx.y;
-    if (k >= lp || i >= m) return;
-    unsigned char* out = D + i * lp + k;
-    const int64_t plane = m * lp;
-    if (k >= l) {
-        for (int s = 0; s < S; s++) out[s * plane] = 0;
-        return;
+                                unsigned long long Ch, unsigned long long Cl, int vec, unsigned char* D) {
+    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int64_t i = blockIdx.y;
+    if (k0 >= lp || i >= m) return;
+    const int sc = 5 * S - e[i] - 1;
+    const double* hiA = A + i * l;
+    const double* loA = A + m * l + i * l;
+    double h[4], o[4];
+    if (vec && k0 + 4 <= l) {   // vec: A 16-byte aligned and l even
+        const double2 h01 = *(const double2*)(hiA + k0), h23 = *(const double2*)(hiA + k0 + 2);
+        const double2 o01 = *(const double2*)(loA + k0), o23 = *(const double2*)(loA + k0 + 2);
+        h[0] = h01.x; h[1] = h01.y; h[2] = h23.x; h[3] = h23.y;
+        o[0] = o01.x; o[1] = o01.y; o[2] = o23.x; o[3] = o23.y;
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const bool in = k0 + t < l;
+            h[t] = in ? hiA[k0 + t] : 0.0;
+            o[t] = in ? loA[k0 + t] : 0.0;
+        }
     }
-    const int64_t idx = i * l + k;
-    dd_digits_b32(A[idx], A[m * l + idx], e[i], S, out, plane);
+    B32 u[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) u[t] = b32_prepare(h[t], o[t], sc, Ch, Cl);
+    const int64_t plane = m * lp;
+    unsigned* out = (unsigned*)(D + i * lp + k0);
+    b32_words<0>(u, S, [&](int K, unsigned w) { out[(int64_t)(S - 1 - K) * (plane >> 2)] = w; });
 }
 
-__global__ void k_slice_cols_f8(int64_t l, int64_t n, int64_t lp, const double* B, const int* f, int S,
-                                unsigned char* D) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t j = blockIdx.y;
-    if (k >= lp || j >= n) return;
-    unsigned char* out = D + j * lp + k;
-    const int64_t plane = n * lp;
-    if (k >= l) {
-        for (int s = 0; s < S; s++) out[s * plane] = 0;
-        return;
+// B (l x n, column scale f): digits transposed into S planes of n x lp.  A
+// block of 128 threads covers 32 columns x 64 rows of B: lane t takes column
+// j0 + t (a warp reads 256 contiguous bytes of a row), warp w rows k0 + 4q
+// .. + 3 for q = w, w + 4, w + 8, w + 12; the digit words go through shared
+// memory (rows of 16 words padded to 17: conflict-free) and leave as 64-byte
+// row segments of each plane.
+constexpr int SLC_COLS = 32, SLC_ROWS = 64, SLC_PITCH = SLC_ROWS / 4 + 1;
+__global__ void __launch_bounds__(128) k_slice_cols_f8(int64_t l, int64_t n, int64_t lp, const double* B,
+                                                       const int* f, int S, unsigned long long Ch,
+                                                       unsigned long long Cl, unsigned char* D) {
+    extern __shared__ unsigned tile[];   // [S][SLC_COLS][SLC_PITCH]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t k0 = (int64_t)blockIdx.x * SLC_ROWS, j0 = (int64_t)blockIdx.y * SLC_COLS;
+    const int64_t j = j0 + lane;
+    const bool jin = j < n;
+    const int sc = 5 * S - (jin ? f[j] : 0) - 1;
+    const double* loB = B + l * n;
+#pragma unroll 1
+    for (int q = warp; q < SLC_ROWS / 4; q += 4) {
+        B32 u[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int64_t k = k0 + 4 * q + t;
+            const bool in = jin && k < l;
+            u[t] = b32_prepare(in ? B[k * n + j] : 0.0, in ? loB[k * n + j] : 0.0, sc, Ch, Cl);
+        }
+        b32_words<0>(u, S, [&](int K, unsigned w) { tile[((S - 1 - K) * SLC_COLS + lane) * SLC_PITCH + q] = w; });
     }
-    const int64_t idx = k * n + j;
-    dd_digits_b32(B[idx], B[l * n + idx], f[j], S, out, plane);
+    __syncthreads();
+    const int64_t plane = n * lp;
+    for (int s = 0; s < S; s++) {
+#pragma unroll
+        for (int r = 0; r < (SLC_COLS * SLC_ROWS / 4) / 128; r++) {
+            const int idx = threadIdx.x + 128 * r, row = idx >> 4, w = idx & 15;
+            const int64_t jj = j0 + row, kk = k0 + 4 * w;
+            if (jj < n && kk < lp)
+                *(unsigned*)(D + (int64_t)s * plane + jj * lp + kk) = tile[(s * SLC_COLS + row) * SLC_PITCH + w];
+        }
+    }
 }
+
 
 // A (m x l, row scale e): digits into S planes of m x lp (K contiguous, zero padded).
 __global__ void k_slice_rows(int64_t m, int64_t l, int64_t lp, const double* A, const int* e, int S, signed char* D) {
@@ -495,8 +548,31 @@ __global__ void k_recombine(int64_t m, int64_t n, int S, int bits, int head, con
     int64_t i = blockIdx.y;
     if (j >= n) return;
     const int64_t mn = m * n, idx = i * n + j;
-    unsigned long long v[3] = {0ull, 0ull, 0ull};
-    for (int g = 2; g <= S + 1; g++) add_shifted(v, (long long)Lv[(int64_t)(g - 2) * mn + idx], bits * (S + 1 - g));
+    // V = sum_g L_g 2^(bits (S + 1 - g)) by Horner's rule, V <- V 2^bits + L_g,
+    // on six 32-bit limbs (two's complement; |L_g| < 2^31 gives |V| < 2^(32 + bits (S - 1)) <= 2^151)
+    unsigned w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    const int* lp = Lv + idx;
+#pragma unroll 4
+    for (int g = 2; g <= S + 1; g++) {
+        const int x = lp[(int64_t)(g - 2) * mn];
+        w5 = __funnelshift_l(w4, w5, bits);
+        w4 = __funnelshift_l(w3, w4, bits);
+        w3 = __funnelshift_l(w2, w3, bits);
+        w2 = __funnelshift_l(w1, w2, bits);
+        w1 = __funnelshift_l(w0, w1, bits);
+        w0 <<= bits;
+        const unsigned ext = (unsigned)(x >> 31);
+        asm("add.cc.u32 %0, %0, %6;\n\t"
+            "addc.cc.u32 %1, %1, %7;\n\t"
+            "addc.cc.u32 %2, %2, %7;\n\t"
+            "addc.cc.u32 %3, %3, %7;\n\t"
+            "addc.cc.u32 %4, %4, %7;\n\t"
+            "addc.u32 %5, %5, %7;"
+            : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3), "+r"(w4), "+r"(w5)
+            : "r"((unsigned)x), "r"(ext));
+    }
+    unsigned long long v[3] = {((unsigned long long)w1 << 32) | w0, ((unsigned long long)w3 << 32) | w2,
+                               ((unsigned long long)w5 << 32) | w4};
     bool neg = (long long)v[2] < 0;
     if (neg) neg192(v);
     const int E = e[i] + f[j] + 2 * head - bits * (S + 1);
@@ -555,18 +631,45 @@ static int max_slices(int kind) { return kind == 1 ? 24 : 18; }
 
 int ozaki_split(int kind, int by_col, int64_t rows, int64_t cols, const double* X, int S, int* expo, void* D,
                 int64_t lp, cudaStream_t s) {
+    unsigned long long Ch, Cl;
+    b32_bias(S, Ch, Cl);
     if (!by_col) {
         k_row_expo<<<ceil_div(rows, 8), 256, 0, s>>>(rows, cols, X, expo);
         if (int rc = check_launch()) return rc;
-        dim3 g(ceil_div(lp, 128), (unsigned)rows);
-        if (kind == 1) k_slice_rows_f8<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (unsigned char*)D);
-        else k_slice_rows<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (signed char*)D);
+        if (kind == 1) {
+            const int vec = ((uintptr_t)X % 16 == 0) && (cols % 2 == 0);
+            dim3 g(ceil_div(lp, 4 * 128), (unsigned)rows);
+            k_slice_rows_f8<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, Ch, Cl, vec, (unsigned char*)D);
+        } else {
+            dim3 g(ceil_div(lp, 128), (unsigned)rows);
+            k_slice_rows<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (signed char*)D);
+        }
     } else {
-        k_col_expo<<<ceil_div(cols, 128), 128, 0, s>>>(rows, cols, X, expo);
+        MPG_CUDA(cudaMemsetAsync(expo, 0x80, sizeof(int) * (size_t)cols, s));   // COLX_EMPTY
+        if (rows > 0) {
+            dim3 g(ceil_div(cols, 32), ceil_div(rows, COLX_ROWS));
+            k_col_expo<<<g, dim3(32, 8), 0, s>>>(rows, cols, X, expo);
+            if (int rc = check_launch()) return rc;
+        }
+        k_expo_fix<<<ceil_div(cols, 256), 256, 0, s>>>(cols, expo);
         if (int rc = check_launch()) return rc;
-        dim3 g(ceil_div(lp, 128), (unsigned)cols);
-        if (kind == 1) k_slice_cols_f8<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (unsigned char*)D);
-        else k_slice_cols<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (signed char*)D);
+        if (kind == 1) {
+            static bool attr_set[64];
+            int dev = 0;
+            MPG_CUDA(cudaGetDevice(&dev));
+            if (dev < 0 || dev >= 64) return MPGEMM_EUNSUPPORTED;
+            const int smem_max = 24 * SLC_COLS * SLC_PITCH * 4;
+            if (!attr_set[dev]) {
+                MPG_CUDA(cudaFuncSetAttribute(k_slice_cols_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+                attr_set[dev] = true;
+            }
+            dim3 g((unsigned)(lp / SLC_ROWS), ceil_div(cols, SLC_COLS));
+            k_slice_cols_f8<<<g, 128, (size_t)S * SLC_COLS * SLC_PITCH * 4, s>>>(rows, cols, lp, X, expo, S, Ch, Cl,
+                                                                               (unsigned char*)D);
+        } else {
+            dim3 g(ceil_div(lp, 128), (unsigned)cols);
+            k_slice_cols<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (signed char*)D);
+        }
     }
     return check_launch();
 }

@@ -44,6 +44,7 @@ def test_split_bit_exact(S):
     A, B = I.dd_rowcol_scaled(37, 70, 45, seed=11)
     A[:, 5, :] = 0.0
     A[:, 6, 9] = 0.0
+    B[:, :, 7] = 0.0          # an all-zero column: exponent 0
     e, DA = _split(A, S, by_col=False)
     f, DB = _split(B, S, by_col=True)
     assert np.array_equal(e, oracle.ozaki_row_expo(A))

@@ -56,11 +56,16 @@ def _split(X, S, by_col):
     return host(ex), host(D)
 
 
+# l = 71: odd row length (scalar loads); l = 300: several 256-row blocks per
+# column exponent and several 64-row tiles of the transposing column split.
 @pytest.mark.parametrize("S", [4, 22, 24])
-def test_fp8_digits_bit_exact(S):
-    A, B = I.dd_rowcol_scaled(37, 70, 45, seed=31)
+@pytest.mark.parametrize("m,l,n", [(37, 70, 45), (37, 71, 45), (130, 300, 70)])
+def test_fp8_digits_bit_exact(S, m, l, n):
+    A, B = I.dd_rowcol_scaled(m, l, n, seed=31 + l)
     A[:, 5, :] = 0.0
     A[:, 6, 9] = 0.0
+    B[:, :, 7] = 0.0          # an all-zero column: exponent 0
+    B[:, 3, 8] = 0.0
     e, DA = _split(A, S, by_col=False)
     f, DB = _split(B, S, by_col=True)
     assert np.array_equal(e, oracle.ozaki_row_expo(A))
@@ -69,9 +74,10 @@ def test_fp8_digits_bit_exact(S):
     assert np.all(va == np.round(va)) and np.abs(va).max() <= 16
     oa = oracle.ozaki_slice_b32(A, e, S, by_col=False)
     ob = oracle.ozaki_slice_b32(B, f, S, by_col=True)
-    assert np.array_equal(va[:, :, :70], oa.astype(np.float64))
-    assert not va[:, :, 70:].any()
-    assert np.array_equal(vb[:, :, :70], ob.transpose(0, 2, 1).astype(np.float64))
+    assert np.array_equal(va[:, :, :l], oa.astype(np.float64))
+    assert not va[:, :, l:].any()
+    assert np.array_equal(vb[:, :, :l], ob.transpose(0, 2, 1).astype(np.float64))
+    assert not vb[:, :, l:].any()
 
 
 # (512, 16, 1024, 24): 384 tile-level jobs, so every CTA of the persistent
