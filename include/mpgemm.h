@@ -50,8 +50,8 @@ typedef enum {
 typedef enum {
     MPGEMM_OK = 0,
     MPGEMM_EINVAL = -1,       /* bad argument (negative size, NULL, overlap, bad n_min)   */
-    MPGEMM_EUNSUPPORTED = -2, /* valid but not supported (odd size at a Strassen level,   */
-                              /* precision not built)                                      */
+    MPGEMM_EUNSUPPORTED = -2, /* valid but not supported (precision not built, size       */
+                              /* beyond a kernel's limits)                                 */
     MPGEMM_ECUDA = -3,        /* a CUDA call failed; mpgemm_last_cuda_error() has it       */
     MPGEMM_EOVERFLOW = -4,    /* device: a multi-limb exponent left the int32 range        */
     MPGEMM_ETIMEOUT = -5,     /* device: a bounded wait gave up                            */
@@ -68,8 +68,11 @@ typedef enum { MPGEMM_KIND_DD = 0, MPGEMM_KIND_QD = 1, MPGEMM_KIND_MP = 2 } mpge
  *                  n_min <= the format's largest CTA tile (64 DD, 32 QD, 16 MP),
  *                  and otherwise the edge of the super-tile of CTAs that run
  *                  back to back (L2 blocking).  <= 0 selects the default.
- *   strassen_depth levels of Eq 3 (0..4) for MPGEMM_STRASSEN; every dimension
- *                  must be divisible by 2^depth (else MPGEMM_EUNSUPPORTED).
+ *   strassen_depth levels of Eq 3 (0..4) for MPGEMM_STRASSEN.  A dimension
+ *                  that 2^depth does not divide is zero-extended to the next
+ *                  multiple of 2^depth (A and B are read as if padded with
+ *                  zero rows and columns; nothing is copied) and only the
+ *                  m x n block of C is written.
  * Strassen needs workspace (mpgemm_workspace_size); it is taken from the
  * buffer given to mpgemm_set_workspace, else allocated stream-ordered
  * (cudaMallocAsync) and released on the same stream.

@@ -660,6 +660,17 @@ static view_t new_mat(const fmt_t *f, int64_t r, int64_t c) {
     return v;
 }
 
+/* X (r x c) copied into the leading block of an R x C matrix of zeros. */
+static view_t zero_extend(const fmt_t *f, view_t X, int64_t r, int64_t c, int64_t R, int64_t C) {
+    view_t Y = new_mat(f, R, C);
+    for (int64_t i = 0; i < R; i++)
+        for (int64_t j = 0; j < C; j++) {
+            if (i < r && j < c) memcpy(at(f, Y, i, j), at(f, X, i, j), f->esz);
+            else el_zero(f, at(f, Y, i, j));
+        }
+    return Y;
+}
+
 /* Eq 3, Strassen: P1..P7 exactly as written, then
    C11 = ((P1 + P4) - P5) + P7, C12 = P3 + P5, C21 = P2 + P4,
    C22 = ((P1 + P3) - P2) + P6, left to right.  `depth` levels of recursion;
@@ -671,7 +682,7 @@ static void gemm_strassen(const fmt_t *f, int64_t m, int64_t l, int64_t n, view_
         gemm_block(f, m, l, n, A, B, C, n_min, 0, m);
         return;
     }
-    if ((m | l | n) & 1) die("Strassen needs even dimensions at every level");
+    if ((m | l | n) & 1) die("Strassen needs even dimensions at every level (the caller zero-extends)");
     int64_t m2 = m / 2, l2 = l / 2, n2 = n / 2;
     view_t A11 = sub_view(f, A, 0, 0), A12 = sub_view(f, A, 0, l2);
     view_t A21 = sub_view(f, A, m2, 0), A22 = sub_view(f, A, m2, l2);
@@ -776,14 +787,23 @@ static int gemm_any(int kind, int prec_bits, int algo, int64_t m, int64_t l, int
     if (algo == ALGO_STRASSEN) { r0 = 0; r1 = m; }
     if (m == 0 || n == 0 || r1 <= r0) return 0;
     if (n_min <= 0) n_min = 64;
-    if (algo == ALGO_STRASSEN) {
-        for (int d = 0; d < depth; d++)
-            if (((m >> d) | (l >> d) | (n >> d)) & 1) return -2;
-    }
     view_t a = to_aos(&f, A, m, l), b = to_aos(&f, B, l, n), c = new_mat(&f, m, n);
     if (algo == ALGO_SIMPLE) gemm_simple(&f, m, l, n, a, b, c, r0, r1);
     else if (algo == ALGO_BLOCK) gemm_block(&f, m, l, n, a, b, c, n_min, r0, r1);
-    else gemm_strassen(&f, m, l, n, a, b, c, n_min, depth);
+    else {
+        /* Dimensions that 2^depth does not divide: A and B are extended with
+           zero rows and columns to the next multiples of 2^depth, Eq 3 runs
+           on the extended matrices and C is their product's leading m x n
+           block (the paper runs Strassen at odd n without saying how). */
+        int64_t q = (int64_t)1 << (depth > 0 ? depth : 0);
+        int64_t mq = (m + q - 1) / q * q, lq = (l + q - 1) / q * q, nq = (n + q - 1) / q * q;
+        view_t ap = zero_extend(&f, a, m, l, mq, lq), bp = zero_extend(&f, b, l, n, lq, nq);
+        view_t cp = new_mat(&f, mq, nq);
+        gemm_strassen(&f, mq, lq, nq, ap, bp, cp, n_min, depth);
+        for (int64_t i = 0; i < m; i++)
+            memcpy(at(&f, c, i, 0), at(&f, cp, i, 0), (size_t)n * f.esz);
+        free(ap.p); free(bp.p); free(cp.p);
+    }
     from_aos_rows(&f, c, C, m, n, r0, r1);
     free(a.p); free(b.p); free(c.p);
     return 0;

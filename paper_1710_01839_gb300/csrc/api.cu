@@ -99,8 +99,9 @@ int check_common(int64_t m, int64_t l, int64_t n, size_t elem_bytes, const void*
     if ((na && !A) || (nb && !B) || (nc && !C)) return MPGEMM_EINVAL;
     if (overlaps(C, nc, A, na) || overlaps(C, nc, B, nb)) return MPGEMM_EINVAL;
     if (algo == MPGEMM_STRASSEN && depth > 0) {
-        int64_t q = (int64_t)1 << depth;
-        if (m % q || l % q || n % q) return MPGEMM_EUNSUPPORTED;
+        // the level-1 operand and assembly kernels put the rows of a half in grid.y
+        if ((strassen_extended(m, depth) >> 1) > 65535 || (strassen_extended(l, depth) >> 1) > 65535)
+            return MPGEMM_EUNSUPPORTED;
     }
     return MPGEMM_OK;
 }

@@ -41,7 +41,7 @@ void encode_features(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, i
     const double lm = std::log2((double)std::max<int64_t>(m, 1)), ll = std::log2((double)std::max<int64_t>(l, 1)),
                  ln = std::log2((double)std::max<int64_t>(n, 1));
     const int bits = kind == MPGEMM_KIND_DD ? 106 : kind == MPGEMM_KIND_QD ? 212 : prec_bits;
-    int64_t mm = m >> depth, nn = n >> depth;
+    int64_t mm = (m + ((int64_t)1 << depth) - 1) >> depth, nn = (n + ((int64_t)1 << depth) - 1) >> depth;
     int64_t ctas = ((mm + tile - 1) / tile) * ((nn + tile - 1) / tile);
     if (algo == MPGEMM_STRASSEN) ctas *= (int64_t)std::pow(7.0, depth);
     if (algo == MPGEMM_SIMPLE) ctas = ((m + 7) / 8) * ((n + 31) / 32);
@@ -275,8 +275,9 @@ static std::vector<Cand> candidates(int kind, int64_t m, int64_t l, int64_t n) {
     const int tmax = kind == MPGEMM_KIND_DD ? 64 : kind == MPGEMM_KIND_QD ? 32 : 16;
     for (int t = 16; t <= tmax; t *= 2) c.push_back({MPGEMM_BLOCK, t, 0});
     for (int d = 1; d <= 3; d++) {
-        int64_t q = (int64_t)1 << d;
-        if (m % q || l % q || n % q || (m >> d) < 16 || (l >> d) < 16 || (n >> d) < 16) continue;
+        if (strassen_extended(m, d) >> d < 16 || strassen_extended(l, d) >> d < 16 ||
+            strassen_extended(n, d) >> d < 16)
+            continue;
         for (int t = 16; t <= tmax; t *= 2) c.push_back({MPGEMM_STRASSEN, t, d});
     }
     return c;

@@ -11,6 +11,11 @@
 //   C22 = ((P1 + P3) - P2) + P6,
 // left to right, every add rounded in the format.  Leaves are the block
 // algorithm (Eq 2) with block size n_min, all 7^d of them in one launch.
+//
+// Dimensions that 2^d does not divide: A and B are read as if extended with
+// zero rows and columns to the next multiples of 2^d (the level-1 operand
+// kernels return zero outside the caller's matrices, nothing is copied) and
+// the level-1 assembly writes only the leading m x n block of C.
 #include "common.cuh"
 #include "ddqd.cuh"
 #include "kernels.h"
@@ -60,29 +65,45 @@ __device__ __forceinline__ void neg(double* x) {
     for (int q = 0; q < E::P; q++) x[q] = -x[q];
 }
 
-// Children operands: grid (cols/128, rows, parents*7).
+// Element (r, c) of parent p, zero outside its first xr rows and xc columns.
 template <class E>
-__global__ void k_expand(int64_t rows, int64_t cols, View<const double> X, View<double> Y, ChildOps ops) {
+__device__ __forceinline__ void ld_ext(const View<const double>& V, int64_t p, int64_t r, int64_t c, int64_t xr,
+                                       int64_t xc, double* x) {
+    if (r < xr && c < xc) {
+        ld<E>(V, p, r, c, x);
+    } else {
+#pragma unroll
+        for (int q = 0; q < E::P; q++) x[q] = 0.0;
+    }
+}
+
+// Children operands: grid (cols/128, rows, parents*7); the parent holds xr x
+// xc elements (2 rows x 2 cols except where zero-extended).
+template <class E>
+__global__ void k_expand(int64_t rows, int64_t cols, int64_t xr, int64_t xc, View<const double> X, View<double> Y,
+                         ChildOps ops) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = blockIdx.y;
     int z = blockIdx.z, p = z / 7, c = z % 7;
     if (j >= cols) return;
     int qa = ops.qa[c], qb = ops.qb[c], op = ops.op[c];
     double x[E::P], y[E::P], r[E::P];
-    ld<E>(X, p, (qa >> 1) * rows + i, (qa & 1) * cols + j, x);
+    ld_ext<E>(X, p, (qa >> 1) * rows + i, (qa & 1) * cols + j, xr, xc, x);
     if (op == 0) {
         st<E>(Y, z, i, j, x);
         return;
     }
-    ld<E>(X, p, (qb >> 1) * rows + i, (qb & 1) * cols + j, y);
+    ld_ext<E>(X, p, (qb >> 1) * rows + i, (qb & 1) * cols + j, xr, xc, y);
     if (op == 2) neg<E>(y);
     E::add(x, y, r);
     st<E>(Y, z, i, j, r);
 }
 
-// Parent products from children: grid (cols/128, rows, parents).
+// Parent products from children: grid (cols/128, rows, parents); only the
+// first xr rows and xc columns of the parent are written.
 template <class E>
-__global__ void k_combine(int64_t rows, int64_t cols, View<const double> Pc, View<double> Out) {
+__global__ void k_combine(int64_t rows, int64_t cols, int64_t xr, int64_t xc, View<const double> Pc,
+                          View<double> Out) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = blockIdx.y;
     int64_t p = blockIdx.z;
@@ -97,13 +118,14 @@ __global__ void k_combine(int64_t rows, int64_t cols, View<const double> Pc, Vie
     for (int q = 0; q < E::P; q++) n5[q] = -P[4][q];
     E::add(t, n5, u);
     E::add(u, P[6], t);
-    st<E>(Out, p, i, j, t);
+    const bool r0 = i < xr, r1 = rows + i < xr, c0 = j < xc, c1 = cols + j < xc;
+    if (r0 && c0) st<E>(Out, p, i, j, t);
     // C12 = P3 + P5
     E::add(P[2], P[4], t);
-    st<E>(Out, p, i, cols + j, t);
+    if (r0 && c1) st<E>(Out, p, i, cols + j, t);
     // C21 = P2 + P4
     E::add(P[1], P[3], t);
-    st<E>(Out, p, rows + i, j, t);
+    if (r1 && c0) st<E>(Out, p, rows + i, j, t);
     // C22 = ((P1 + P3) - P2) + P6
     E::add(P[0], P[2], t);
     double n2[E::P];
@@ -111,7 +133,7 @@ __global__ void k_combine(int64_t rows, int64_t cols, View<const double> Pc, Vie
     for (int q = 0; q < E::P; q++) n2[q] = -P[1][q];
     E::add(t, n2, u);
     E::add(u, P[5], t);
-    st<E>(Out, p, rows + i, cols + j, t);
+    if (r1 && c1) st<E>(Out, p, rows + i, cols + j, t);
 }
 
 // ---------------------------------------------------------------- multi-limb element ops
@@ -134,20 +156,27 @@ __device__ __forceinline__ void stm(const View<uint32_t>& V, int64_t z, int64_t 
 }
 
 template <int W>
-__global__ void k_expand_mp(int64_t rows, int64_t cols, View<const uint32_t> X, View<uint32_t> Y, ChildOps ops,
-                            unsigned* status) {
+__device__ __forceinline__ void ldm_ext(const View<const uint32_t>& V, int64_t p, int64_t r, int64_t c, int64_t xr,
+                                        int64_t xc, MPV<W>& v) {
+    if (r < xr && c < xc) ldm<W>(V, p, r, c, v);
+    else mp_set_zero(v, 0u);   // +0, the extension's value
+}
+
+template <int W>
+__global__ void k_expand_mp(int64_t rows, int64_t cols, int64_t xr, int64_t xc, View<const uint32_t> X,
+                            View<uint32_t> Y, ChildOps ops, unsigned* status) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = blockIdx.y;
     int z = blockIdx.z, p = z / 7, c = z % 7;
     if (j >= cols) return;
     int qa = ops.qa[c], qb = ops.qb[c], op = ops.op[c];
     MPV<W> x, y, r;
-    ldm<W>(X, p, (qa >> 1) * rows + i, (qa & 1) * cols + j, x);
+    ldm_ext<W>(X, p, (qa >> 1) * rows + i, (qa & 1) * cols + j, xr, xc, x);
     if (op == 0) {
         stm<W>(Y, z, i, j, x);
         return;
     }
-    ldm<W>(X, p, (qb >> 1) * rows + i, (qb & 1) * cols + j, y);
+    ldm_ext<W>(X, p, (qb >> 1) * rows + i, (qb & 1) * cols + j, xr, xc, y);
     if (op == 2) y.f ^= 1u;
     unsigned sts = 0u;
     mp_add<W>(x, y, r, sts);
@@ -156,12 +185,13 @@ __global__ void k_expand_mp(int64_t rows, int64_t cols, View<const uint32_t> X, 
 }
 
 template <int W>
-__global__ void k_combine_mp(int64_t rows, int64_t cols, View<const uint32_t> Pc, View<uint32_t> Out,
-                             unsigned* status) {
+__global__ void k_combine_mp(int64_t rows, int64_t cols, int64_t xr, int64_t xc, View<const uint32_t> Pc,
+                             View<uint32_t> Out, unsigned* status) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = blockIdx.y;
     int64_t p = blockIdx.z;
     if (j >= cols) return;
+    const bool r0 = i < xr, r1 = rows + i < xr, c0 = j < xc, c1 = cols + j < xc;
     unsigned sts = 0u;
     MPV<W> a, b, t, u;
     // C11 = ((P1 + P4) - P5) + P7
@@ -173,17 +203,17 @@ __global__ void k_combine_mp(int64_t rows, int64_t cols, View<const uint32_t> Pc
     mp_add<W>(t, b, u, sts);
     ldm<W>(Pc, p * 7 + 6, i, j, b);
     mp_add<W>(u, b, t, sts);
-    stm<W>(Out, p, i, j, t);
+    if (r0 && c0) stm<W>(Out, p, i, j, t);
     // C12 = P3 + P5
     ldm<W>(Pc, p * 7 + 2, i, j, a);
     ldm<W>(Pc, p * 7 + 4, i, j, b);
     mp_add<W>(a, b, t, sts);
-    stm<W>(Out, p, i, cols + j, t);
+    if (r0 && c1) stm<W>(Out, p, i, cols + j, t);
     // C21 = P2 + P4
     ldm<W>(Pc, p * 7 + 1, i, j, a);
     ldm<W>(Pc, p * 7 + 3, i, j, b);
     mp_add<W>(a, b, t, sts);
-    stm<W>(Out, p, rows + i, j, t);
+    if (r1 && c0) stm<W>(Out, p, rows + i, j, t);
     // C22 = ((P1 + P3) - P2) + P6
     ldm<W>(Pc, p * 7 + 0, i, j, a);
     ldm<W>(Pc, p * 7 + 2, i, j, b);
@@ -193,7 +223,7 @@ __global__ void k_combine_mp(int64_t rows, int64_t cols, View<const uint32_t> Pc
     mp_add<W>(t, b, u, sts);
     ldm<W>(Pc, p * 7 + 5, i, j, b);
     mp_add<W>(u, b, t, sts);
-    stm<W>(Out, p, rows + i, cols + j, t);
+    if (r1 && c1) stm<W>(Out, p, rows + i, cols + j, t);
     if (sts) atomicOr(status, sts);
 }
 
@@ -212,7 +242,16 @@ int fill_u32(uint32_t* p, size_t count, uint32_t value, cudaStream_t s) {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// x rounded up to a multiple of 2^depth (the zero-extended size).
+int64_t strassen_extended(int64_t x, int depth) {
+    const int64_t q = (int64_t)1 << depth;
+    return (x + q - 1) / q * q;
+}
+
 size_t strassen_workspace_bytes(size_t eb, int64_t m, int64_t l, int64_t n, int depth) {
+    m = strassen_extended(m, depth);
+    l = strassen_extended(l, depth);
+    n = strassen_extended(n, depth);
     size_t total = 0, nodes = 1;
     for (int k = 1; k <= depth; k++) {
         nodes *= 7;
@@ -266,36 +305,40 @@ int strassen_ddqd_ws(int kind, int64_t m, int64_t l, int64_t n, View<const doubl
                      View<double> C, int n_min, int depth, void* ws, size_t ws_bytes, cudaStream_t s) {
     const int P = kind == MPGEMM_KIND_DD ? 2 : 4;
     const size_t eb = sizeof(double) * P;
+    const int64_t mq = strassen_extended(m, depth), lq = strassen_extended(l, depth), nq = strassen_extended(n, depth);
     Levels<double> L;
-    int rc = carve<double>((char*)ws, ws_bytes, eb, P, m, l, n, depth, L);
+    int rc = carve<double>((char*)ws, ws_bytes, eb, P, mq, lq, nq, depth, L);
     if (rc) return rc;
     const ChildOps ao = a_side_ops(), bo = b_side_ops();
     unsigned parents = 1;
     for (int k = 1; k <= depth; k++) {
-        int64_t mk = m >> k, lk = l >> k, nk = n >> k;
+        int64_t mk = mq >> k, lk = lq >> k, nk = nq >> k;
         View<const double> pa = k == 1 ? A : cview(L.SA[k - 1]);
         View<const double> pb = k == 1 ? B : cview(L.SB[k - 1]);
+        // level 1 reads the caller's m x l and l x n matrices, deeper levels whole parents
+        const int64_t ar = k == 1 ? m : 2 * mk, ac = k == 1 ? l : 2 * lk, bc = k == 1 ? n : 2 * nk;
         dim3 ga(ceil_div(lk, 128), (unsigned)mk, parents * 7), gb(ceil_div(nk, 128), (unsigned)lk, parents * 7);
         if (kind == MPGEMM_KIND_DD) {
-            k_expand<DDE><<<ga, 128, 0, s>>>(mk, lk, pa, L.SA[k], ao);
-            k_expand<DDE><<<gb, 128, 0, s>>>(lk, nk, pb, L.SB[k], bo);
+            k_expand<DDE><<<ga, 128, 0, s>>>(mk, lk, ar, ac, pa, L.SA[k], ao);
+            k_expand<DDE><<<gb, 128, 0, s>>>(lk, nk, ac, bc, pb, L.SB[k], bo);
         } else {
-            k_expand<QDE><<<ga, 128, 0, s>>>(mk, lk, pa, L.SA[k], ao);
-            k_expand<QDE><<<gb, 128, 0, s>>>(lk, nk, pb, L.SB[k], bo);
+            k_expand<QDE><<<ga, 128, 0, s>>>(mk, lk, ar, ac, pa, L.SA[k], ao);
+            k_expand<QDE><<<gb, 128, 0, s>>>(lk, nk, ac, bc, pb, L.SB[k], bo);
         }
         if ((rc = check_launch())) return rc;
         parents *= 7;
     }
-    rc = ddqd_gemm(kind, MPGEMM_BLOCK, m >> depth, l >> depth, n >> depth, parents, cview(L.SA[depth]),
+    rc = ddqd_gemm(kind, MPGEMM_BLOCK, mq >> depth, lq >> depth, nq >> depth, parents, cview(L.SA[depth]),
                    cview(L.SB[depth]), L.PR[depth], n_min, s);
     if (rc) return rc;
     for (int k = depth; k >= 1; k--) {
         parents /= 7;
-        int64_t mk = m >> k, nk = n >> k;
+        int64_t mk = mq >> k, nk = nq >> k;
         View<double> out = k == 1 ? C : L.PR[k - 1];
+        const int64_t xr = k == 1 ? m : 2 * mk, xc = k == 1 ? n : 2 * nk;
         dim3 g(ceil_div(nk, 128), (unsigned)mk, parents);
-        if (kind == MPGEMM_KIND_DD) k_combine<DDE><<<g, 128, 0, s>>>(mk, nk, cview(L.PR[k]), out);
-        else k_combine<QDE><<<g, 128, 0, s>>>(mk, nk, cview(L.PR[k]), out);
+        if (kind == MPGEMM_KIND_DD) k_combine<DDE><<<g, 128, 0, s>>>(mk, nk, xr, xc, cview(L.PR[k]), out);
+        else k_combine<QDE><<<g, 128, 0, s>>>(mk, nk, xr, xc, cview(L.PR[k]), out);
         if ((rc = check_launch())) return rc;
     }
     return MPGEMM_OK;
@@ -308,30 +351,33 @@ static int strassen_mp_w(int64_t m, int64_t l, int64_t n, View<const uint32_t> A
     const size_t eb = sizeof(uint32_t) * P;
     unsigned* status = device_status_ptr();
     if (!status) return MPGEMM_ECUDA;
+    const int64_t mq = strassen_extended(m, depth), lq = strassen_extended(l, depth), nq = strassen_extended(n, depth);
     Levels<uint32_t> L;
-    int rc = carve<uint32_t>((char*)ws, ws_bytes, eb, P, m, l, n, depth, L);
+    int rc = carve<uint32_t>((char*)ws, ws_bytes, eb, P, mq, lq, nq, depth, L);
     if (rc) return rc;
     const ChildOps ao = a_side_ops(), bo = b_side_ops();
     unsigned parents = 1;
     for (int k = 1; k <= depth; k++) {
-        int64_t mk = m >> k, lk = l >> k, nk = n >> k;
+        int64_t mk = mq >> k, lk = lq >> k, nk = nq >> k;
         View<const uint32_t> pa = k == 1 ? A : cview(L.SA[k - 1]);
         View<const uint32_t> pb = k == 1 ? B : cview(L.SB[k - 1]);
+        const int64_t ar = k == 1 ? m : 2 * mk, ac = k == 1 ? l : 2 * lk, bc = k == 1 ? n : 2 * nk;
         dim3 ga(ceil_div(lk, 128), (unsigned)mk, parents * 7), gb(ceil_div(nk, 128), (unsigned)lk, parents * 7);
-        k_expand_mp<W><<<ga, 128, 0, s>>>(mk, lk, pa, L.SA[k], ao, status);
-        k_expand_mp<W><<<gb, 128, 0, s>>>(lk, nk, pb, L.SB[k], bo, status);
+        k_expand_mp<W><<<ga, 128, 0, s>>>(mk, lk, ar, ac, pa, L.SA[k], ao, status);
+        k_expand_mp<W><<<gb, 128, 0, s>>>(lk, nk, ac, bc, pb, L.SB[k], bo, status);
         if ((rc = check_launch())) return rc;
         parents *= 7;
     }
-    rc = mp_gemm(W, MPGEMM_BLOCK, m >> depth, l >> depth, n >> depth, parents, cview(L.SA[depth]),
+    rc = mp_gemm(W, MPGEMM_BLOCK, mq >> depth, lq >> depth, nq >> depth, parents, cview(L.SA[depth]),
                  cview(L.SB[depth]), L.PR[depth], n_min, s);
     if (rc) return rc;
     for (int k = depth; k >= 1; k--) {
         parents /= 7;
-        int64_t mk = m >> k, nk = n >> k;
+        int64_t mk = mq >> k, nk = nq >> k;
         View<uint32_t> out = k == 1 ? C : L.PR[k - 1];
+        const int64_t xr = k == 1 ? m : 2 * mk, xc = k == 1 ? n : 2 * nk;
         dim3 g(ceil_div(nk, 128), (unsigned)mk, parents);
-        k_combine_mp<W><<<g, 128, 0, s>>>(mk, nk, cview(L.PR[k]), out, status);
+        k_combine_mp<W><<<g, 128, 0, s>>>(mk, nk, xr, xc, cview(L.PR[k]), out, status);
         if ((rc = check_launch())) return rc;
     }
     return MPGEMM_OK;

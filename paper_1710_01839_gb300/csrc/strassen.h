@@ -13,6 +13,9 @@
 
 namespace mpg {
 
+// x rounded up to a multiple of 2^depth: Strassen's zero-extended size.
+int64_t strassen_extended(int64_t x, int depth);
+// Workspace of Strassen at the zero-extended sizes.
 size_t strassen_workspace_bytes(size_t elem_bytes, int64_t m, int64_t l, int64_t n, int depth);
 
 int strassen_ddqd(int kind, int64_t m, int64_t l, int64_t n, View<const double> A, View<const double> B,

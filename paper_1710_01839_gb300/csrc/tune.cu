@@ -212,8 +212,10 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
     }
     for (int d = 1; d <= 3; d++) {
         rep->strassen_ms[d] = NAN;
-        int64_t q = (int64_t)1 << d;
-        if (m % q || l % q || n % q || (m >> d) < 16 || (n >> d) < 16 || (l >> d) < 16) continue;
+        // leaves of the zero-extended problem at least 16 on every side
+        if (strassen_extended(m, d) >> d < 16 || strassen_extended(l, d) >> d < 16 ||
+            strassen_extended(n, d) >> d < 16)
+            continue;
         rc = time_it(P, MPGEMM_STRASSEN, nm, d, m, reps, &rep->strassen_ms[d]);
         if (rc) return rc;
         if (rep->strassen_ms[d] < best_ms) {

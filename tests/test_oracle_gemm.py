@@ -87,10 +87,38 @@ def test_strassen_equals_simple_on_integers(fmt, depth):
     assert np.array_equal(Cs, want)
 
 
-def test_strassen_rejects_odd_dimensions():
-    A, B = I.dd_random(6, 6, 1), I.dd_random(6, 6, 2)
-    with pytest.raises(ValueError):
-        oracle.dd_gemm(A, B, algo="strassen", depth=2)
+# Dimensions that 2^depth does not divide run on zero-extended matrices: on
+# integer matrices every intermediate is still exact, so the result is the
+# exact product, bit-identical to Eq 1, at any depth.
+@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("fmt", ["dd", "qd", "mp128"])
+@pytest.mark.parametrize("m,l,n", [(13, 21, 7), (1, 5, 3), (9, 8, 17)])
+def test_strassen_odd_dimensions_equal_simple_on_integers(fmt, depth, m, l, n):
+    a = I.int_matrix(m, l, 40 + depth)
+    b = I.int_matrix(l, n, 50 + depth)
+    if fmt == "dd":
+        A, B, run, kw, want = I.ints_to_dd(a), I.ints_to_dd(b), oracle.dd_gemm, {}, I.ints_to_dd(a @ b)
+    elif fmt == "qd":
+        A, B, run, kw, want = I.ints_to_qd(a), I.ints_to_qd(b), oracle.qd_gemm, {}, I.ints_to_qd(a @ b)
+    else:
+        A, B, run, kw = I.ints_to_mp(a, 4), I.ints_to_mp(b, 4), oracle.mp_gemm, {"prec_bits": 128}
+        want = I.ints_to_mp(a @ b, 4)
+    Ct = run(A, B, algo="strassen", n_min=2, depth=depth, **kw)
+    assert np.array_equal(Ct, want)
+    assert np.array_equal(Ct, run(A, B, algo="simple", **kw))
+
+
+def test_dd_strassen_odd_dimensions_within_bound_of_exact():
+    m, l, n = 11, 19, 13
+    A, B = I.dd_random(m, l, 61, 20), I.dd_random(l, n, 62, 20)
+    C = oracle.dd_gemm(A, B, algo="strassen", n_min=2, depth=2)
+    Cx, _ = _exact_product(A, B)
+    amax = max(abs(value(A[:, i, k])) for i in range(m) for k in range(l))
+    bmax = max(abs(value(B[:, k, j])) for k in range(l) for j in range(n))
+    tol = Fraction(2) ** -96 * 20 * amax * bmax   # 20: the zero-extended inner dimension
+    for i in range(m):
+        for j in range(n):
+            assert abs(value(C[:, i, j]) - Cx[i][j]) <= tol
 
 
 # ---------------------------------------------------------------- error bounds vs exact
