@@ -260,17 +260,19 @@ int mpgemm_set_workspace(void* dev_ptr, size_t bytes);
 /* ---------------------------------------------------------------------------
  * Tuning (Section 3).  mpgemm_tune runs the paper's procedure on the given
  * operands (device pointers in the format of `kind`; C is overwritten):
- *   1. for each n_min in {16, 32, 64, 128, 256} time the block algorithm on
- *      the first r rows of A against all of B, r = mpgemm_sample_rows(),
- *      and predict the full time by scaling T_sample with the ratio of
- *      per-SM rounds of CTAs, ceil(CTAs(m) / SMs) / ceil(CTAs(r) / SMs)
- *      (the paper's m / r when both runs are whole rounds);
+ *   1. for each n_min in {16, 32, 64, 128, 256, 512} time the block
+ *      algorithm on the first r rows of A against all of B, r =
+ *      mpgemm_sample_rows(), and predict the full time by scaling T_sample
+ *      with the ratio of per-SM rounds of CTAs, ceil(CTAs(m) / SMs) /
+ *      ceil(CTAs(r) / SMs) (the paper's m / r when both runs are whole
+ *      rounds); SMs = mpgemm_stream_sms(stream);
  *   2. keep the n_min with the smallest prediction;
  *   3. time simple, block(n_min) and Strassen depths 1..3 (leaves at n_min)
  *      and report the fastest.
  * Timings are medians of 3 event-timed runs (1 with MPGEMM_TUNE_QUICK).
  * With MPGEMM_TUNE_REMEMBER the choice is stored for this (kind, prec_bits,
- * m, l, n) and used by MPGEMM_AUTO.  Synchronous; returns MPGEMM_OK or an
+ * m, l, n, SMs of the stream) and used by MPGEMM_AUTO on streams with as
+ * many SMs.  Synchronous; returns MPGEMM_OK or an
  * error status.
  * ------------------------------------------------------------------------- */
 enum {
@@ -296,7 +298,8 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
                 int flags, void* stream, mpgemm_tune_report* report);
 /* Forget every remembered choice. */
 int mpgemm_tune_forget(void);
-/* The (algo, n_min, depth) MPGEMM_AUTO would use for this problem. */
+/* The (algo, n_min, depth) MPGEMM_AUTO would use for this problem on the
+   whole device. */
 int mpgemm_auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int* algo, int* n_min,
                        int* depth);
 /* The paper's prediction (Fig. 1): full time = sampled time * m / rows. */
@@ -310,6 +313,34 @@ int64_t mpgemm_sample_rows(int kind, int64_t m, int64_t n, int n_min, int num_sm
 /* Synchronise `stream`, then read and clear the current device's status
    word: MPGEMM_OK, MPGEMM_EOVERFLOW or MPGEMM_ETIMEOUT. */
 int mpgemm_stream_status(void* stream);
+
+/* ---------------------------------------------------------------------------
+ * SM partitions (the GPU counterpart of the paper's thread counts, Section
+ * 4: every algorithm is timed with 1, 2, 4 and 8 threads).
+ *   mpgemm_partition_create   a CUDA green context holding at least num_sms
+ *                             SMs (rounded up to the device's partition
+ *                             granularity; *sms_out receives the count) and a
+ *                             non-blocking stream in it, returned in *stream.
+ *                             Every library call issued on that stream runs
+ *                             on those SMs only; device memory is shared with
+ *                             the rest of the process.  MPGEMM_EUNSUPPORTED
+ *                             when the driver has no green contexts,
+ *                             MPGEMM_EINVAL for num_sms <= 0 or above the
+ *                             device's SM count.
+ *   mpgemm_partition_destroy  synchronises the stream, destroys it and its
+ *                             green context (MPGEMM_EINVAL for a stream not
+ *                             made by mpgemm_partition_create).
+ *   mpgemm_stream_sms         SMs the stream's kernels run on: the
+ *                             partition's count, else the device's.  The
+ *                             tuner's rounds model, remembered choices, the
+ *                             cost model's features and the persistent
+ *                             tcgen05 kernel's grid use it.
+ * A partition only restricts where this process's kernels run; it changes
+ * no device setting.
+ * ------------------------------------------------------------------------- */
+int mpgemm_partition_create(int num_sms, void** stream, int* sms_out);
+int mpgemm_partition_destroy(void* stream);
+int mpgemm_stream_sms(void* stream);
 const char* mpgemm_strerror(int status);
 /* The cudaError_t of the last MPGEMM_ECUDA on this host thread. */
 int mpgemm_last_cuda_error(void);

@@ -18,7 +18,7 @@ import os
 from ._lib import (ALGO, KIND, MpgemmError, check, lib, lib_path)  # noqa: F401
 
 __all__ = ["gemm_dd", "gemm_qd", "gemm_mp", "workspace_size", "set_workspace", "stream_status", "strerror",
-           "MpgemmError", "ALGO", "KIND", "lib", "lib_path"]
+           "Partition", "MpgemmError", "ALGO", "KIND", "lib", "lib_path"]
 
 
 def _torch():
@@ -117,3 +117,31 @@ def stream_status(stream=None):
 
 def strerror(status):
     return lib().mpgemm_strerror(int(status)).decode()
+
+
+class Partition:
+    """A stream whose kernels run on (at least) `num_sms` SMs: a CUDA green
+    context made by mpgemm_partition_create.  `stream` is a
+    torch.cuda.ExternalStream to pass as the `stream` argument of this
+    module's calls; `sms` is the partition's actual SM count.  Synchronise
+    with stream_status(p.stream); close() (or leaving a `with` block)
+    synchronises and destroys it."""
+
+    def __init__(self, num_sms):
+        torch = _torch()
+        h, n = ctypes.c_void_p(), ctypes.c_int()
+        check(lib().mpgemm_partition_create(int(num_sms), ctypes.byref(h), ctypes.byref(n)))
+        self.handle = h.value
+        self.sms = n.value
+        self.stream = torch.cuda.ExternalStream(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            h, self.handle = self.handle, None
+            check(lib().mpgemm_partition_destroy(ctypes.c_void_p(h)))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

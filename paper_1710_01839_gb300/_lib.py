@@ -35,6 +35,9 @@ SIGNATURES = {
     "mpgemm_workspace_size": (_SZ, [_I, _I, _I64, _I64, _I64, _I, _I]),
     "mpgemm_set_workspace": (_I, [_P, _SZ]),
     "mpgemm_stream_status": (_I, [_P]),
+    "mpgemm_partition_create": (_I, [_I, _P, _P]),
+    "mpgemm_partition_destroy": (_I, [_P]),
+    "mpgemm_stream_sms": (_I, [_P]),
     "mpgemm_strerror": (ctypes.c_char_p, [_I]),
     "mpgemm_last_cuda_error": (_I, []),
     "mpgemm_version": (_I, []),

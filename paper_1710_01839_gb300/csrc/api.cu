@@ -125,11 +125,12 @@ static int ddqd_entry(int kind, int64_t m, int64_t l, int64_t n, const double* A
     int rc = check_common(m, l, n, sizeof(double) * P, A, B, C, algo, n_min, depth);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    PartitionScope pscope(s);
     if (m == 0 || n == 0) return MPGEMM_OK;
     if (l == 0) return zero_result<double>(kind, m, n, P, C, s);
     if (algo == MPGEMM_AUTO) {
         Choice ch;
-        rc = auto_choice(kind, 0, m, l, n, &ch);
+        rc = auto_choice(kind, 0, m, l, n, stream_sms(s), &ch);
         if (rc) return rc;
         algo = ch.algo;
         n_min = ch.n_min;
@@ -150,11 +151,12 @@ static int mp_entry(int64_t m, int64_t l, int64_t n, int prec_bits, const uint32
     int rc = check_common(m, l, n, sizeof(uint32_t) * (size_t)(2 + w), A, B, C, algo, n_min, depth);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    PartitionScope pscope(s);
     if (m == 0 || n == 0) return MPGEMM_OK;
     if (l == 0) return zero_result<uint32_t>(MPGEMM_KIND_MP, m, n, 2 + w, C, s);
     if (algo == MPGEMM_AUTO) {
         Choice ch;
-        rc = auto_choice(MPGEMM_KIND_MP, prec_bits, m, l, n, &ch);
+        rc = auto_choice(MPGEMM_KIND_MP, prec_bits, m, l, n, stream_sms(s), &ch);
         if (rc) return rc;
         algo = ch.algo;
         n_min = ch.n_min;
@@ -211,6 +213,7 @@ int mpgemm_set_workspace(void* dev_ptr, size_t bytes) {
 }
 
 int mpgemm_stream_status(void* stream) {
+    PartitionScope pscope((cudaStream_t)stream);
     MPG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     unsigned* p = device_status_ptr();
     if (!p) return MPGEMM_ECUDA;

@@ -41,6 +41,19 @@ enum : unsigned {
 };
 
 unsigned* device_status_ptr();   // address of this device's status word
+int stream_sms(cudaStream_t s);   // SMs the stream's kernels run on (an SM partition's, else the device's)
+// Makes an SM partition's context current while a call issues work on the
+// partition's stream (no-op for other streams).
+class PartitionScope {
+   public:
+    explicit PartitionScope(cudaStream_t s);
+    ~PartitionScope();
+    PartitionScope(const PartitionScope&) = delete;
+    PartitionScope& operator=(const PartitionScope&) = delete;
+
+   private:
+    bool pushed_ = false;
+};
 
 // Launch-shape helpers.
 __host__ __device__ inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }

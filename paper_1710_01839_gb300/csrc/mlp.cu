@@ -283,7 +283,7 @@ static std::vector<Cand> candidates(int kind, int64_t m, int64_t l, int64_t n) {
     return c;
 }
 
-bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, Choice* out) {
+bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out) {
     {
         std::lock_guard<std::mutex> lk(g_mmu);
         if (!g_model.ready) return false;
@@ -291,7 +291,7 @@ bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n,
     std::vector<Cand> cs = candidates(kind, m, l, n);
     std::vector<float> F(cs.size() * NF), T(cs.size());
     for (size_t i = 0; i < cs.size(); i++)
-        encode_features(kind, prec_bits, m, l, n, cs[i].algo, cs[i].tile, cs[i].depth, g_model.sms, &F[i * NF]);
+        encode_features(kind, prec_bits, m, l, n, cs[i].algo, cs[i].tile, cs[i].depth, sms, &F[i * NF]);
     if (predict(F.data(), (int)cs.size(), T.data()) != MPGEMM_OK) return false;
     size_t best = (size_t)(std::min_element(T.begin(), T.end()) - T.begin());
     out->algo = cs[best].algo;

@@ -654,15 +654,9 @@ int ozaki_split(int kind, int by_col, int64_t rows, int64_t cols, const double* 
         k_expo_fix<<<ceil_div(cols, 256), 256, 0, s>>>(cols, expo);
         if (int rc = check_launch()) return rc;
         if (kind == 1) {
-            static bool attr_set[64];
-            int dev = 0;
-            MPG_CUDA(cudaGetDevice(&dev));
-            if (dev < 0 || dev >= 64) return MPGEMM_EUNSUPPORTED;
+            // set on every call: the current context may be an SM partition's (partition.cu)
             const int smem_max = 24 * SLC_COLS * SLC_PITCH * 4;
-            if (!attr_set[dev]) {
-                MPG_CUDA(cudaFuncSetAttribute(k_slice_cols_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
-                attr_set[dev] = true;
-            }
+            MPG_CUDA(cudaFuncSetAttribute(k_slice_cols_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
             dim3 g((unsigned)(lp / SLC_ROWS), ceil_div(cols, SLC_COLS));
             k_slice_cols_f8<<<g, 128, (size_t)S * SLC_COLS * SLC_PITCH * 4, s>>>(rows, cols, lp, X, expo, S, Ch, Cl,
                                                                                (unsigned char*)D);
@@ -677,14 +671,8 @@ int ozaki_split(int kind, int by_col, int64_t rows, int64_t cols, const double* 
 template <bool F8>
 static int levels_launch(int64_t m, int64_t n, int64_t lp, int S, const void* DA, const void* DB, int* Lv,
                          cudaStream_t s) {
-    static bool attr_set[64];
-    int dev = 0;
-    MPG_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return MPGEMM_EUNSUPPORTED;
-    if (!attr_set[dev]) {
-        MPG_CUDA(cudaFuncSetAttribute(k_ozaki_levels<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-        attr_set[dev] = true;
-    }
+    // set on every call: the current context may be an SM partition's (partition.cu)
+    MPG_CUDA(cudaFuncSetAttribute(k_ozaki_levels<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     unsigned tm = ceil_div(m, OZ_BM), tn = ceil_div(n, OZ_BN);
     ProfScope ps(s);
     k_ozaki_levels<F8><<<tm * tn * (unsigned)S, OZ_THREADS, OZ_SMEM, s>>>(
@@ -755,6 +743,7 @@ int mpgemm_dd_ozaki_ex(int64_t m, int64_t l, int64_t n, const double* A, const d
     }
     if (m > 65535 || n > 65535) return MPGEMM_EUNSUPPORTED;   // grid.y limits of the slice kernels
     cudaStream_t s = (cudaStream_t)stream;
+    PartitionScope pscope(s);
     if (m == 0 || n == 0) return MPGEMM_OK;
     if (l == 0) {
         MPG_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * 2 * (size_t)(m * n), s));
@@ -783,6 +772,7 @@ int mpgemm_ozaki_split_ex(int digit_kind, int by_col, int64_t rows, int64_t cols
     if (rows > 65535 && !by_col) return MPGEMM_EUNSUPPORTED;
     if (cols > 65535 && by_col) return MPGEMM_EUNSUPPORTED;
     int64_t inner = by_col ? rows : cols;
+    PartitionScope pscope((cudaStream_t)stream);
     return ozaki_split(digit_kind, by_col, rows, cols, X, S, expo, digits, ozaki_padded_k(inner), (cudaStream_t)stream);
 }
 
@@ -798,6 +788,7 @@ int mpgemm_ozaki_levels_ex(int digit_kind, int64_t m, int64_t l, int64_t n, int 
     if (m <= 0 || l <= 0 || n <= 0 || !DA || !DB || !levels || S < 1 || S > max_slices(digit_kind))
         return MPGEMM_EINVAL;
     if (digit_kind == 1 && l > 65536) return MPGEMM_EUNSUPPORTED;
+    PartitionScope pscope((cudaStream_t)stream);
     return ozaki_levels(digit_kind, m, n, ozaki_padded_k(l), S, DA, DB, levels, (cudaStream_t)stream);
 }
 

@@ -377,20 +377,13 @@ int tc_levels(int64_t m, int64_t n, int64_t lp, int S, const void* DA, const voi
     int rc;
     if ((rc = digit_map(&mA, DA, m, lp, S, TC_M))) return rc;
     if ((rc = digit_map(&mB, DB, n, lp, S, TC_N))) return rc;
-    static int sms[64];
-    static bool attr_set[64];
-    int devno = 0;
-    MPG_CUDA(cudaGetDevice(&devno));
-    if (devno < 0 || devno >= 64) return MPGEMM_EUNSUPPORTED;
-    if (!attr_set[devno]) {
-        MPG_CUDA(cudaFuncSetAttribute(k_levels_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-        MPG_CUDA(cudaDeviceGetAttribute(&sms[devno], cudaDevAttrMultiProcessorCount, devno));
-        attr_set[devno] = true;
-    }
+    // set on every call: the current context may be an SM partition's (partition.cu)
+    MPG_CUDA(cudaFuncSetAttribute(k_levels_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    const int sms = stream_sms(s);   // one persistent CTA per SM of the stream's partition
     const int tiles_m = (int)ceil_div(m, TC_M), tiles_n = (int)ceil_div(n, TC_N);
     const int tiles = tiles_m * tiles_n;
     const int64_t jobs = (int64_t)tiles * S;
-    const int grid = (int)(jobs < sms[devno] ? jobs : sms[devno]);
+    const int grid = (int)(jobs < sms ? jobs : sms);
     const int vec = ((uintptr_t)Lv % 16 == 0) && (n % 4 == 0);
     {
         ProfScope ps(s);

@@ -30,23 +30,25 @@
 
 namespace mpg {
 
-using Key = std::tuple<int, int, int64_t, int64_t, int64_t>;
+// (kind, bits, m, l, n, SMs): choices are remembered per SM count, so a run
+// on an SM partition (partition.cu) keeps its own.
+using Key = std::tuple<int, int, int64_t, int64_t, int64_t, int>;
 static std::mutex g_tmu;
 static std::map<Key, Choice> g_table;
 
 // Installed cost model (mlp.cu); returns false when none is installed.
-bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, Choice* out);
+bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out);
 
-int auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, Choice* out) {
+int auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out) {
     {
         std::lock_guard<std::mutex> lk(g_tmu);
-        auto it = g_table.find(Key(kind, prec_bits, m, l, n));
+        auto it = g_table.find(Key(kind, prec_bits, m, l, n, sms));
         if (it != g_table.end()) {
             *out = it->second;
             return MPGEMM_OK;
         }
     }
-    if (cost_model_choice(kind, prec_bits, m, l, n, out)) return MPGEMM_OK;
+    if (cost_model_choice(kind, prec_bits, m, l, n, sms, out)) return MPGEMM_OK;
     out->algo = MPGEMM_BLOCK;
     out->n_min = default_n_min(kind);
     out->depth = 0;
@@ -166,15 +168,15 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
     if (kind == MPGEMM_KIND_MP && (prec_bits <= 0 || prec_bits % 32)) return MPGEMM_EINVAL;
     auto t_start = std::chrono::steady_clock::now();
     Problem P{kind, kind == MPGEMM_KIND_MP ? prec_bits : 0, m, l, n, A, B, C, (cudaStream_t)stream};
-    int dev = 0, sms = 0;
-    MPG_CUDA(cudaGetDevice(&dev));
-    MPG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PartitionScope pscope(P.s);
+    const int sms = stream_sms(P.s);   // the partition's SMs when the stream has one
     const int reps = (flags & MPGEMM_TUNE_QUICK) ? 1 : 3;
     memset(rep, 0, sizeof *rep);
-    static const int cands[] = {16, 32, 64, 128, 256};
+    static const int cands[] = {16, 32, 64, 128, 256, 512};
+    constexpr int NC = (int)(sizeof cands / sizeof cands[0]);
     int best = -1;
     double best_pred = 0;
-    for (int c = 0; c < 5; c++) {
+    for (int c = 0; c < NC; c++) {
         int nm = cands[c];
         int64_t r = mpgemm_sample_rows(kind, m, n, nm, sms);
         double ms = 0;
@@ -194,7 +196,7 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
             best_pred = rep->cand_pred_ms[c];
         }
     }
-    rep->n_cand = 5;
+    rep->n_cand = NC;
     const int nm = cands[best];
     int rc;
     rep->simple_ms = NAN;
@@ -229,7 +231,7 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
     rep->best_ms = best_ms;
     if (flags & MPGEMM_TUNE_REMEMBER) {
         std::lock_guard<std::mutex> lk(g_tmu);
-        g_table[Key(kind, P.prec_bits, m, l, n)] = ch;
+        g_table[Key(kind, P.prec_bits, m, l, n, sms)] = ch;
     }
     rep->tuning_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return MPGEMM_OK;
@@ -243,7 +245,7 @@ int mpgemm_tune_forget(void) {
 
 int mpgemm_auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int* algo, int* n_min, int* depth) {
     Choice c;
-    int rc = auto_choice(kind, prec_bits, m, l, n, &c);
+    int rc = auto_choice(kind, prec_bits, m, l, n, stream_sms(nullptr), &c);
     if (rc) return rc;
     if (algo) *algo = c.algo;
     if (n_min) *n_min = c.n_min;
