@@ -315,6 +315,62 @@ int64_t mpgemm_sample_rows(int kind, int64_t m, int64_t n, int n_min, int num_sm
 int mpgemm_stream_status(void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Precision selection from an accuracy target (the paper's outlook: choose
+ * the precision as well as the algorithm).  Every configuration gets an
+ * a-priori elementwise bound |C - AB| <= beta |A||B|:
+ *   MPGEMM_SEL_DD           4 l 2^-104 (simple / block);
+ *   MPGEMM_SEL_QD           4 l 2^-208 (simple / block);
+ *   MPGEMM_SEL_MP           gamma_l = l 2^-p / (1 - l 2^-p), p = prec_bits;
+ *   MPGEMM_SEL_OZAKI_INT8 / _E4M3  split precision with S slices: with every
+ *       entry at most `spread` binades below the largest of its row of A or
+ *       column of B, t = 2^(spread+1-7S) (int8) or 2^(spread+2-5S) (e4m3),
+ *       beta = 2t + t^2 + (S+1) c 2^(2 spread + 2 - bS) + 2^-106
+ *       (b = 7 / 5, c = 1.02 / 1.07: the truncation of both operands, the
+ *       dropped triangle s + t > S + 1, the final DD rounding).
+ * Strassen is not offered (its bound is normwise, not elementwise).
+ *   mpgemm_precision_log2_bound  log2(beta) of one configuration (NaN for
+ *                                invalid arguments).
+ *   mpgemm_select_precision      the configurations with log2(beta) <=
+ *                                log2_target (split precision with the
+ *                                fewest slices, the smallest multi-limb
+ *                                precision of 128..1024 bits), fastest
+ *                                first by predicted time (the installed cost
+ *                                model's best simple/block configuration,
+ *                                else measured GB300 block rates; split
+ *                                precision from its tensor work at the
+ *                                measured level-kernel rates plus its memory
+ *                                passes); writes up to max_out of them to out
+ *                                and returns how many there are (>= 0), or
+ *                                MPGEMM_EINVAL.  Host only, except that a
+ *                                loaded cost model runs its inference kernel.
+ * ------------------------------------------------------------------------- */
+enum {
+    MPGEMM_SEL_DD = 0,
+    MPGEMM_SEL_QD = 1,
+    MPGEMM_SEL_MP = 2,
+    MPGEMM_SEL_OZAKI_INT8 = 3,
+    MPGEMM_SEL_OZAKI_E4M3 = 4
+};
+typedef struct {
+    int method;          /* MPGEMM_SEL_*                                  */
+    int prec_bits;       /* multi-limb precision (MPGEMM_SEL_MP), else 0   */
+    int num_slices;      /* split-precision S, else 0                      */
+    double log2_bound;   /* log2 of the a-priori bound beta                */
+    double est_ms;       /* predicted time                                 */
+} mpgemm_precision_choice;
+double mpgemm_precision_log2_bound(int method, int prec_bits, int num_slices, int64_t l, int spread);
+/* The `spread` of DD operands (A m x l, B l x n, device planes): the largest,
+   over rows of A's hi plane and columns of B's hi plane, of (largest frexp
+   exponent - smallest frexp exponent of a nonzero entry); 0 for empty or
+   all-zero operands.  Using the hi words bounds every |a| from below to
+   within a factor 1 - 2^-53.  Synchronous (allocates 4 (2n + 1) bytes
+   stream-ordered on `stream`). */
+int mpgemm_dd_exponent_spread(int64_t m, int64_t l, int64_t n, const double* A, const double* B, int* spread,
+                              void* stream);
+int mpgemm_select_precision(double log2_target, int64_t m, int64_t l, int64_t n, int spread,
+                            mpgemm_precision_choice* out, int max_out);
+
+/* ---------------------------------------------------------------------------
  * SM partitions (the GPU counterpart of the paper's thread counts, Section
  * 4: every algorithm is timed with 1, 2, 4 and 8 threads).
  *   mpgemm_partition_create   a CUDA green context holding at least num_sms

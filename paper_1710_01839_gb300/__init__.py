@@ -18,7 +18,8 @@ import os
 from ._lib import (ALGO, KIND, MpgemmError, check, lib, lib_path)  # noqa: F401
 
 __all__ = ["gemm_dd", "gemm_qd", "gemm_mp", "workspace_size", "set_workspace", "stream_status", "strerror",
-           "Partition", "MpgemmError", "ALGO", "KIND", "lib", "lib_path"]
+           "Partition", "PrecisionChoice", "precision_log2_bound", "select_precision", "exponent_spread",
+           "MpgemmError", "ALGO", "KIND", "lib", "lib_path"]
 
 
 def _torch():
@@ -117,6 +118,44 @@ def stream_status(stream=None):
 
 def strerror(status):
     return lib().mpgemm_strerror(int(status)).decode()
+
+
+SEL_METHOD = {0: "dd", 1: "qd", 2: "mp", 3: "ozaki_int8", 4: "ozaki_e4m3"}
+_SEL_CODE = {v: k for k, v in SEL_METHOD.items()}
+
+
+class PrecisionChoice(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("prec_bits", ctypes.c_int), ("num_slices", ctypes.c_int),
+                ("log2_bound", ctypes.c_double), ("est_ms", ctypes.c_double)]
+
+
+def precision_log2_bound(method, l, prec_bits=0, num_slices=0, spread=0):
+    """log2 of the a-priori elementwise bound |C - AB| <= beta |A||B| of one
+    configuration (mpgemm_precision_log2_bound)."""
+    return float(lib().mpgemm_precision_log2_bound(_SEL_CODE[method], int(prec_bits), int(num_slices), int(l),
+                                                   int(spread)))
+
+
+def select_precision(log2_target, m, l, n, spread=0, max_out=8):
+    """Configurations whose bound meets 2^log2_target, fastest first
+    (mpgemm_select_precision): a list of dicts."""
+    out = (PrecisionChoice * max_out)()
+    k = lib().mpgemm_select_precision(float(log2_target), int(m), int(l), int(n), int(spread), out, int(max_out))
+    if k < 0:
+        check(k)
+    return [{"method": SEL_METHOD[c.method], "prec_bits": c.prec_bits, "num_slices": c.num_slices,
+             "log2_bound": c.log2_bound, "est_ms": c.est_ms} for c in out[:min(k, max_out)]]
+
+
+def exponent_spread(A, B, stream=None):
+    """Binade spread of DD operands (mpgemm_dd_exponent_spread), computed on the GPU."""
+    torch = _torch()
+    _check_tensor(A, 2, (torch.float64,), "A")
+    _check_tensor(B, 2, (torch.float64,), "B")
+    v = ctypes.c_int()
+    check(lib().mpgemm_dd_exponent_spread(A.shape[1], A.shape[2], B.shape[2], ctypes.c_void_p(A.data_ptr()),
+                                          ctypes.c_void_p(B.data_ptr()), ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
 
 
 class Partition:

@@ -36,6 +36,9 @@ SIGNATURES = {
     "mpgemm_set_workspace": (_I, [_P, _SZ]),
     "mpgemm_stream_status": (_I, [_P]),
     "mpgemm_partition_create": (_I, [_I, _P, _P]),
+    "mpgemm_precision_log2_bound": (ctypes.c_double, [_I, _I, _I, _I64, _I]),
+    "mpgemm_select_precision": (_I, [ctypes.c_double, _I64, _I64, _I64, _I, _P, _I]),
+    "mpgemm_dd_exponent_spread": (_I, [_I64, _I64, _I64, _P, _P, _P, _P]),
     "mpgemm_partition_destroy": (_I, [_P]),
     "mpgemm_stream_sms": (_I, [_P]),
     "mpgemm_strerror": (ctypes.c_char_p, [_I]),

@@ -300,6 +300,23 @@ bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n,
     return true;
 }
 
+// Predicted time (ms) of the model's best simple / block configuration
+// (Strassen excluded: its bound is normwise); negative without a model.
+double cost_model_block_ms(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms) {
+    {
+        std::lock_guard<std::mutex> lk(g_mmu);
+        if (!g_model.ready) return -1.0;
+    }
+    std::vector<Cand> cs;
+    for (const Cand& c : candidates(kind, m, l, n))
+        if (c.algo != MPGEMM_STRASSEN) cs.push_back(c);
+    std::vector<float> F(cs.size() * NF), T(cs.size());
+    for (size_t i = 0; i < cs.size(); i++)
+        encode_features(kind, prec_bits, m, l, n, cs[i].algo, cs[i].tile, cs[i].depth, sms, &F[i * NF]);
+    if (predict(F.data(), (int)cs.size(), T.data()) != MPGEMM_OK) return -1.0;
+    return (double)*std::min_element(T.begin(), T.end());
+}
+
 // Tile (16 or 32) the model prefers for a DD / QD block GEMM; 0 without a model.
 int cost_model_tile(int kind, int prec_bits, int64_t m, int64_t l, int64_t n) {
     {
