@@ -81,7 +81,7 @@ int mpgemm_dd(int64_t m, int64_t l, int64_t n, const double* A, const double* B,
               int n_min, int strassen_depth, void* stream);
 int mpgemm_qd(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int algo,
               int n_min, int strassen_depth, void* stream);
-/* prec_bits = 32 w, w in {1, 2, 4, 8, 16, 32}.  Round to nearest, ties to
+/* prec_bits = 32 w, w in {1, 2, 4, 8, 16, 32, 64}.  Round to nearest, ties to
    even, after every multiply and every add (c <- RN(c + RN(a b)), k
    ascending); simple and block results are bit-identical to each other. */
 int mpgemm_mp(int64_t m, int64_t l, int64_t n, int prec_bits, const uint32_t* A, const uint32_t* B,

@@ -147,7 +147,7 @@ static int mp_entry(int64_t m, int64_t l, int64_t n, int prec_bits, const uint32
                     uint32_t* C, int algo, int n_min, int depth, void* stream) {
     if (prec_bits <= 0 || prec_bits % 32) return MPGEMM_EINVAL;
     int w = prec_bits / 32;
-    if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32)) return MPGEMM_EUNSUPPORTED;
+    if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32 || w == 64)) return MPGEMM_EUNSUPPORTED;
     int rc = check_common(m, l, n, sizeof(uint32_t) * (size_t)(2 + w), A, B, C, algo, n_min, depth);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;

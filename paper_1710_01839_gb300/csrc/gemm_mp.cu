@@ -96,6 +96,7 @@ int mp_gemm(int w, int algo, int64_t m, int64_t l, int64_t n, int64_t batch, Vie
         case 8: return mp_gemm_w<8>(algo, m, l, n, batch, A, B, C, n_min, s);
         case 16: return mp_gemm_w<16>(algo, m, l, n, batch, A, B, C, n_min, s);
         case 32: return mp_gemm_w<32>(algo, m, l, n, batch, A, B, C, n_min, s);
+        case 64: return mp_gemm_w<64>(algo, m, l, n, batch, A, B, C, n_min, s);
         default: return MPGEMM_EUNSUPPORTED;
     }
 }
@@ -120,6 +121,7 @@ int mp_addsub(int w, int64_t r, int64_t c, int64_t batch, View<uint32_t> Z, View
         case 8: return mp_addsub_w<8>(r, c, batch, Z, X, Y, sub, s);
         case 16: return mp_addsub_w<16>(r, c, batch, Z, X, Y, sub, s);
         case 32: return mp_addsub_w<32>(r, c, batch, Z, X, Y, sub, s);
+        case 64: return mp_addsub_w<64>(r, c, batch, Z, X, Y, sub, s);
         default: return MPGEMM_EUNSUPPORTED;
     }
 }

@@ -392,6 +392,7 @@ int strassen_mp_ws(int w, int64_t m, int64_t l, int64_t n, View<const uint32_t> 
         case 8: return strassen_mp_w<8>(m, l, n, A, B, C, n_min, depth, ws, ws_bytes, s);
         case 16: return strassen_mp_w<16>(m, l, n, A, B, C, n_min, depth, ws, ws_bytes, s);
         case 32: return strassen_mp_w<32>(m, l, n, A, B, C, n_min, depth, ws, ws_bytes, s);
+        case 64: return strassen_mp_w<64>(m, l, n, A, B, C, n_min, depth, ws, ws_bytes, s);
         default: return MPGEMM_EUNSUPPORTED;
     }
 }

@@ -149,7 +149,7 @@ template <int W>
 __device__ __forceinline__ void load_mp(MPV<W>& v, const uint32_t* p, int64_t ps) {
     v.e = (int)p[0];
     v.f = p[ps];
-#pragma unroll
+MP_UNROLL
     for (int i = 0; i < W; i++) v.m[i] = p[(2 + i) * ps];
 }
 
@@ -157,7 +157,7 @@ template <int W>
 __device__ __forceinline__ void store_mp(const MPV<W>& v, uint32_t* p, int64_t ps) {
     p[0] = (uint32_t)v.e;
     p[ps] = v.f;
-#pragma unroll
+MP_UNROLL
     for (int i = 0; i < W; i++) p[(2 + i) * ps] = v.m[i];
 }
 
@@ -206,7 +206,7 @@ __device__ __forceinline__ void mp_block_tile(int64_t m, int64_t l, int64_t n, c
             a.f = As[kk][ty][1];
             b.e = (int)Bs[kk][tx][0];
             b.f = Bs[kk][tx][1];
-#pragma unroll
+MP_UNROLL
             for (int w = 0; w < W; w++) {
                 a.m[w] = As[kk][ty][2 + w];
                 b.m[w] = Bs[kk][tx][2 + w];

@@ -97,7 +97,7 @@ def test_qd_large_config_sampled(n):
 
 # ---------------------------------------------------------------- multi-limb
 
-@pytest.mark.parametrize("w", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("w", [1, 2, 4, 8, 16, 32, 64])
 @pytest.mark.parametrize("algo", ["simple", "block"])
 def test_mp_ragged_bit_exact(w, algo):
     m, l, n = 37, 29, 23
@@ -108,7 +108,7 @@ def test_mp_ragged_bit_exact(w, algo):
     assert mpg.stream_status() == 0
 
 
-@pytest.mark.parametrize("w,n", [(4, 256), (8, 256), (16, 256), (32, 256), (4, 512)])
+@pytest.mark.parametrize("w,n", [(4, 256), (8, 256), (16, 256), (32, 256), (64, 128), (4, 512)])
 def test_mp_large_config_sampled_rows(w, n):
     A = I.mp_random(n, n, w, I.seed_for(2, w))
     B = I.mp_random(n, n, w, I.seed_for(2, 100 + w))
@@ -225,6 +225,14 @@ def test_mp_strassen_odd_sizes_bit_exact_vs_oracle(m, l, n, depth):
     A, B = I.mp_random(m, l, 4, 840 + depth), I.mp_random(l, n, 4, 850 + depth)
     C = host(mpg.gemm_mp(dev(A), dev(B), 128, algo="strassen", n_min=8, depth=depth), mp=True)
     Co = oracle.mp_gemm(A, B, prec_bits=128, algo="strassen", n_min=8, depth=depth)
+    assert np.array_equal(C, Co)
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+def test_mp2048_strassen_bit_exact_vs_oracle(depth):
+    A, B = I.mp_random(20, 18, 64, 860 + depth), I.mp_random(18, 14, 64, 870 + depth)
+    C = host(mpg.gemm_mp(dev(A), dev(B), 2048, algo="strassen", n_min=8, depth=depth), mp=True)
+    Co = oracle.mp_gemm(A, B, prec_bits=2048, algo="strassen", n_min=8, depth=depth)
     assert np.array_equal(C, Co)
 
 

@@ -192,11 +192,11 @@ def _check_against_refs(w, x, y, op):
     assert got.tolist() == mp_words(*want, w).tolist(), (x, y, op)
 
 
-@pytest.mark.parametrize("w", [1, 2, 4, 8, 32])
+@pytest.mark.parametrize("w", [1, 2, 4, 8, 32, 64])
 def test_mp_random_vs_mpmath(w):
     pytest.importorskip("mpmath")
     rng = random.Random(100 + w)
-    n = 400 if w <= 8 else 120
+    n = 400 if w <= 8 else 120 if w <= 32 else 60
     for _ in range(n):
         x, y = _rand_mp(rng, w), _rand_mp(rng, w)
         _check_against_refs(w, x, y, "mul")
@@ -206,7 +206,7 @@ def test_mp_random_vs_mpmath(w):
         _check_against_refs(w, x, y2, "add")
 
 
-@pytest.mark.parametrize("w", [1, 4])
+@pytest.mark.parametrize("w", [1, 4, 64])
 def test_mp_constructed_ties_and_carries(w):
     pytest.importorskip("mpmath")
     p = 32 * w
