@@ -313,6 +313,14 @@ int64_t mpgemm_sample_rows(int kind, int64_t m, int64_t n, int n_min, int num_sm
 /* Synchronise `stream`, then read and clear the current device's status
    word: MPGEMM_OK, MPGEMM_EOVERFLOW or MPGEMM_ETIMEOUT. */
 int mpgemm_stream_status(void* stream);
+/* Self-test of the device failure path (the paper has no counterpart): one
+   warp runs the kernels' bounded mbarrier wait on a phase that nothing ever
+   completes, with a time limit of limit_ms (1..2000).  The wait gives up,
+   the kernel records a timeout in the status word and returns; the call
+   synchronises and returns what mpgemm_stream_status reads:
+   MPGEMM_ETIMEOUT is the expected result (the status word is cleared and
+   the context stays usable).  MPGEMM_EINVAL for a limit out of range. */
+int mpgemm_selftest_wait_timeout(int limit_ms, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Precision selection from an accuracy target (the paper's outlook: choose

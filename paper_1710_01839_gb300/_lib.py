@@ -35,6 +35,7 @@ SIGNATURES = {
     "mpgemm_workspace_size": (_SZ, [_I, _I, _I64, _I64, _I64, _I, _I]),
     "mpgemm_set_workspace": (_I, [_P, _SZ]),
     "mpgemm_stream_status": (_I, [_P]),
+    "mpgemm_selftest_wait_timeout": (_I, [_I, _P]),
     "mpgemm_partition_create": (_I, [_I, _P, _P]),
     "mpgemm_precision_log2_bound": (ctypes.c_double, [_I, _I, _I, _I64, _I]),
     "mpgemm_select_precision": (_I, [ctypes.c_double, _I64, _I64, _I64, _I, _P, _I]),

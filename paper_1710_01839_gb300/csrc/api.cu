@@ -7,6 +7,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "strassen.h"
+#include "tc_levels.h"
 #include "tune.h"
 
 namespace mpg {
@@ -243,6 +244,14 @@ const char* mpgemm_strerror(int status) {
 }
 
 int mpgemm_last_cuda_error(void) { return t_last_cuda_error; }
+
+int mpgemm_selftest_wait_timeout(int limit_ms, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    PartitionScope pscope(s);
+    int rc = wait_selftest(limit_ms, s);
+    if (rc) return rc;
+    return mpgemm_stream_status(stream);
+}
 
 int mpgemm_version(void) { return 10000 * 0 + 100 * 1 + 0; }
 

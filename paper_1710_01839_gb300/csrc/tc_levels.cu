@@ -83,7 +83,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 // TC_WAIT_NS nanoseconds, or when another role has raised the abort flag
 // (abort_flag == nullptr: teardown wait for asynchronous work already in
 // flight, which ignores the flag).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag,
+                                          uint64_t limit_ns = TC_WAIT_NS) {
     uint64_t t0 = 0;
     for (uint32_t i = 0; i < TC_SPIN; i++) {
         if (mbar_try(bar, parity)) return true;
@@ -91,7 +92,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const v
             if (abort_flag && *abort_flag) return false;
             const uint64_t t = global_ns();
             if (!t0) t0 = t;
-            else if (t - t0 > TC_WAIT_NS) return false;
+            else if (t - t0 > limit_ns) return false;
         }
     }
     return false;
@@ -326,6 +327,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+// Self-test of the failure path: one warp waits, with the kernels' bounded
+// wait, for an mbarrier phase that nothing completes.  The wait gives up
+// after limit_ns, the kernel records DEV_TIMEOUT in the status word and
+// returns normally, so the host sees MPGEMM_ETIMEOUT and the context stays
+// usable.  Nothing is faulted, trapped or left running.
+__global__ void k_wait_selftest(uint64_t limit_ns, unsigned* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(su32(&bar), 0, nullptr, limit_ns);   // no thread ever arrives
+    if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(status, DEV_TIMEOUT);
+}
+
+int wait_selftest(int limit_ms, cudaStream_t s) {
+    if (limit_ms < 1 || limit_ms > 2000) return MPGEMM_EINVAL;
+    unsigned* status = device_status_ptr();
+    if (!status) return MPGEMM_ECUDA;
+    k_wait_selftest<<<1, 32, 0, s>>>((uint64_t)limit_ms * 1000000ull, status);
+    return check_launch();
 }
 
 // ---------------------------------------------------------------- host side

@@ -58,3 +58,10 @@ def test_host_only_calls(built):
     assert w1 >= 7 * 3 * 32 * 32 * 16
     assert built.workspace_size("dd", 64, 64, 64, algo="strassen", depth=2) > w1
     assert built.workspace_size("mp", 64, 64, 64, algo="strassen", depth=1, prec_bits=256) > 0
+    # odd sizes are zero-extended: the workspace is that of the extended problem
+    assert built.workspace_size("dd", 63, 63, 63, algo="strassen", depth=2) == \
+        built.workspace_size("dd", 64, 64, 64, algo="strassen", depth=2)
+    # argument checks that return before any CUDA call
+    assert L.mpgemm_selftest_wait_timeout(0, None) == -1
+    assert L.mpgemm_selftest_wait_timeout(5000, None) == -1
+    assert L.mpgemm_stream_sms is not None
