@@ -144,6 +144,31 @@ int mpgemm_ozaki_levels_ex(int digit_kind, int64_t m, int64_t l, int64_t n, int 
                            const void* DB, int* levels, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Split-precision QD GEMM (the FP8-digit scheme carried to quad-double; the
+ * paper has no counterpart).  A, B, C are QD planes (4 x rows x cols,
+ * x_0 leading, canonical: each term at most half an ulp of the one
+ * before).  e_i / f_j are the frexp exponents of A's row / B's column
+ * maxima of the leading plane; every element is truncated toward zero to
+ * 5 S bits of x 2^-(e+1) (exactly, from the exact sum of its four terms),
+ * written as S balanced base-32 digits in e4m3, multiplied on the tcgen05
+ * tensor cores with exact f32 chunk sums, recombined exactly and rounded
+ * greedily to four doubles (x_0 = RN(c), x_1 = RN(c - x_0), ...).
+ * num_slices S in 1..48 (0 = 44, which meets 4 l 2^-208 |A||B| on inputs
+ * whose entries lie within a few binades of their row / column maxima; see
+ * mpgemm_select_precision for the bound).  Limits as for
+ * mpgemm_dd_ozaki_ex with e4m3 digits (l <= 65536, S 256 l < 2^31, m and n
+ * <= 65535).  Workspace: mpgemm_ozaki_workspace_size(m, l, n, S).
+ * mpgemm_ozaki_split_terms: the digit step alone for T-term expansions
+ * (terms = 4 only), in the layout of mpgemm_ozaki_split_ex with e4m3
+ * digits.
+ * ------------------------------------------------------------------------- */
+int mpgemm_qd_ozaki(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int num_slices,
+                    void* stream);
+int mpgemm_qd_ozaki_slices_default(void);
+int mpgemm_ozaki_split_terms(int terms, int by_col, int64_t rows, int64_t cols, const double* X, int num_slices,
+                             int* expo, void* digits, void* stream);
+
+/* ---------------------------------------------------------------------------
  * DD Strassen that allocates nothing.  The paper has no counterpart.  It is
  * for callers that cannot allocate device memory while they run: for
  * example a service whose device memory is all handed to its own pool

@@ -89,6 +89,10 @@ def _declare(L):
     L.or_ozaki_recombine_bits.argtypes = [_I64, _I64, _I, _I, _I, _P, _P, _P, _P]
     L.or_ozaki_gemm_b32.argtypes = [_I64, _I64, _I64, _P, _P, _P, _I]
     L.or_ozaki_gemm_b32.restype = _I
+    L.or_ozaki_slice_b32_terms.argtypes = [_I, _I, _I64, _I64, _P, _P, _I, _P]
+    L.or_ozaki_recombine_terms.argtypes = [_I64, _I64, _I, _I, _I, _I, _P, _P, _P, _P]
+    L.or_ozaki_gemm_b32_terms.argtypes = [_I, _I64, _I64, _I64, _P, _P, _P, _I]
+    L.or_ozaki_gemm_b32_terms.restype = _I
 
 
 def _ptr(a: np.ndarray):
@@ -309,4 +313,34 @@ def ozaki_gemm_b32(A, B, S):
     m, l, n = A.shape[1], A.shape[2], B.shape[2]
     C = np.zeros((2, m, n))
     lib().or_ozaki_gemm_b32(m, l, n, _ptr(A), _ptr(B), _ptr(C), S)
+    return C
+
+
+def ozaki_slice_b32_terms(X, expo, S, by_col):
+    """Balanced base-32 digits of a T-plane expansion (T = X.shape[0]: 2 DD,
+    4 QD) from its exact sum: S planes (B not transposed)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    expo = np.ascontiguousarray(expo, dtype=np.int32)
+    D = np.zeros((S, X.shape[1], X.shape[2]), dtype=np.int8)
+    lib().or_ozaki_slice_b32_terms(1 if by_col else 0, X.shape[0], X.shape[1], X.shape[2], _ptr(X), _ptr(expo), S,
+                                   _ptr(D))
+    return D
+
+
+def ozaki_recombine_terms(L, e, f, S, T, bits=5, head=1):
+    m, n = L.shape[1], L.shape[2]
+    C = np.zeros((T, m, n))
+    lib().or_ozaki_recombine_terms(m, n, S, bits, head, T, _ptr(np.ascontiguousarray(L)),
+                                   _ptr(np.ascontiguousarray(e, dtype=np.int32)),
+                                   _ptr(np.ascontiguousarray(f, dtype=np.int32)), _ptr(C))
+    return C
+
+
+def ozaki_gemm_b32_terms(A, B, S):
+    """The FP8-digit split-precision GEMM of T-term expansions (T = A.shape[0])."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    T, m, l, n = A.shape[0], A.shape[1], A.shape[2], B.shape[2]
+    C = np.zeros((T, m, n))
+    lib().or_ozaki_gemm_b32_terms(T, m, l, n, _ptr(A), _ptr(B), _ptr(C), S)
     return C

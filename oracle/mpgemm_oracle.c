@@ -1062,6 +1062,92 @@ OR_API void or_ozaki_recombine_bits(int64_t m, int64_t n, int S, int bits, int h
         }
 }
 
+/* Balanced base-32 digits of a T-term expansion x = x_0 + ... + x_{T-1}
+   (T = 2: DD, T = 4: QD), the same definition as ozaki_digits_b32 computed
+   another way: the exact sum is formed in the wide fixed-point accumulator,
+   its magnitude's bits e, e-1, ..., e+1-5S (the first 5S bits of
+   |x| 2^-(e+1), i.e. trunc toward zero) are read as S 5-bit digits from the
+   most significant down, balanced from the least significant up (a digit
+   >= 16 becomes digit - 32 and carries one), and given x's sign. */
+static void ozaki_digits_b32_terms(const double *x, int64_t xstride, int T, int e, int S, int8_t *d,
+                                   int64_t stride) {
+    wfx_t W;
+    int mag[96];
+    int neg;
+    if (S > 96) die("too many slices");
+    wfx_zero(&W);
+    for (int t = 0; t < T; t++) wfx_add_double(&W, x[(int64_t)t * xstride]);
+    neg = wfx_is_neg(&W);
+    if (neg) wfx_negate(&W);
+    const int top = WFX_FRAC + e + 1;                /* window index of 2^(e+1) */
+    if (top - 5 * S < 0) die("digits below the exact accumulator's window");
+    if (top < WFX_LIMBS * 32 - 1 && wfx_bits(&W, top, 32) != 0) die("value not below 2^(e+1)");
+    for (int s = 0; s < S; s++) mag[s] = (int)wfx_bits(&W, top - 5 * (s + 1), 5);
+    for (int s = S - 1; s >= 1; s--) {
+        if (mag[s] >= 16) {
+            mag[s] -= 32;
+            mag[s - 1] += 1;
+        }
+    }
+    if (mag[0] > 16) die("balanced top digit out of range");
+    for (int s = 0; s < S; s++) d[(int64_t)s * stride] = (int8_t)(neg ? -mag[s] : mag[s]);
+}
+
+/* Digits of a T-plane matrix X (rows x cols per plane), row (A) or column
+   (B) scaled, as S planes of rows x cols int8 (B not transposed). */
+OR_API void or_ozaki_slice_b32_terms(int by_col, int T, int64_t rows, int64_t cols, const double *X,
+                                     const int32_t *expo, int S, int8_t *D) {
+    size_t N = (size_t)(rows * cols);
+    for (int64_t i = 0; i < rows; i++)
+        for (int64_t j = 0; j < cols; j++) {
+            size_t e = (size_t)(i * cols + j);
+            ozaki_digits_b32_terms(X + e, (int64_t)N, T, by_col ? expo[j] : expo[i], S, D + e, (int64_t)N);
+        }
+}
+
+/* Step 4 rounded to T terms: c_ij = the greedy T-term rounding (x_0 =
+   RN(x), x_1 = RN(x - x_0), ...) of x = 2^(e_i + f_j + 2 head) sum_g L_g
+   2^(-bits g), summed exactly.  C has T planes. */
+OR_API void or_ozaki_recombine_terms(int64_t m, int64_t n, int S, int bits, int head, int T, const int64_t *L,
+                                     const int32_t *e, const int32_t *f, double *C) {
+    size_t NC = (size_t)(m * n);
+    if (T < 1 || T > 8) die("bad term count");
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t j = 0; j < n; j++) {
+            wfx_t W;
+            double r[8];
+            wfx_zero(&W);
+            for (int g = 2; g <= S + 1; g++) {
+                int64_t v = L[(size_t)g * NC + (size_t)(i * n + j)];
+                if (v > (1LL << 53) || v < -(1LL << 53)) die("level sum beyond 2^53");
+                wfx_add_double(&W, ldexp((double)v, e[i] + f[j] + 2 * head - bits * g));
+            }
+            wfx_round_terms(&W, r, T);
+            for (int t = 0; t < T; t++) C[(size_t)t * NC + (size_t)(i * n + j)] = r[t];
+        }
+}
+
+/* The FP8-digit pipeline for T-term expansions (T = 2: DD, T = 4: QD):
+   exponents of the leading plane, balanced base-32 digits, level sums,
+   exact recombination rounded to T terms. */
+OR_API int or_ozaki_gemm_b32_terms(int T, int64_t m, int64_t l, int64_t n, const double *A, const double *B,
+                                   double *C, int S) {
+    int32_t *e = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int32_t *f = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int8_t *DA = (int8_t *)malloc((size_t)(m * l * S) + 1);
+    int8_t *DB = (int8_t *)malloc((size_t)(l * n * S) + 1);
+    int64_t *L = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m * n) * (size_t)(2 * S + 1) + 8);
+    if (!e || !f || !DA || !DB || !L) die("out of host memory");
+    or_ozaki_row_expo(m, l, A, e);
+    or_ozaki_col_expo(l, n, B, f);
+    or_ozaki_slice_b32_terms(0, T, m, l, A, e, S, DA);
+    or_ozaki_slice_b32_terms(1, T, l, n, B, f, S, DB);
+    or_ozaki_levels(m, l, n, S, DA, DB, L);
+    or_ozaki_recombine_terms(m, n, S, 5, 1, T, L, e, f, C);
+    free(e); free(f); free(DA); free(DB); free(L);
+    return 0;
+}
+
 /* The FP8-digit pipeline (steps 1, 2 with balanced base-32 digits, 3, 4). */
 OR_API int or_ozaki_gemm_b32(int64_t m, int64_t l, int64_t n, const double *A, const double *B, double *C, int S) {
     int32_t *e = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));

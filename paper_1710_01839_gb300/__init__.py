@@ -17,7 +17,7 @@ import os
 
 from ._lib import (ALGO, KIND, MpgemmError, check, lib, lib_path)  # noqa: F401
 
-__all__ = ["gemm_dd", "gemm_qd", "gemm_mp", "workspace_size", "set_workspace", "stream_status", "strerror",
+__all__ = ["gemm_dd", "gemm_qd", "gemm_mp", "gemm_split", "workspace_size", "set_workspace", "stream_status", "strerror",
            "Partition", "PrecisionChoice", "precision_log2_bound", "select_precision", "exponent_spread",
            "MpgemmError", "ALGO", "KIND", "lib", "lib_path"]
 
@@ -94,6 +94,35 @@ def gemm_mp(A, B, prec_bits, C=None, algo="block", n_min=0, depth=0, stream=None
     rc = lib().mpgemm_mp(m, l, n, int(prec_bits), ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                          ctypes.c_void_p(C.data_ptr()), _algo(algo), int(n_min), int(depth), _stream_ptr(stream))
     check(rc)
+    return C
+
+
+def gemm_split(A, B, C=None, slices=0, digits="e4m3", stream=None):
+    """Split-precision GEMM on the tensor cores: DD (2 planes; int8 or e4m3
+    digits) or QD (4 planes; e4m3 digits).  slices = 0 picks the default
+    (DD: 16 int8 / 22 e4m3; QD: 44)."""
+    torch = _torch()
+    T = A.shape[0]
+    if T not in (2, 4):
+        raise ValueError("A must hold 2 (DD) or 4 (QD) planes")
+    _check_tensor(A, T, (torch.float64,), "A")
+    _check_tensor(B, T, (torch.float64,), "B")
+    m, l = A.shape[1], A.shape[2]
+    if B.shape[1] != l:
+        raise ValueError("inner dimensions differ")
+    n = B.shape[2]
+    if C is None:
+        C = torch.empty((T, m, n), dtype=torch.float64, device=A.device)
+    else:
+        _check_tensor(C, T, (torch.float64,), "C")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    if T == 4:
+        if digits != "e4m3":
+            raise ValueError("QD split precision uses e4m3 digits")
+        check(lib().mpgemm_qd_ozaki(m, l, n, p(A), p(B), p(C), int(slices), _stream_ptr(stream)))
+    else:
+        kind = {"int8": 0, "e4m3": 1}[digits]
+        check(lib().mpgemm_dd_ozaki_ex(m, l, n, p(A), p(B), p(C), int(slices), kind, _stream_ptr(stream)))
     return C
 
 

@@ -258,6 +258,105 @@ __global__ void __launch_bounds__(128) k_slice_cols_f8(int64_t l, int64_t n, int
 }
 
 
+// ---- FP8 digits of T-term expansions (QD, T = 4): the same scheme with the
+// exact truncation on NW = 4 64-bit words and up to QD_SMAX digits.
+constexpr int QD_SMAX = 48;   // 5 S + 1 bits of the biased value stay below 2^256
+
+struct Bias4 {
+    unsigned long long w[4];
+};
+
+template <int K>
+__device__ __forceinline__ int b32_digit_q(const WideB32<4>& u, int S) {
+    const int d = b32_field_wide<K, 4>(u) - (K < S - 1 ? 16 : 0);
+    return u.neg ? -d : d;
+}
+
+template <int K>
+__device__ __forceinline__ unsigned b32_word_q(const WideB32<4> (&u)[4], int S) {
+    return e4m3x2_of(b32_digit_q<K>(u[0], S), b32_digit_q<K>(u[1], S)) |
+           (e4m3x2_of(b32_digit_q<K>(u[2], S), b32_digit_q<K>(u[3], S)) << 16);
+}
+
+template <int K, typename F>
+__device__ __forceinline__ void b32_words_q(const WideB32<4> (&u)[4], int S, F&& f) {
+    if constexpr (K < QD_SMAX) {
+        if (K < S) {
+            f(K, b32_word_q<K>(u, S));
+            b32_words_q<K + 1>(u, S, f);
+        }
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void prepare_q(const double (&x)[T], int sc, const Bias4& C, WideB32<4>& u) {
+    expansion_trunc_scaled<T, 4>(x, sc, u);
+    const unsigned long long c[4] = {C.w[0], C.w[1], C.w[2], C.w[3]};
+    b32_prepare_wide<4>(u, c);
+}
+
+// A (T planes of m x l, row scale e): digits into S planes of m x lp, four
+// consecutive K positions per thread (one 32-bit store per plane).
+template <int T>
+__global__ void k_slice_rows_f8_terms(int64_t m, int64_t l, int64_t lp, const double* X, const int* e, int S,
+                                      Bias4 C, unsigned char* D) {
+    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int64_t i = blockIdx.y;
+    if (k0 >= lp || i >= m) return;
+    const int sc = 5 * S - e[i] - 1;
+    const int64_t plane_in = m * l;
+    WideB32<4> u[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        double x[T];
+#pragma unroll
+        for (int q = 0; q < T; q++) x[q] = k0 + t < l ? X[q * plane_in + i * l + k0 + t] : 0.0;
+        prepare_q<T>(x, sc, C, u[t]);
+    }
+    const int64_t plane = m * lp;
+    unsigned* out = (unsigned*)(D + i * lp + k0);
+    b32_words_q<0>(u, S, [&](int K, unsigned w) { out[(int64_t)(S - 1 - K) * (plane >> 2)] = w; });
+}
+
+// B (T planes of l x n, column scale f): digits transposed into S planes of
+// n x lp through shared memory, as k_slice_cols_f8 does for DD.
+template <int T>
+__global__ void __launch_bounds__(128) k_slice_cols_f8_terms(int64_t l, int64_t n, int64_t lp, const double* X,
+                                                             const int* f, int S, Bias4 C, unsigned char* D) {
+    extern __shared__ unsigned tile[];   // [S][SLC_COLS][SLC_PITCH]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t k0 = (int64_t)blockIdx.x * SLC_ROWS, j0 = (int64_t)blockIdx.y * SLC_COLS;
+    const int64_t j = j0 + lane;
+    const bool jin = j < n;
+    const int sc = 5 * S - (jin ? f[j] : 0) - 1;
+    const int64_t plane_in = l * n;
+#pragma unroll 1
+    for (int q4 = warp; q4 < SLC_ROWS / 4; q4 += 4) {
+        WideB32<4> u[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int64_t k = k0 + 4 * q4 + t;
+            const bool in = jin && k < l;
+            double x[T];
+#pragma unroll
+            for (int q = 0; q < T; q++) x[q] = in ? X[q * plane_in + k * n + j] : 0.0;
+            prepare_q<T>(x, sc, C, u[t]);
+        }
+        b32_words_q<0>(u, S, [&](int K, unsigned w) { tile[((S - 1 - K) * SLC_COLS + lane) * SLC_PITCH + q4] = w; });
+    }
+    __syncthreads();
+    const int64_t plane = n * lp;
+    for (int s = 0; s < S; s++) {
+#pragma unroll
+        for (int r = 0; r < (SLC_COLS * SLC_ROWS / 4) / 128; r++) {
+            const int idx = threadIdx.x + 128 * r, row = idx >> 4, w = idx & 15;
+            const int64_t jj = j0 + row, kk = k0 + 4 * w;
+            if (jj < n && kk < lp)
+                *(unsigned*)(D + (int64_t)s * plane + jj * lp + kk) = tile[(s * SLC_COLS + row) * SLC_PITCH + w];
+        }
+    }
+}
+
 // A (m x l, row scale e): digits into S planes of m x lp (K contiguous, zero padded).
 __global__ void k_slice_rows(int64_t m, int64_t l, int64_t lp, const double* A, const int* e, int S, signed char* D) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -610,6 +709,118 @@ __global__ void k_recombine(int64_t m, int64_t n, int S, int bits, int head, con
     C[mn + idx] = lo;
 }
 
+// Step 4 rounded to T terms (QD: T = 4) on NW = 5 64-bit words:
+// V = sum_g L_g 2^(bits (S + 1 - g)) by Horner's rule (|V| < 2^(32 + bits
+// (S - 1)) <= 2^267), then x_t = RN(V - x_0 - ... - x_{t-1}) for t < T,
+// each remainder exact, scaled by 2^(e_i + f_j + 2 head - bits (S + 1)).
+template <int NW>
+__device__ __forceinline__ bool wide_neg_sign(const unsigned long long (&v)[NW]) {
+    return (long long)v[NW - 1] < 0;
+}
+template <int NW>
+__device__ __forceinline__ void wide_negate(unsigned long long (&v)[NW]) {
+    unsigned long long c = 1ull;
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+        const unsigned long long x = ~v[i] + c;
+        c = (c && x == 0ull) ? 1ull : 0ull;
+        v[i] = x;
+    }
+}
+template <int NW>
+__device__ __forceinline__ int wide_top_bit(const unsigned long long (&v)[NW]) {
+    int t = -1;
+#pragma unroll
+    for (int i = 0; i < NW; i++)
+        if (v[i]) t = 64 * i + 63 - __clzll(v[i]);
+    return t;
+}
+template <int NW>
+__device__ __forceinline__ unsigned long long wide_bits(const unsigned long long (&v)[NW], int lo, int cnt) {
+    // bits [lo, lo + cnt), cnt <= 64, lo >= 0
+    const int q = lo >> 6, r = lo & 63;
+    unsigned long long a = 0ull, b = 0ull;
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+        if (i == q) a = v[i];
+        if (i == q + 1) b = v[i];
+    }
+    const unsigned long long x = r ? ((a >> r) | (b << (64 - r))) : a;
+    return cnt >= 64 ? x : (x & ((1ull << cnt) - 1ull));
+}
+template <int NW>
+__device__ __forceinline__ bool wide_any_below(const unsigned long long (&v)[NW], int pos) {
+    const int q = pos >> 6, r = pos & 63;
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+        if (i < q) any |= v[i] != 0ull;
+        if (i == q && r) any |= (v[i] & ((1ull << r) - 1ull)) != 0ull;
+    }
+    return any;
+}
+
+template <int T>
+__global__ void k_recombine_terms(int64_t m, int64_t n, int S, int bits, int head, const int* Lv, const int* e,
+                                  const int* f, double* C) {
+    constexpr int NW = 5;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.y;
+    if (j >= n) return;
+    const int64_t mn = m * n, idx = i * n + j;
+    unsigned long long v[NW];
+#pragma unroll
+    for (int q = 0; q < NW; q++) v[q] = 0ull;
+    const int* lp = Lv + idx;
+    for (int g = 2; g <= S + 1; g++) {
+        const long long x = lp[(int64_t)(g - 2) * mn];
+#pragma unroll
+        for (int q = NW - 1; q > 0; q--) v[q] = (v[q] << bits) | (v[q - 1] >> (64 - bits));
+        v[0] <<= bits;
+        const unsigned long long ext = x < 0 ? ~0ull : 0ull;
+        unsigned long long c = 0ull;
+#pragma unroll
+        for (int q = 0; q < NW; q++) {
+            const unsigned long long a = q == 0 ? (unsigned long long)x : ext;
+            const unsigned long long s1 = v[q] + a;
+            const unsigned long long c1 = s1 < v[q] ? 1ull : 0ull;
+            const unsigned long long s2 = s1 + c;
+            const unsigned long long c2 = s2 < s1 ? 1ull : 0ull;
+            v[q] = s2;
+            c = c1 | c2;
+        }
+    }
+    const int E = e[i] + f[j] + 2 * head - bits * (S + 1);
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        const bool neg = wide_neg_sign<NW>(v);
+        unsigned long long a[NW];
+#pragma unroll
+        for (int q = 0; q < NW; q++) a[q] = v[q];
+        if (neg) wide_negate<NW>(a);
+        const int top = wide_top_bit<NW>(a);
+        double x = 0.0;
+        if (top >= 0) {
+            unsigned long long M;
+            int pos;
+            if (top <= 52) {
+                M = a[0];
+                pos = 0;
+            } else {
+                M = wide_bits<NW>(a, top - 52, 53);
+                const bool rb = wide_bits<NW>(a, top - 53, 1) != 0ull;
+                const bool st = wide_any_below<NW>(a, top - 53);
+                if (rb && (st || (M & 1ull))) M += 1ull;
+                pos = top - 52;
+            }
+            x = ldexp((double)M, pos + E);
+            if (neg) x = -x;
+            wide_add_shifted<NW>(v, M, pos, !neg);   // v -= x (exact)
+        }
+        C[(int64_t)t * mn + idx] = x;
+    }
+}
+
 // ---------------------------------------------------------------- driver
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -629,6 +840,42 @@ static int digit_bits(int kind) { return kind == 1 ? 5 : 7; }
 static int digit_head(int kind) { return kind == 1 ? 1 : 0; }
 static int max_slices(int kind) { return kind == 1 ? 24 : 18; }
 
+// Column exponents of a rows x cols leading plane (0 for an all-zero column).
+static int col_exponents(int64_t rows, int64_t cols, const double* X, int* expo, cudaStream_t s) {
+    MPG_CUDA(cudaMemsetAsync(expo, 0x80, sizeof(int) * (size_t)cols, s));   // COLX_EMPTY
+    if (rows > 0) {
+        dim3 g(ceil_div(cols, 32), ceil_div(rows, COLX_ROWS));
+        k_col_expo<<<g, dim3(32, 8), 0, s>>>(rows, cols, X, expo);
+        if (int rc = check_launch()) return rc;
+    }
+    k_expo_fix<<<ceil_div(cols, 256), 256, 0, s>>>(cols, expo);
+    return check_launch();
+}
+
+// FP8 digits of a T-term expansion matrix (QD: T = 4): exponents of the
+// leading plane, then the balanced base-32 digits (rows: K contiguous; by
+// column: transposed to K contiguous).
+static int split_terms(int T, int by_col, int64_t rows, int64_t cols, const double* X, int S, int* expo, void* D,
+                       int64_t lp, cudaStream_t s) {
+    if (T != 4) return MPGEMM_EUNSUPPORTED;
+    Bias4 C;
+    b32_bias_wide<4>(S, C.w);
+    if (!by_col) {
+        k_row_expo<<<ceil_div(rows, 8), 256, 0, s>>>(rows, cols, X, expo);
+        if (int rc = check_launch()) return rc;
+        dim3 g(ceil_div(lp, 4 * 128), (unsigned)rows);
+        k_slice_rows_f8_terms<4><<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, C, (unsigned char*)D);
+    } else {
+        if (int rc = col_exponents(rows, cols, X, expo, s)) return rc;
+        const int smem = S * SLC_COLS * SLC_PITCH * 4;
+        MPG_CUDA(cudaFuncSetAttribute(k_slice_cols_f8_terms<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      QD_SMAX * SLC_COLS * SLC_PITCH * 4));
+        dim3 g((unsigned)(lp / SLC_ROWS), ceil_div(cols, SLC_COLS));
+        k_slice_cols_f8_terms<4><<<g, 128, smem, s>>>(rows, cols, lp, X, expo, S, C, (unsigned char*)D);
+    }
+    return check_launch();
+}
+
 int ozaki_split(int kind, int by_col, int64_t rows, int64_t cols, const double* X, int S, int* expo, void* D,
                 int64_t lp, cudaStream_t s) {
     unsigned long long Ch, Cl;
@@ -645,14 +892,7 @@ int ozaki_split(int kind, int by_col, int64_t rows, int64_t cols, const double* 
             k_slice_rows<<<g, 128, 0, s>>>(rows, cols, lp, X, expo, S, (signed char*)D);
         }
     } else {
-        MPG_CUDA(cudaMemsetAsync(expo, 0x80, sizeof(int) * (size_t)cols, s));   // COLX_EMPTY
-        if (rows > 0) {
-            dim3 g(ceil_div(cols, 32), ceil_div(rows, COLX_ROWS));
-            k_col_expo<<<g, dim3(32, 8), 0, s>>>(rows, cols, X, expo);
-            if (int rc = check_launch()) return rc;
-        }
-        k_expo_fix<<<ceil_div(cols, 256), 256, 0, s>>>(cols, expo);
-        if (int rc = check_launch()) return rc;
+        if (int rc = col_exponents(rows, cols, X, expo, s)) return rc;
         if (kind == 1) {
             // set on every call: the current context may be an SM partition's (partition.cu)
             const int smem_max = 24 * SLC_COLS * SLC_PITCH * 4;
@@ -714,11 +954,73 @@ int ozaki_gemm_ws(int kind, int64_t m, int64_t l, int64_t n, const double* A, co
     return ozaki_recombine(kind, m, n, S, Lv, e, f, C, s);
 }
 
+// The split-precision QD GEMM (FP8 digits, T = 4) on a caller-sized workspace.
+static int ozaki_qd_gemm_ws(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int S,
+                            void* ws, size_t ws_bytes, cudaStream_t s) {
+    const int64_t lp = ozaki_padded_k(l);
+    if (ws_bytes < ozaki_workspace_bytes(m, l, n, S)) return MPGEMM_ENOMEM;
+    char* p = (char*)ws;
+    int* e = (int*)p;
+    p += a256(sizeof(int) * (size_t)m);
+    int* f = (int*)p;
+    p += a256(sizeof(int) * (size_t)n);
+    void* DA = p;
+    p += a256((size_t)S * (size_t)(m * lp));
+    void* DB = p;
+    p += a256((size_t)S * (size_t)(n * lp));
+    int* Lv = (int*)p;
+    int rc;
+    if ((rc = split_terms(4, 0, m, l, A, S, e, DA, lp, s))) return rc;
+    if ((rc = split_terms(4, 1, l, n, B, S, f, DB, lp, s))) return rc;
+    if ((rc = tc_levels(m, n, lp, S, DA, DB, Lv, s))) return rc;
+    dim3 g(ceil_div(n, 128), (unsigned)m);
+    k_recombine_terms<4><<<g, 128, 0, s>>>(m, n, S, 5, 1, Lv, e, f, C);
+    return check_launch();
+}
+
 }  // namespace mpg
 
 using namespace mpg;
 
 extern "C" {
+
+int mpgemm_qd_ozaki_slices_default(void) { return 44; }
+
+int mpgemm_qd_ozaki(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int num_slices,
+                    void* stream) {
+    const int S = num_slices <= 0 ? 44 : num_slices;
+    if (m < 0 || l < 0 || n < 0 || S < 1 || S > QD_SMAX) return MPGEMM_EINVAL;
+    if ((m * l && !A) || (l * n && !B) || (m * n && !C)) return MPGEMM_EINVAL;
+    // a slice pair's f32 sum stays below 2^24 (256 l), a level inside int32
+    if (l > 65536 || (double)S * 256.0 * (double)l >= 2147483648.0) return MPGEMM_EUNSUPPORTED;
+    if (m > 65535 || n > 65535) return MPGEMM_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    PartitionScope pscope(s);
+    if (m == 0 || n == 0) return MPGEMM_OK;
+    if (l == 0) {
+        MPG_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * 4 * (size_t)(m * n), s));
+        return MPGEMM_OK;
+    }
+    size_t bytes = ozaki_workspace_bytes(m, l, n, S);
+    void* ws = nullptr;
+    bool owned = false;
+    int rc = workspace_get(bytes, s, &ws, &owned);
+    if (rc) return rc;
+    rc = ozaki_qd_gemm_ws(m, l, n, A, B, C, S, ws, bytes, s);
+    int rc2 = workspace_release(ws, owned, s);
+    return rc ? rc : rc2;
+}
+
+int mpgemm_ozaki_split_terms(int terms, int by_col, int64_t rows, int64_t cols, const double* X, int num_slices,
+                             int* expo, void* digits, void* stream) {
+    if (terms != 4) return MPGEMM_EUNSUPPORTED;
+    const int S = num_slices <= 0 ? 44 : num_slices;
+    if (rows <= 0 || cols <= 0 || !X || !expo || !digits || S < 1 || S > QD_SMAX) return MPGEMM_EINVAL;
+    if ((rows > 65535 && !by_col) || (cols > 65535 && by_col)) return MPGEMM_EUNSUPPORTED;
+    PartitionScope pscope((cudaStream_t)stream);
+    return split_terms(terms, by_col, rows, cols, X, S, expo, digits, ozaki_padded_k(by_col ? rows : cols),
+                       (cudaStream_t)stream);
+}
 
 int mpgemm_ozaki_slices_default(void) { return 16; }
 

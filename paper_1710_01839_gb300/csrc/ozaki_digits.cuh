@@ -133,4 +133,107 @@ MPG_HD void b32_bias(int S, unsigned long long& Ch, unsigned long long& Cl) {
     }
 }
 
+// ---- T-term expansions (QD: T = 4) on NW 64-bit words.
+//
+// floor(|x| 2^sc) for a canonical expansion x = x_0 + ... + x_{T-1} (each
+// term at most half an ulp of the one before, as the QD library keeps
+// them): with y_t = sign(x) x_t, the terms that are integers after scaling
+// add exactly; the first term with a fractional part adds its floor and
+// ends the sum, because everything after it is smaller than half its ulp
+// and so cannot move the floor.  The result is below 2^(64 NW).
+template <int NW>
+struct WideB32 {
+    unsigned long long w[NW];
+    bool neg;
+};
+
+// v += (neg ? -1 : 1) * M 2^q, 0 <= q < 64 NW.
+template <int NW>
+MPG_HD void wide_add_shifted(unsigned long long (&v)[NW], unsigned long long M, int q, bool neg) {
+    const int k = q >> 6, b = q & 63;
+    unsigned long long t[NW];
+    for (int i = 0; i < NW; i++) t[i] = 0ull;
+    if (k < NW) t[k] = M << b;
+    if (b && k + 1 < NW) t[k + 1] = M >> (64 - b);
+    unsigned long long c = neg ? 1ull : 0ull;   // two's complement of t when subtracting
+    for (int i = 0; i < NW; i++) {
+        const unsigned long long x = neg ? ~t[i] : t[i];
+        const unsigned long long s1 = v[i] + x;
+        const unsigned long long c1 = s1 < v[i] ? 1ull : 0ull;
+        const unsigned long long s2 = s1 + c;
+        const unsigned long long c2 = s2 < s1 ? 1ull : 0ull;
+        v[i] = s2;
+        c = c1 | c2;
+    }
+}
+
+template <int T, int NW>
+MPG_HD void expansion_trunc_scaled(const double (&x)[T], int sc, WideB32<NW>& r) {
+    bool sigma = false;   // sign of the expansion: that of its first nonzero term
+    for (int t = T - 1; t >= 0; t--)
+        if ((dbl_bits(x[t]) << 1) != 0ull) sigma = (dbl_bits(x[t]) >> 63) != 0ull;
+    for (int i = 0; i < NW; i++) r.w[i] = 0ull;
+    r.neg = sigma;
+    for (int t = 0; t < T; t++) {
+        unsigned long long M;
+        int p;
+        bool s;
+        dbl_decode(x[t], M, p, s);
+        if (M == 0ull) continue;
+        const bool sub = s != sigma;
+        const int q = p + sc;
+        if (q >= 0) {
+            if (q < 64 * NW) wide_add_shifted<NW>(r.w, M, q, sub);
+            continue;
+        }
+        const unsigned long long ip = q > -64 ? M >> (-q) : 0ull;
+        if (!frac_bits(M, q)) {
+            if (ip) wide_add_shifted<NW>(r.w, ip, 0, sub);
+            continue;
+        }
+        // the first term with a fraction: floor(y_t 2^sc), then stop
+        if (!sub) {
+            if (ip) wide_add_shifted<NW>(r.w, ip, 0, false);
+        } else {
+            wide_add_shifted<NW>(r.w, ip + 1ull, 0, true);
+        }
+        break;
+    }
+}
+
+// C = 16 (1 + 32 + ... + 32^(S-2)) on NW words.
+template <int NW>
+MPG_HD void b32_bias_wide(int S, unsigned long long (&C)[NW]) {
+    for (int i = 0; i < NW; i++) C[i] = 0ull;
+    for (int k = 0; k < S - 1; k++) {
+        const int b = 5 * k + 4;
+        C[b >> 6] |= 1ull << (b & 63);
+    }
+}
+
+template <int NW>
+MPG_HD void b32_prepare_wide(WideB32<NW>& u, const unsigned long long (&C)[NW]) {
+    unsigned long long c = 0ull;
+    for (int i = 0; i < NW; i++) {
+        const unsigned long long s1 = u.w[i] + C[i];
+        const unsigned long long c1 = s1 < u.w[i] ? 1ull : 0ull;
+        const unsigned long long s2 = s1 + c;
+        const unsigned long long c2 = s2 < s1 ? 1ull : 0ull;
+        u.w[i] = s2;
+        c = c1 | c2;
+    }
+}
+
+// 5-bit field K of U (K compile-time).
+template <int K, int NW>
+MPG_HD int b32_field_wide(const WideB32<NW>& u) {
+    constexpr int b = 5 * K, k = b >> 6, r = b & 63;
+    if constexpr (r <= 59) {
+        return (int)((u.w[k] >> r) & 31ull);
+    } else {
+        const unsigned long long hi = k + 1 < NW ? u.w[k + 1] : 0ull;
+        return (int)(((u.w[k] >> r) | (hi << (64 - r))) & 31ull);
+    }
+}
+
 }  // namespace mpg

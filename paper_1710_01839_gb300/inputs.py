@@ -151,6 +151,18 @@ def dd_rowcol_scaled(m: int, l: int, n: int, seed: int, spread: int = 16, inner_
     return np.ascontiguousarray(A), np.ascontiguousarray(B)
 
 
+def qd_rowcol_scaled(m: int, l: int, n: int, seed: int, spread: int = 16):
+    """Split-precision QD workload: QD A (m x l) with row i scaled by 2^{r_i},
+    QD B (l x n) with column j scaled by 2^{c_j}, r, c ~ U{-spread..spread}."""
+    rng = np.random.default_rng(seed)
+    A = qd_random(m, l, seed + 1)
+    B = qd_random(l, n, seed + 2)
+    r = rng.integers(-spread, spread + 1, size=m)
+    c = rng.integers(-spread, spread + 1, size=n)
+    return (np.ascontiguousarray(np.ldexp(A, r[None, :, None])),
+            np.ascontiguousarray(np.ldexp(B, c[None, None, :])))
+
+
 # ----------------------------------------------------------------------------
 # integer-valued matrices (exact in every format)
 # ----------------------------------------------------------------------------

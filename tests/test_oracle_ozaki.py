@@ -161,3 +161,73 @@ def test_b32_pipeline_recombination_and_bound():
     assert np.array_equal(C, oracle.ozaki_gemm_b32(A, B, S))
     errs = {s: _max_rel_err(A, B, oracle.ozaki_gemm_b32(A, B, s)) for s in (12, 18, 22)}
     assert errs[22] <= 2.0**-100 and errs[22] <= errs[18] <= errs[12]
+
+
+# ---------------------------------------------------------------- expansions of T terms (QD)
+
+def test_terms_digits_equal_dd_digits():
+    """Two implementations of one definition: the exact-sum digit routine on
+    DD inputs reproduces the DD digit routine (S exact base-32 steps)."""
+    A, _ = I.dd_rowcol_scaled(9, 14, 4, seed=16)
+    A[:, 2, :] = 0.0
+    A[0, 3, 5] = 3.0                     # integer-valued entries with a small lo of either sign
+    A[1, 3, 5] = -2.0**-60
+    A[0, 3, 6] = -5.0
+    A[1, 3, 6] = 2.0**-58
+    e = oracle.ozaki_row_expo(A)
+    for S in (1, 7, 22, 24):
+        assert np.array_equal(oracle.ozaki_slice_b32_terms(A, e, S, by_col=False),
+                              oracle.ozaki_slice_b32(A, e, S, by_col=False))
+    f = oracle.ozaki_col_expo(A)
+    assert np.array_equal(oracle.ozaki_slice_b32_terms(A, f, 22, by_col=True),
+                          oracle.ozaki_slice_b32(A, f, 22, by_col=True))
+
+
+@pytest.mark.parametrize("S", [1, 10, 48, 52])
+def test_qd_digits_are_exact_balanced_truncation(S):
+    A, _ = I.qd_rowcol_scaled(5, 9, 3, seed=17)
+    A[:, 1, 4] = 0.0
+    A[2:, 3, :] = 0.0                    # DD-like rows
+    e = oracle.ozaki_row_expo(A)
+    D = oracle.ozaki_slice_b32_terms(A, e, S, by_col=False)
+    assert np.abs(D.astype(np.int64)).max() <= 16
+    for i in range(5):
+        for k in range(9):
+            x = value(A[:, i, k]) * Fraction(2) ** -(int(e[i]) + 1)
+            assert abs(x) < Fraction(1, 2)
+            scaled = x * (1 << (5 * S))
+            trunc = (abs(scaled.numerator) // scaled.denominator) * (1 if x >= 0 else -1)
+            got = sum(int(D[s, i, k]) * (32 ** (S - 1 - s)) for s in range(S))
+            assert got == trunc
+
+
+def test_recombine_terms_two_equals_dd_recombination():
+    S = 12
+    A, B = I.dd_rowcol_scaled(7, 11, 6, seed=18)
+    e, f = oracle.ozaki_row_expo(A), oracle.ozaki_col_expo(B)
+    L = oracle.ozaki_levels(oracle.ozaki_slice_b32(A, e, S, False), oracle.ozaki_slice_b32(B, f, S, True), S)
+    assert np.array_equal(oracle.ozaki_recombine_terms(L, e, f, S, 2), oracle.ozaki_recombine_bits(L, e, f, S, 5, 1))
+    C4 = oracle.ozaki_recombine_terms(L, e, f, S, 4)
+    for i in (0, 6):
+        for j in (0, 5):
+            x = sum((Fraction(int(L[g, i, j])) * Fraction(2) ** (int(e[i]) + int(f[j]) + 2 - 5 * g)
+                     for g in range(2, S + 2)), Fraction(0))
+            assert C4[:, i, j].tolist() == greedy(x, 4)
+    assert np.array_equal(oracle.ozaki_gemm_b32_terms(A, B, 22), oracle.ozaki_gemm_b32(A, B, 22))
+
+
+def test_qd_split_exact_on_integers_and_within_qd_bound():
+    a, b = I.int_matrix(8, 12, 31, -1000, 1000), I.int_matrix(12, 7, 32, -1000, 1000)
+    C = oracle.ozaki_gemm_b32_terms(I.ints_to_qd(a), I.ints_to_qd(b), 10)
+    assert np.array_equal(C[0], (a @ b).astype(np.float64)) and not C[1:].any()
+    m, l, n = 10, 16, 9
+    A, B = I.qd_rowcol_scaled(m, l, n, seed=19, spread=4)
+    C = oracle.ozaki_gemm_b32_terms(A, B, 48)
+    errs = []
+    for i in range(m):
+        for j in range(n):
+            ex = sum((value(A[:, i, k]) * value(B[:, k, j]) for k in range(l)), Fraction(0))
+            absab = sum((abs(value(A[:, i, k]) * value(B[:, k, j])) for k in range(l)), Fraction(0))
+            errs.append(abs(value(C[:, i, j]) - ex) / absab)
+    # the QD tolerance 4 l 2^-208 |A||B|
+    assert max(errs) <= 4 * l * Fraction(2) ** -208
