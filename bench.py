@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--ozaki-slices", type=int, default=16)
     ap.add_argument("--batched-count", type=int, default=512)
     ap.add_argument("--ozaki-fp8-slices", type=int, default=22)
+    ap.add_argument("--qd-split-n", type=int, default=1024)
+    ap.add_argument("--qd-split-slices", type=int, default=44)
     return ap.parse_args()
 
 
@@ -177,6 +179,55 @@ def split_precision_extra(args, stream):
                                "frac": f8_flops / (f8_kms * 1e-3) / 1e12 / E4M3_PEAK_TFLOPS,
                                "kernel": f"k_levels_tc (tcgen05 kind::f8f6f4), {pairs8} slice pairs x 2 n^2 l",
                                "kernel_ms": f8_kms, "kernel_share": f8_kms / f8_ms}}
+    return out
+
+
+def qd_split_extra(args, stream):
+    """Split-precision QD GEMM (FP8 digits of 4-term expansions, tcgen05)
+    against the plain FP64-pipe QD kernels on the same QD inputs (the large
+    QD workload: m = l = n = qd_split_n, per-element exponents 2^U{-20..20}).
+    Accuracy (<= 4 l 2^-208 |A||B|) is asserted by the parity tests."""
+    import ctypes
+    import torch
+    import paper_1710_01839_gb300 as mpg
+    n, S = args.qd_split_n, args.qd_split_slices
+    A, B = inputs_for("qd", n)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    Cd = torch.empty_like(Ad)
+    L = mpg.lib()
+
+    def timed(fn, steps):
+        fn()
+        torch.cuda.synchronize()
+        L.mpgemm_profile(1)
+        L.mpgemm_profile_read(None, None)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, kl = ctypes.c_double(), ctypes.c_int()
+        L.mpgemm_profile_read(ctypes.byref(kms), ctypes.byref(kl))
+        L.mpgemm_profile(0)
+        return e0.elapsed_time(e1) / steps, kms.value / max(kl.value, 1)
+
+    flops = 2.0 * n ** 3
+    sp_ms, sp_kms = timed(lambda: mpg.gemm_split(Ad, Bd, Cd, slices=S), 3)
+    lp = (n + 127) // 128 * 128
+    tc_flops = 2.0 * n * n * lp * S * (S + 1) / 2
+    out = {"workload": f"QD m=l=n={n}, per-element exponents 2^U{{-20..20}}, S={S} e4m3 slices",
+           "qd_split_gflops": flops / (sp_ms * 1e-3) / 1e9, "qd_split_ms": sp_ms,
+           "roofline": {"bound": "tensor", "unit": "TFLOP/s (e4m3)",
+                        "achieved": tc_flops / (sp_kms * 1e-3) / 1e12, "peak": E4M3_PEAK_TFLOPS,
+                        "peak_note": E4M3_PEAK_NOTE, "frac": tc_flops / (sp_kms * 1e-3) / 1e12 / E4M3_PEAK_TFLOPS,
+                        "kernel": f"k_levels_tc (tcgen05 kind::f8f6f4), {S * (S + 1) // 2} slice pairs x 2 n^2 l",
+                        "kernel_ms": sp_kms, "kernel_share": sp_kms / sp_ms}}
+    for name, algo, nm, d in (("plain_qd_block", "block", 32, 0), ("plain_qd_strassen3", "strassen", 16, 3)):
+        ms, _ = timed(lambda: mpg.gemm_qd(Ad, Bd, Cd, algo=algo, n_min=nm, depth=d), 1)
+        out[name + "_gflops"] = flops / (ms * 1e-3) / 1e9
+        out[name + "_ms"] = ms
+    out["speedup_vs_best_plain_qd"] = min(out["plain_qd_block_ms"], out["plain_qd_strassen3_ms"]) / sp_ms
     return out
 
 
@@ -542,9 +593,10 @@ def main():
                "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(Ch.numel() * Ch.element_size()),
                "ms_per_step": e_ms / args.steps}
 
-    extras = bextra = None
+    extras = bextra = qextra = None
     if not args.no_extras and fmt == "dd":
         extras = split_precision_extra(args, stream)
+        qextra = qd_split_extra(args, stream)
         bextra = batched_extra(args, stream)
 
     if dist:
@@ -571,6 +623,8 @@ def main():
         line["tuning"] = tune_info
     if extras is not None:
         line["split_precision"] = extras
+    if qextra is not None:
+        line["qd_split_precision"] = qextra
     if bextra is not None:
         line["batched"] = bextra
     print(json.dumps(line), flush=True)

@@ -365,7 +365,9 @@ int mpgemm_selftest_wait_timeout(int limit_ms, void* stream);
  *                                invalid arguments).
  *   mpgemm_select_precision      the configurations with log2(beta) <=
  *                                log2_target (split precision with the
- *                                fewest slices, the smallest multi-limb
+ *                                fewest slices; the QD split only when
+ *                                no DD split meets the target; the
+ *                                smallest multi-limb
  *                                precision of 128..1024 bits), fastest
  *                                first by predicted time (the installed cost
  *                                model's best simple/block configuration,
@@ -382,7 +384,8 @@ enum {
     MPGEMM_SEL_QD = 1,
     MPGEMM_SEL_MP = 2,
     MPGEMM_SEL_OZAKI_INT8 = 3,
-    MPGEMM_SEL_OZAKI_E4M3 = 4
+    MPGEMM_SEL_OZAKI_E4M3 = 4,
+    MPGEMM_SEL_OZAKI_QD = 5   /* split-precision QD (mpgemm_qd_ozaki), e4m3 digits, final rounding 2^-211 */
 };
 typedef struct {
     int method;          /* MPGEMM_SEL_*                                  */

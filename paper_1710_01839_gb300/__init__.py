@@ -149,7 +149,7 @@ def strerror(status):
     return lib().mpgemm_strerror(int(status)).decode()
 
 
-SEL_METHOD = {0: "dd", 1: "qd", 2: "mp", 3: "ozaki_int8", 4: "ozaki_e4m3"}
+SEL_METHOD = {0: "dd", 1: "qd", 2: "mp", 3: "ozaki_int8", 4: "ozaki_e4m3", 5: "ozaki_qd"}
 _SEL_CODE = {v: k for k, v in SEL_METHOD.items()}
 
 

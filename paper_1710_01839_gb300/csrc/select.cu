@@ -16,7 +16,8 @@
 //                           triangle s + t > S + 1 at most
 //                           (S + 1) c 2^(2 spread + 2 - bS) (c = 1.02 / 1.07
 //                           for b = 7 / 5), the final DD rounding 2^-106:
-//                           beta = 2t + t^2 + triangle + 2^-106.
+//                           beta = 2t + t^2 + triangle + 2^-106 (DD result;
+//                           2^-211 for the QD result of the QD split).
 // Strassen is left out: its bound (2^-96 l max|A| max|B| for DD) is not
 // elementwise.  Predicted times: the installed cost model's best simple /
 // block configuration for DD, QD and multi-limb, else the block rates
@@ -49,11 +50,12 @@ double log2_sum(std::initializer_list<double> xs) {
     return mx + std::log2(s);
 }
 
-double split_log2_bound(int digit_bits, int S, int spread) {
+// final_log2: the rounding of the exact result (DD: 2^-106, QD: 2^-211).
+double split_log2_bound(int digit_bits, int S, int spread, double final_log2 = -106.0) {
     const double t = (digit_bits == 7 ? spread + 1.0 : spread + 2.0) - (double)digit_bits * S;
     const double c = digit_bits == 7 ? 1.02 : 1.07;
     const double tri = std::log2((S + 1) * c) + 2.0 * spread + 2.0 - (double)digit_bits * S;
-    return log2_sum({1.0 + t, 2.0 * t, tri, -106.0});
+    return log2_sum({1.0 + t, 2.0 * t, tri, final_log2});
 }
 
 // Block-algorithm rates measured on GB300 (effective GFLOP/s, 1024-2048).
@@ -68,12 +70,12 @@ double static_block_gflops(int method, int bits) {
     }
 }
 
-double split_ms(int digit_bits, int S, int64_t m, int64_t l, int64_t n) {
+double split_ms(int digit_bits, int S, int64_t m, int64_t l, int64_t n, int terms = 2) {
     const double lp = (double)((l + 127) / 128 * 128);
     const double ops = 2.0 * (double)m * (double)n * lp * S * (S + 1) / 2.0;
     const double rate = digit_bits == 5 ? 3.4e15 : 1.5e14;   // k_levels_tc / k_ozaki_levels, measured
-    const double bytes = 16.0 * ((double)m * l + (double)l * n) + (double)S * (m + n) * lp +
-                         8.0 * S * (double)m * n + 16.0 * (double)m * n;
+    const double bytes = 8.0 * terms * ((double)m * l + (double)l * n) + (double)S * (m + n) * lp +
+                         8.0 * S * (double)m * n + 8.0 * terms * (double)m * n;
     return 1e3 * (ops / rate + bytes / 3.0e12) + 0.05;
 }
 
@@ -154,6 +156,8 @@ double mpgemm_precision_log2_bound(int method, int prec_bits, int num_slices, in
             return (num_slices >= 1 && num_slices <= 18) ? split_log2_bound(7, num_slices, spread) : NAN;
         case MPGEMM_SEL_OZAKI_E4M3:
             return (num_slices >= 1 && num_slices <= 24) ? split_log2_bound(5, num_slices, spread) : NAN;
+        case MPGEMM_SEL_OZAKI_QD:
+            return (num_slices >= 1 && num_slices <= 48) ? split_log2_bound(5, num_slices, spread, -211.0) : NAN;
         default: return NAN;
     }
 }
@@ -217,6 +221,18 @@ int mpgemm_select_precision(double log2_target, int64_t m, int64_t l, int64_t n,
             const double b = mpgemm_precision_log2_bound(method, 0, S, l, spread);
             if (b <= log2_target) {
                 cs.push_back({method, 0, S, b, split_ms(db, S, m, l, n)});
+                break;
+            }
+        }
+    }
+    // QD split (QD operands and result): only for targets the DD splits cannot reach
+    bool dd_split = false;
+    for (const Cand& c : cs) dd_split |= c.method == MPGEMM_SEL_OZAKI_E4M3 || c.method == MPGEMM_SEL_OZAKI_INT8;
+    if (!dd_split && l <= 65536 && 48.0 * 256.0 * (double)l < 2147483648.0) {
+        for (int S = 1; S <= 48; S++) {
+            const double b = mpgemm_precision_log2_bound(MPGEMM_SEL_OZAKI_QD, 0, S, l, spread);
+            if (b <= log2_target) {
+                cs.push_back({MPGEMM_SEL_OZAKI_QD, 0, S, b, split_ms(5, S, m, l, n, 4)});
                 break;
             }
         }

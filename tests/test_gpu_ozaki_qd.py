@@ -94,3 +94,15 @@ def test_qd_split_arguments():
     assert L.mpgemm_qd_ozaki_slices_default() == 44
     assert L.mpgemm_ozaki_split_terms(2, 0, 4, 4, ctypes.c_void_p(16), 10, ctypes.c_void_p(16),
                                       ctypes.c_void_p(16), None) == -2
+
+
+def test_qd_split_bound_on_the_qd_workload():
+    """The large QD workload (per-element exponents 2^U{-20..20}, as the plain
+    QD kernels are benchmarked) at 1024^3 with the default 44 slices."""
+    n = 1024
+    A = I.qd_random(n, n, I.seed_for(1, 0), exp_spread=20)
+    B = I.qd_random(n, n, I.seed_for(1, 1), exp_spread=20)
+    C = host(mpg.gemm_split(dev(A), dev(B)))
+    ii, jj = sample_indices(n, n, 256, seed=45)
+    err, absab = oracle.exact_check(A, B, C, ii, jj)
+    assert np.max(err / absab) <= 4 * n * 2.0**-208

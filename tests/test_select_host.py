@@ -63,6 +63,10 @@ def test_ranking_and_minimality(built):
             assert built.precision_log2_bound(x["method"], 4096, num_slices=x["num_slices"] - 1) > -100
     # a loose target lets DD in; a tight one leaves only the wide formats
     assert "dd" in {x["method"] for x in built.select_precision(-80, 1024, 1024, 1024)}
+    qd = {x["method"]: x for x in built.select_precision(-200, 1024, 1024, 1024)}
+    assert qd["ozaki_qd"]["num_slices"] == 42 and list(qd)[0] == "ozaki_qd"   # the QD split is fastest
+    assert "ozaki_e4m3" not in qd and "dd" not in qd
+    assert built.precision_log2_bound("ozaki_qd", 1024, num_slices=48) >= -211 - 1e-9
     tight = built.select_precision(-400, 256, 256, 256)
     assert [(x["method"], x["prec_bits"]) for x in tight] == [("mp", 512)]
     assert built.select_precision(-2000, 64, 64, 64) == []
