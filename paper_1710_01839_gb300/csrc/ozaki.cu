@@ -559,6 +559,68 @@ __global__ void __launch_bounds__(OZ_THREADS) k_ozaki_levels(int64_t m, int64_t 
 
 // ---------------------------------------------------------------- step 4
 
+// V += x (a sign-extended int64) on NL 32-bit limbs, one carry chain.
+template <int NL>
+__device__ __forceinline__ void limbs_add_i64(uint32_t (&w)[NL], long long x);
+template <>
+__device__ __forceinline__ void limbs_add_i64<6>(uint32_t (&w)[6], long long x) {
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)((unsigned long long)x >> 32), ext = (uint32_t)(x >> 63);
+    asm("add.cc.u32 %0, %0, %6;\n\taddc.cc.u32 %1, %1, %7;\n\taddc.cc.u32 %2, %2, %8;\n\t"
+        "addc.cc.u32 %3, %3, %8;\n\taddc.cc.u32 %4, %4, %8;\n\taddc.u32 %5, %5, %8;"
+        : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5])
+        : "r"(lo), "r"(hi), "r"(ext));
+}
+template <>
+__device__ __forceinline__ void limbs_add_i64<10>(uint32_t (&w)[10], long long x) {
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)((unsigned long long)x >> 32), ext = (uint32_t)(x >> 63);
+    asm("add.cc.u32 %0, %0, %10;\n\taddc.cc.u32 %1, %1, %11;\n\taddc.cc.u32 %2, %2, %12;\n\t"
+        "addc.cc.u32 %3, %3, %12;\n\taddc.cc.u32 %4, %4, %12;\n\taddc.cc.u32 %5, %5, %12;\n\t"
+        "addc.cc.u32 %6, %6, %12;\n\taddc.cc.u32 %7, %7, %12;\n\taddc.cc.u32 %8, %8, %12;\n\t"
+        "addc.u32 %9, %9, %12;"
+        : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]), "+r"(w[6]), "+r"(w[7]),
+          "+r"(w[8]), "+r"(w[9])
+        : "r"(lo), "r"(hi), "r"(ext));
+}
+
+// V = sum_{g=2}^{S+1} L_g 2^(BITS (S + 1 - g)) as NW 64-bit words (two's
+// complement), computed on 2 NW 32-bit limbs.  Levels go in groups of G
+// (G BITS <= 30): a group's sum sum_j L_{g0+j} 2^(BITS (G' - 1 - j)) is
+// exact in an int64 (|L_g| < 2^31), then V <- V 2^(BITS G') + group with
+// funnel shifts and one carry chain; a group's loads are issued together.
+// Used for QD (10 limbs), where it cuts the wide steps by G; the DD kernel
+// keeps one level per step (measured faster on 6 limbs).
+template <int BITS, int NW, int G>
+__device__ __forceinline__ void horner_levels(const int* __restrict__ lp, int64_t mn, int S,
+                                              unsigned long long (&v)[NW]) {
+    static_assert(G >= 1 && G * BITS <= 30, "group shift must stay within one limb");
+    constexpr int NL = 2 * NW;
+    uint32_t w[NL];
+#pragma unroll
+    for (int q = 0; q < NL; q++) w[q] = 0u;
+    for (int g0 = 2; g0 <= S + 1; g0 += G) {
+        const int cnt = (S + 2 - g0) < G ? (S + 2 - g0) : G;
+        int x[G];
+#pragma unroll
+        for (int j = 0; j < G; j++) {   // unconditional loads (clamped plane), zeroed past the group
+            const int gi = (g0 - 2 + j) < S - 1 ? (g0 - 2 + j) : S - 1;
+            x[j] = lp[(int64_t)gi * mn];
+        }
+#pragma unroll
+        for (int j = 0; j < G; j++) x[j] = j < cnt ? x[j] : 0;
+        long long grp = 0;
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (j < cnt) grp = (long long)((unsigned long long)grp << BITS) + x[j];
+        const int sh = BITS * cnt;   // <= 30
+#pragma unroll
+        for (int q = NL - 1; q > 0; q--) w[q] = __funnelshift_l(w[q - 1], w[q], sh);
+        w[0] <<= sh;
+        limbs_add_i64<NL>(w, grp);
+    }
+#pragma unroll
+    for (int q = 0; q < NW; q++) v[q] = ((unsigned long long)w[2 * q + 1] << 32) | w[2 * q];
+}
+
 // v (192-bit two's complement, 3 limbs) += x * 2^sh, 0 <= sh < 128.
 __device__ __forceinline__ void add_shifted(unsigned long long (&v)[3], long long x, int sh) {
     unsigned long long w0 = (unsigned long long)x, ext = x < 0 ? ~0ull : 0ull;
@@ -641,8 +703,10 @@ __device__ __forceinline__ void neg192(unsigned long long (&v)[3]) {
 
 // bits = digit width (7 for int8, 5 for e4m3), head = headroom bits per side
 // (0 for int8, 1 for e4m3): x = 2^(e_i + f_j + 2 head) sum_g L_g 2^(-bits g).
-__global__ void k_recombine(int64_t m, int64_t n, int S, int bits, int head, const int* Lv, const int* e,
-                            const int* f, double* C) {
+template <int BITS>
+__global__ void k_recombine(int64_t m, int64_t n, int S, int head, const int* Lv, const int* e, const int* f,
+                            double* C) {
+    constexpr int bits = BITS;
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = blockIdx.y;
     if (j >= n) return;
@@ -761,35 +825,15 @@ __device__ __forceinline__ bool wide_any_below(const unsigned long long (&v)[NW]
 }
 
 template <int T>
-__global__ void k_recombine_terms(int64_t m, int64_t n, int S, int bits, int head, const int* Lv, const int* e,
-                                  const int* f, double* C) {
-    constexpr int NW = 5;
+__global__ void k_recombine_terms(int64_t m, int64_t n, int S, int head, const int* Lv, const int* e, const int* f,
+                                  double* C) {
+    constexpr int NW = 5, bits = 5;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = blockIdx.y;
     if (j >= n) return;
     const int64_t mn = m * n, idx = i * n + j;
     unsigned long long v[NW];
-#pragma unroll
-    for (int q = 0; q < NW; q++) v[q] = 0ull;
-    const int* lp = Lv + idx;
-    for (int g = 2; g <= S + 1; g++) {
-        const long long x = lp[(int64_t)(g - 2) * mn];
-#pragma unroll
-        for (int q = NW - 1; q > 0; q--) v[q] = (v[q] << bits) | (v[q - 1] >> (64 - bits));
-        v[0] <<= bits;
-        const unsigned long long ext = x < 0 ? ~0ull : 0ull;
-        unsigned long long c = 0ull;
-#pragma unroll
-        for (int q = 0; q < NW; q++) {
-            const unsigned long long a = q == 0 ? (unsigned long long)x : ext;
-            const unsigned long long s1 = v[q] + a;
-            const unsigned long long c1 = s1 < v[q] ? 1ull : 0ull;
-            const unsigned long long s2 = s1 + c;
-            const unsigned long long c2 = s2 < s1 ? 1ull : 0ull;
-            v[q] = s2;
-            c = c1 | c2;
-        }
-    }
+    horner_levels<5, NW, 6>(Lv + idx, mn, S, v);
     const int E = e[i] + f[j] + 2 * head - bits * (S + 1);
 #pragma unroll
     for (int t = 0; t < T; t++) {
@@ -929,7 +973,8 @@ int ozaki_levels(int kind, int64_t m, int64_t n, int64_t lp, int S, const void* 
 int ozaki_recombine(int kind, int64_t m, int64_t n, int S, const int* Lv, const int* e, const int* f, double* C,
                     cudaStream_t s) {
     dim3 g(ceil_div(n, 128), (unsigned)m);
-    k_recombine<<<g, 128, 0, s>>>(m, n, S, digit_bits(kind), digit_head(kind), Lv, e, f, C);
+    if (digit_bits(kind) == 5) k_recombine<5><<<g, 128, 0, s>>>(m, n, S, digit_head(kind), Lv, e, f, C);
+    else k_recombine<7><<<g, 128, 0, s>>>(m, n, S, digit_head(kind), Lv, e, f, C);
     return check_launch();
 }
 
@@ -974,7 +1019,7 @@ static int ozaki_qd_gemm_ws(int64_t m, int64_t l, int64_t n, const double* A, co
     if ((rc = split_terms(4, 1, l, n, B, S, f, DB, lp, s))) return rc;
     if ((rc = tc_levels(m, n, lp, S, DA, DB, Lv, s))) return rc;
     dim3 g(ceil_div(n, 128), (unsigned)m);
-    k_recombine_terms<4><<<g, 128, 0, s>>>(m, n, S, 5, 1, Lv, e, f, C);
+    k_recombine_terms<4><<<g, 128, 0, s>>>(m, n, S, 1, Lv, e, f, C);
     return check_launch();
 }
 
