@@ -53,7 +53,7 @@ ISSUE_PEAK_GWIPS = 4 * 152 * 2.070
 # Multi-limb thread-instructions per multiply-accumulate (ncu
 # smsp__inst_executed x 32 / MACs of the block kernel k_mp_block on 256^3
 # (2048 bits: 128^3) inputs of the multi-limb workload), by precision in bits.
-MP_INSTR_PER_MAC = {128: 333.3, 256: 619.3, 512: 1504.2, 1024: 4418.7, 2048: 59352.9}
+MP_INSTR_PER_MAC = {128: 302.7, 256: 546.9, 512: 1356.4, 1024: 4104.2, 2048: 58515.5}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from ncu captures of exactly these configurations (profiles/):
 # (fmt, n, algo, n_min, depth) -> bytes.  Absent => null.

@@ -209,7 +209,16 @@ MP_UNROLL
     X[N - 1] = 0u;
     Y[N - 1] = 0u;
     uint32_t sticky = 0u;
-    shr_sticky<N>(Y, (int)d, sticky);
+    if (d < 32) {
+        // the common GEMM case: no limb moves, and the two guard limbs keep
+        // every shifted-out bit (no sticky)
+        const int r = (int)d;
+MP_UNROLL
+        for (int i = 0; i < N - 1; i++) Y[i] = __funnelshift_r(Y[i], Y[i + 1], r);
+        Y[N - 1] >>= r;
+    } else {
+        shr_sticky<N>(Y, (int)d, sticky);
+    }
     const bool stk = sticky != 0u;
     uint32_t S[N];
     unsigned sign = sx;
@@ -257,13 +266,24 @@ MP_UNROLL
         S[N - 1] >>= 1;
         e = (long long)ex + 1;
     } else {
-        // leading bit to position p + 63 (top of limb N-2)
-        int L = 0;
+        // leading bit to position p + 63 (top of limb N-2); a shift of 0 or 1
+        // (no cancellation of the leading bits) is the common case
+        int s;
+        if (S[N - 2] >> 30) {
+            s = (S[N - 2] >> 31) ? 0 : 1;
+            if (s) {
 MP_UNROLL
-        for (int i = 0; i < N - 1; i++)
-            if (S[i]) L = 32 * i + 32 - __clz(S[i]);
-        int s = p + 64 - L;
-        shl<N>(S, s);
+                for (int i = N - 1; i > 0; i--) S[i] = __funnelshift_l(S[i - 1], S[i], 1);
+                S[0] <<= 1;
+            }
+        } else {
+            int L = 0;
+MP_UNROLL
+            for (int i = 0; i < N - 1; i++)
+                if (S[i]) L = 32 * i + 32 - __clz(S[i]);
+            s = p + 64 - L;
+            shl<N>(S, s);
+        }
         e = (long long)ex - s;
         sticky = 0u;
     }
