@@ -213,7 +213,7 @@ def qd_split_extra(args, stream):
         return e0.elapsed_time(e1) / steps, kms.value / max(kl.value, 1)
 
     flops = 2.0 * n ** 3
-    sp_ms, sp_kms = timed(lambda: mpg.gemm_split(Ad, Bd, Cd, slices=S), 3)
+    sp_ms, sp_kms = timed(lambda: mpg.gemm_split(Ad, Bd, Cd, slices=S), 10)
     lp = (n + 127) // 128 * 128
     tc_flops = 2.0 * n * n * lp * S * (S + 1) / 2
     out = {"workload": f"QD m=l=n={n}, per-element exponents 2^U{{-20..20}}, S={S} e4m3 slices",

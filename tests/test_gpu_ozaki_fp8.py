@@ -145,3 +145,14 @@ def test_fp8_rejects_too_long_inner_dimension():
     assert L.mpgemm_dd_ozaki_ex(4, 70000, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 22,
                                 E4M3, None) == -2
     assert L.mpgemm_dd_ozaki_ex(4, 4, 4, None, None, None, 25, E4M3, None) == -1
+
+
+def test_fp8_maximum_inner_dimension_and_degenerate_shapes():
+    """l = 65536, the largest inner dimension whose slice-pair sums stay
+    exact in f32 (Q = 1: every pair is its own chunk, added chunk by chunk),
+    and 1 x 1 x 1 / 1 x l x 1 products."""
+    A, B = I.dd_rowcol_scaled(3, 65536, 2, seed=71)
+    assert np.array_equal(_ozaki_fp8(A, B, 8), oracle.ozaki_gemm_b32(A, B, 8))
+    for (m, l, n) in [(1, 1, 1), (1, 300, 1), (2, 1, 3)]:
+        A, B = I.dd_rowcol_scaled(m, l, n, seed=72 + l)
+        assert np.array_equal(_ozaki_fp8(A, B, 22), oracle.ozaki_gemm_b32(A, B, 22))

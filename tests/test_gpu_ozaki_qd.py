@@ -106,3 +106,17 @@ def test_qd_split_bound_on_the_qd_workload():
     ii, jj = sample_indices(n, n, 256, seed=45)
     err, absab = oracle.exact_check(A, B, C, ii, jj)
     assert np.max(err / absab) <= 4 * n * 2.0**-208
+
+
+def test_qd_split_maximum_inner_dimension_and_degenerate_shapes():
+    A, B = I.qd_rowcol_scaled(2, 65536, 2, seed=73)
+    C = host(mpg.gemm_split(dev(A), dev(B), slices=6))
+    assert np.array_equal(C, oracle.ozaki_gemm_b32_terms(A, B, 6))
+    for (m, l, n) in [(1, 1, 1), (1, 130, 1), (3, 1, 2)]:
+        A, B = I.qd_rowcol_scaled(m, l, n, seed=74 + l)
+        C = host(mpg.gemm_split(dev(A), dev(B), slices=44))
+        assert np.array_equal(C, oracle.ozaki_gemm_b32_terms(A, B, 44))
+    import torch
+    Z = torch.zeros((4, 3, 0), dtype=torch.float64, device="cuda")
+    Z2 = torch.zeros((4, 0, 5), dtype=torch.float64, device="cuda")
+    assert not host(mpg.gemm_split(Z, Z2)).any()              # empty inner dimension: C = 0

@@ -59,3 +59,16 @@ def test_noalloc_refuses_problems_beyond_its_scratch():
     assert torch.isnan(Cd).all()
     rc, _ = _noalloc(Ad[:, :64, :64].contiguous(), Bd[:, :64, :64].contiguous(), 16, 0)
     assert rc == -1   # depth 0 is not a Strassen call
+
+
+def test_noalloc_odd_sizes_match_allocating_entry_point():
+    """Sizes 2^depth does not divide are zero-extended, here as in mpgemm_dd:
+    the same kernels on the same extended problem give the same bits."""
+    m, l, n, depth = 253, 255, 257, 2
+    A = I.dd_random(m, l, 821, exp_spread=20)
+    B = I.dd_random(l, n, 822, exp_spread=20)
+    Ad, Bd = dev(A), dev(B)
+    want = host(mpg.gemm_dd(Ad, Bd, algo="strassen", n_min=32, depth=depth))
+    rc, Cd = _noalloc(Ad, Bd, 32, depth)
+    assert rc == 0, mpg.strerror(rc)
+    assert np.array_equal(host(Cd), want)
