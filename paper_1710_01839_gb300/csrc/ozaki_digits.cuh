@@ -151,13 +151,12 @@ struct WideB32 {
 template <int NW>
 MPG_HD void wide_add_shifted(unsigned long long (&v)[NW], unsigned long long M, int q, bool neg) {
     const int k = q >> 6, b = q & 63;
-    unsigned long long t[NW];
-    for (int i = 0; i < NW; i++) t[i] = 0ull;
-    if (k < NW) t[k] = M << b;
-    if (b && k + 1 < NW) t[k + 1] = M >> (64 - b);
-    unsigned long long c = neg ? 1ull : 0ull;   // two's complement of t when subtracting
+    const unsigned long long lo = M << b, hi = b ? M >> (64 - b) : 0ull;
+    unsigned long long c = neg ? 1ull : 0ull;   // two's complement of the addend when subtracting
     for (int i = 0; i < NW; i++) {
-        const unsigned long long x = neg ? ~t[i] : t[i];
+        // word i of M 2^q, by selects (no dynamically indexed array)
+        const unsigned long long ti = i == k ? lo : (i == k + 1 ? hi : 0ull);
+        const unsigned long long x = neg ? ~ti : ti;
         const unsigned long long s1 = v[i] + x;
         const unsigned long long c1 = s1 < v[i] ? 1ull : 0ull;
         const unsigned long long s2 = s1 + c;
