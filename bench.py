@@ -182,6 +182,38 @@ def split_precision_extra(args, stream):
     return out
 
 
+def mlp_arm(fmt, Ad, Bd, Cd, gemm, tuned_ms, prec_bits):
+    """The selection's third arm (the paper times every candidate; the
+    prediction times samples; the FP32 MLP times nothing): the shipped cost
+    model's choice, the host time of that decision, the choice's measured
+    time and its regret against the tuned (measured) best."""
+    import torch
+    from paper_1710_01839_gb300 import costmodel
+    if not os.path.exists(costmodel.DEFAULT_MODEL):
+        return None
+    costmodel.load(costmodel.DEFAULT_MODEL)
+    m, l, n = Ad.shape[1], Ad.shape[2], Bd.shape[2]
+    t0 = time.perf_counter()
+    ch = costmodel.choice(fmt, m, l, n, prec_bits)
+    decision_ms = (time.perf_counter() - t0) * 1e3
+    if ch is None:
+        return None
+    run = lambda: gemm(Ad, Bd, Cd, algo=ch["algo"], n_min=ch["n_min"], depth=ch["depth"])
+    run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    return {"choice": {k: ch[k] for k in ("algo", "n_min", "depth")}, "predicted_ms": ch["pred_ms"],
+            "measured_ms": ms, "regret_vs_tuned": ms / tuned_ms - 1.0, "decision_ms": decision_ms}
+
+
 def qd_split_extra(args, stream):
     """Split-precision QD GEMM (FP8 digits of 4-term expansions, tcgen05)
     against the plain FP64-pipe QD kernels on the same QD inputs (the large
@@ -497,6 +529,7 @@ def main():
                                        prec_bits=args.prec if is_mp else 0)
         t_tune = time.perf_counter() - t0
         algo, n_min, depth = choice["algo"], choice["n_min"], choice["depth"]
+        tune_info["mlp"] = mlp_arm(fmt, Ad, Bd, Cd, gemm, tune_info["best_ms"], args.prec if is_mp else 0)
     else:
         algo, n_min, depth = args.algo, args.n_min, args.depth if args.algo == "strassen" else 0
 

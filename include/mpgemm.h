@@ -262,6 +262,11 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
  *   mpgemm_cost_save/load  binary model file; mpgemm_cost_clear uninstalls
  * ------------------------------------------------------------------------- */
 int mpgemm_cost_num_features(void);
+/* The installed model's choice for a problem on the stream's SMs (the
+   candidate of least predicted time, ignoring remembered tuner choices) and
+   its predicted time in ms; MPGEMM_EUNSUPPORTED when no model is installed. */
+int mpgemm_cost_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, void* stream, int* algo, int* n_min,
+                       int* depth, float* pred_ms);
 int mpgemm_cost_features(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo, int tile, int depth,
                          float* out);
 int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* features, float* times_ms,

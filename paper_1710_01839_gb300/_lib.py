@@ -47,6 +47,7 @@ SIGNATURES = {
     "mpgemm_version": (_I, []),
     "mpgemm_profile": (_I, [_I]),
     "mpgemm_cost_num_features": (_I, []),
+    "mpgemm_cost_choice": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _P, _P]),
     "mpgemm_cost_features": (_I, [_I, _I, _I64, _I64, _I64, _I, _I, _I, _P]),
     "mpgemm_cost_collect": (_I, [_I, ctypes.c_ulonglong, _I, _P, _P, _P]),
     "mpgemm_cost_train": (_I, [_P, _P, _I, _I, ctypes.c_ulonglong, _P]),

@@ -70,3 +70,17 @@ def load(path=DEFAULT_MODEL):
 
 def clear():
     lib().mpgemm_cost_clear()
+
+
+def choice(fmt, m, l, n, prec_bits=0, stream=None):
+    """The installed model's (algo, n_min, depth) and predicted ms for a
+    problem (mpgemm_cost_choice); None when no model is installed."""
+    algo, nm, d, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    sp = None if stream is None else ctypes.c_void_p(int(stream.cuda_stream))
+    rc = lib().mpgemm_cost_choice(KIND["mp" if fmt.startswith("mp") else fmt], int(prec_bits), int(m), int(l), int(n),
+                                  sp, ctypes.byref(algo), ctypes.byref(nm), ctypes.byref(d), ctypes.byref(ms))
+    if rc == -2:
+        return None
+    check(rc)
+    return {"algo": {0: "simple", 1: "block", 2: "strassen"}[algo.value], "n_min": nm.value, "depth": d.value,
+            "pred_ms": ms.value}

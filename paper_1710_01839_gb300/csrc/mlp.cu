@@ -283,7 +283,8 @@ static std::vector<Cand> candidates(int kind, int64_t m, int64_t l, int64_t n) {
     return c;
 }
 
-bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out) {
+bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out,
+                       float* pred_ms = nullptr) {
     {
         std::lock_guard<std::mutex> lk(g_mmu);
         if (!g_model.ready) return false;
@@ -297,6 +298,7 @@ bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n,
     out->algo = cs[best].algo;
     out->n_min = cs[best].tile;
     out->depth = cs[best].depth;
+    if (pred_ms) *pred_ms = T[best];
     return true;
 }
 
@@ -368,6 +370,21 @@ int mpgemm_cost_features(int kind, int prec_bits, int64_t m, int64_t l, int64_t 
 }
 
 int mpgemm_cost_num_features(void) { return NF; }
+
+int mpgemm_cost_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, void* stream, int* algo, int* n_min,
+                       int* depth, float* pred_ms) {
+    if (m <= 0 || l <= 0 || n <= 0 || !algo || !n_min || !depth) return MPGEMM_EINVAL;
+    if (kind < MPGEMM_KIND_DD || kind > MPGEMM_KIND_MP) return MPGEMM_EINVAL;
+    Choice c;
+    float ms = 0.f;
+    if (!cost_model_choice(kind, prec_bits, m, l, n, stream_sms((cudaStream_t)stream), &c, &ms))
+        return MPGEMM_EUNSUPPORTED;   // no model installed
+    *algo = c.algo;
+    *n_min = c.n_min;
+    *depth = c.depth;
+    if (pred_ms) *pred_ms = ms;
+    return MPGEMM_OK;
+}
 
 // Time `count` random configurations: shapes log-uniform in [16, max_dim],
 // format uniform over {DD, QD, 256-bit multi-limb}, algorithm / tile /

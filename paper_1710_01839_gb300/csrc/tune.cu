@@ -37,7 +37,8 @@ static std::mutex g_tmu;
 static std::map<Key, Choice> g_table;
 
 // Installed cost model (mlp.cu); returns false when none is installed.
-bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out);
+bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out,
+                       float* pred_ms = nullptr);
 
 int auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out) {
     {
