@@ -9,8 +9,11 @@ all of the device's SMs, on square DD, QD and 256-bit problems with the
 inputs of the large DD/QD and multi-limb workloads.
 
     python -m paper_1710_01839_gb300.partition_sweep [--out sweep.json]
+    python -m paper_1710_01839_gb300.partition_sweep --precisions [--out map.json]
 
-prints one markdown table and optionally writes the rows as JSON.
+prints one markdown table and optionally writes the rows as JSON; with
+--precisions it maps the fastest algorithm and the tuning time over the
+multi-limb precisions 128..2048 bits (the paper's Figure 2 and Table 4).
 """
 
 from __future__ import annotations
@@ -61,6 +64,45 @@ def sweep(fractions=(8, 4, 2, 1), sizes=None, flags=None):
     return rows
 
 
+def precision_sweep(precisions=(128, 256, 512, 1024, 2048), sizes=(128, 256, 512, 1024), max_2048=512):
+    """The paper's multi-precision map (its Figure 2 and Table 4): for every
+    multi-limb precision and size, the tuner's fastest algorithm, its time
+    and the tuner's own wall time, on the whole device (2048 bits up to
+    max_2048, its runs being long)."""
+    import numpy as np
+    import time
+    import torch
+    from . import inputs as I
+    from . import tuner
+    rows = []
+    for bits in precisions:
+        for n in sizes:
+            if bits == 2048 and n > max_2048:
+                continue
+            w = bits // 32
+            A = I.mp_random(n, n, w, 1710 + n).view(np.int32)
+            B = I.mp_random(n, n, w, 1711 + n).view(np.int32)
+            Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+            Cd = torch.empty_like(Ad)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            choice, rep = tuner.tune("mp", Ad, Bd, Cd, flags=tuner.QUICK, prec_bits=bits)
+            wall = time.perf_counter() - t0
+            rows.append({"bits": bits, "n": n, "algo": choice["algo"], "n_min": choice["n_min"],
+                         "depth": choice["depth"], "best_ms": rep["best_ms"], "tuning_s": wall,
+                         "gflops": 2.0 * n ** 3 / (rep["best_ms"] * 1e-3) / 1e9})
+    return rows
+
+
+def precision_table(rows):
+    lines = ["| bits | n | fastest | n_min | best ms | GFLOP/s | tuning s |", "|---|---|---|---|---|---|---|"]
+    for r in rows:
+        algo = r["algo"] + (f" d={r['depth']}" if r["algo"] == "strassen" else "")
+        lines.append(f"| {r['bits']} | {r['n']} | {algo} | {r['n_min']} | {r['best_ms']:.3g} | {r['gflops']:.3g} | "
+                     f"{r['tuning_s']:.2f} |")
+    return "\n".join(lines)
+
+
 def table(rows):
     lines = ["| SMs | format | n | fastest | n_min | best ms | GFLOP/s | simple / block / Strassen d=1,2,3 ms |",
              "|---|---|---|---|---|---|---|---|"]
@@ -77,9 +119,15 @@ def table(rows):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--out", default=None, help="write the rows as JSON here")
+    ap.add_argument("--precisions", action="store_true",
+                    help="instead: the multi-limb precision map (128..2048 bits) on the whole device")
     args = ap.parse_args()
-    rows = sweep()
-    print(table(rows))
+    if args.precisions:
+        rows = precision_sweep()
+        print(precision_table(rows))
+    else:
+        rows = sweep()
+        print(table(rows))
     if args.out:
         with open(args.out, "w") as f:
             json.dump(rows, f, indent=1)
