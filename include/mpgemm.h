@@ -433,7 +433,10 @@ int mpgemm_select_precision(double log2_target, int64_t m, int64_t l, int64_t n,
  *                             cost model's features and the persistent
  *                             tcgen05 kernel's grid use it.
  * A partition only restricts where this process's kernels run; it changes
- * no device setting.
+ * no device setting.  A call on a partition's stream makes the partition's
+ * context current on the calling thread for its duration, and a green
+ * context can be current on one thread at a time: calls on the same
+ * partition must not run concurrently from several host threads.
  * ------------------------------------------------------------------------- */
 int mpgemm_partition_create(int num_sms, void** stream, int* sms_out);
 int mpgemm_partition_destroy(void* stream);
