@@ -2,7 +2,7 @@
 // 2 hidden layers of 64 ReLU units, trained with Adam on timings the library
 // measures itself.  It stands in for the paper's time prediction (Section 3)
 // when picking algorithm, tile and Strassen depth (MPGEMM_AUTO, batched
-// tiles); exhaustive measured tuning stays the fallback and the judge.
+// tiles); exhaustive measured tuning stays the fallback and the yardstick of its regret.
 //
 // Kernels: k_mlp_train runs the whole training in one CTA (1024 threads,
 // activations and weights in shared memory, one minibatch of 128 per step:
