@@ -302,3 +302,48 @@ def test_paper_matrices_dd_closed_form():
         for j in (0, n // 3, n - 1):
             got = Fraction(C[0, i - 1, j]) + Fraction(C[1, i - 1, j])
             assert abs(got - truth) <= (4 * n + 3) * Fraction(2) ** -104 * truth
+
+
+# ---------------------------------------------------------------- the bench's own launch configurations
+
+def test_dd_bench_configuration_sampled():
+    """DD 2048^3 with the bench's inputs and its tuned launch (Strassen depth
+    3, n_min 32): sampled entries against the exact product, Strassen bound."""
+    n = 2048
+    A = I.dd_random(n, n, I.seed_for(1, 0), exp_spread=20)
+    B = I.dd_random(n, n, I.seed_for(1, 1), exp_spread=20)
+    C = host(mpg.gemm_dd(dev(A), dev(B), algo="strassen", n_min=32, depth=3))
+    ii, jj = sample_indices(n, n, 384, seed=2048)
+    err, _ = oracle.exact_check(A, B, C, ii, jj)
+    amax, bmax = np.max(np.abs(A[0] + A[1])), np.max(np.abs(B[0] + B[1]))
+    assert np.max(err) <= 2.0**-96 * n * amax * bmax
+
+
+def test_qd_bench_configuration_sampled():
+    n = 1024
+    A = I.qd_random(n, n, I.seed_for(1, 0), exp_spread=20)
+    B = I.qd_random(n, n, I.seed_for(1, 1), exp_spread=20)
+    C = host(mpg.gemm_qd(dev(A), dev(B), algo="strassen", n_min=16, depth=3))
+    ii, jj = sample_indices(n, n, 128, seed=1024)
+    err, _ = oracle.exact_check(A, B, C, ii, jj)
+    assert np.max(err) <= 2.0**-200 * n * np.max(np.abs(A[0])) * np.max(np.abs(B[0]))
+
+
+def test_mp256_bench_configuration_sampled():
+    """256-bit 1024^3 with the bench's inputs and tuned launch (Strassen
+    depth 3, n_min 512): sampled entries exactly (Fractions) within
+    2^-(p-8) l max|A| max|B|, the multi-limb Strassen tolerance."""
+    from fractions import Fraction
+    from exact import mp_words_to_fraction
+    n, w = 1024, 8
+    A = I.mp_random(n, n, w, I.seed_for(2, w))
+    B = I.mp_random(n, n, w, I.seed_for(2, w + 1))
+    C = host(mpg.gemm_mp(dev(A), dev(B), 256, algo="strassen", n_min=512, depth=3), mp=True)
+    fa = lambda X, i, k: mp_words_to_fraction(X[:, i, k], w)
+    # max|A| max|B| < 2^64 2^64: exponents are at most 64 and mantissas below 1
+    tol = Fraction(2) ** -(256 - 8) * n * Fraction(2) ** 128
+    rng = np.random.default_rng(5)
+    for _ in range(12):
+        i, j = int(rng.integers(0, n)), int(rng.integers(0, n))
+        ex = sum((fa(A, i, k) * fa(B, k, j) for k in range(n)), Fraction(0))
+        assert abs(mp_words_to_fraction(C[:, i, j], w) - ex) <= tol
