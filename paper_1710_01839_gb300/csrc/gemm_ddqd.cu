@@ -55,7 +55,7 @@ template <class Fmt, int BM, int RM, int KT>
 __global__ void __launch_bounds__((BM / RM) * (BM / RM)) k_block(int64_t m, int64_t l, int64_t n,
                                                                  View<const double> A, View<const double> B,
                                                                  View<double> C, unsigned G) {
-    __shared__ __align__(16) double sm[2 * KT * BM * Fmt::P];
+    __shared__ __align__(16) double sm[ddqd_tile_doubles<Fmt, BM, KT>()];
     const unsigned tiles_m = ceil_div(m, BM), tiles_n = ceil_div(n, BM);
     unsigned tm, tn;
     raster(blockIdx.x, tiles_m, tiles_n, G, tm, tn);

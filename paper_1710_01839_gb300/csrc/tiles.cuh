@@ -39,11 +39,21 @@ struct QDFmt {
     }
 };
 
+// Shared memory (doubles) of one ddqd_block_tile: two KT-deep panels, each
+// k-plane P rows of BM values plus one pad.
+template <class Fmt, int BM, int KT>
+__host__ __device__ constexpr int ddqd_tile_doubles() {
+    return 2 * KT * (BM * Fmt::P + 1);
+}
+
 // One BM x BM block of C (rows i0.., columns j0.., batch z) computed by the
 // calling CTA (NT = (BM/RM)^2 threads): each thread an RM x RM register tile
 // (rows ty + r*TPD, columns tx + c*TPD); K advances in panels of KT staged
-// through shared memory `sm` (2 * KT * BM * P doubles) as [k][row][plane],
-// the next panel's global loads issued before the current panel's arithmetic.
+// through shared memory `sm` (ddqd_tile_doubles() doubles) as [k][plane][row]
+// with an odd k-stride of BM*P + 1 doubles: a warp's B reads are BM
+// consecutive doubles (no bank conflict), its A reads broadcasts, and the
+// padding spreads a panel store's k-planes over the banks.  The next panel's
+// global loads are issued before the current panel's arithmetic.
 template <class Fmt, int BM, int RM, int KT>
 __device__ __forceinline__ void ddqd_block_tile(int64_t m, int64_t l, int64_t n, const View<const double>& A,
                                                 const View<const double>& B, const View<double>& C, int64_t z,
@@ -54,8 +64,9 @@ __device__ __forceinline__ void ddqd_block_tile(int64_t m, int64_t l, int64_t n,
     constexpr int LD = (BM * KT) / NT;   // elements per thread per panel and operand
     static_assert((BM * KT) % NT == 0, "panel must split evenly over the threads");
     static_assert(KT % Fmt::R == 0, "renormalisation period must divide the panel depth");
-    auto As = reinterpret_cast<double (*)[BM][P]>(sm);
-    auto Bs = reinterpret_cast<double (*)[BM][P]>(sm + KT * BM * P);
+    constexpr int KS = BM * P + 1;   // k-plane stride (doubles)
+    double* As = sm;                 // element (k, plane q, row r) at k KS + q BM + r
+    double* Bs = sm + KT * KS;       // element (k, plane q, column c) at k KS + q BM + c
     const int tid = threadIdx.x;
     const int ty = tid / TPD, tx = tid % TPD;
 
@@ -90,8 +101,8 @@ __device__ __forceinline__ void ddqd_block_tile(int64_t m, int64_t l, int64_t n,
             int rr = idx / BM, cc = idx % BM;
 #pragma unroll
             for (int q = 0; q < P; q++) {
-                As[c][r][q] = ra[v][q];
-                Bs[rr][cc][q] = rb[v][q];
+                As[c * KS + q * BM + r] = ra[v][q];
+                Bs[rr * KS + q * BM + cc] = rb[v][q];
             }
         }
     };
@@ -108,11 +119,11 @@ __device__ __forceinline__ void ddqd_block_tile(int64_t m, int64_t l, int64_t n,
 #pragma unroll
             for (int r = 0; r < RM; r++)
 #pragma unroll
-                for (int q = 0; q < P; q++) a[r][q] = As[kk][ty + r * TPD][q];
+                for (int q = 0; q < P; q++) a[r][q] = As[kk * KS + q * BM + ty + r * TPD];
 #pragma unroll
             for (int c = 0; c < RM; c++)
 #pragma unroll
-                for (int q = 0; q < P; q++) b[c][q] = Bs[kk][tx + c * TPD][q];
+                for (int q = 0; q < P; q++) b[c][q] = Bs[kk * KS + q * BM + tx + c * TPD];
 #pragma unroll
             for (int r = 0; r < RM; r++)
 #pragma unroll
