@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
     constexpr int SMD = ddqd_tile_doubles<DDFmt, 32, 16>() > ddqd_tile_doubles<QDFmt, 32, 8>()
                             ? ddqd_tile_doubles<DDFmt, 32, 16>()
                             : ddqd_tile_doubles<QDFmt, 32, 8>();
-    static_assert(SMD * 8 >= 2 * 8 * 16 * 10 * 4, "the 256-bit tile's staging fits too");
+    static_assert(SMD * 8 >= mp_tile_words<8, 8>() * 4, "the 256-bit tile's staging fits too");
     __shared__ __align__(16) double sm[SMD];   // the largest tile's staging
     __shared__ int s_item;
     unsigned st = 0u;

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_mp_block(int64_t m, int64_t l, int64_t 
                                                   View<const uint32_t> B, View<uint32_t> C, unsigned G,
                                                   unsigned* status) {
     constexpr int BM = 16;
-    __shared__ uint32_t sm[2 * KT * BM * (2 + W)];
+    __shared__ __align__(16) uint32_t sm[mp_tile_words<W, KT>()];
     const unsigned tiles_m = ceil_div(m, BM), tiles_n = ceil_div(n, BM);
     unsigned tm, tn;
     raster(blockIdx.x, tiles_m, tiles_n, G, tm, tn);

@@ -1,10 +1,13 @@
 // Device p-bit multi-limb binary floating point, p = 32 W, round to nearest
 // with ties to even after every operation (the fixed-precision stand-in for
-// MPFR, Section 4.2 of the paper).  One thread owns one value.  Up to 1024
-// bits every loop is unrolled over compile-time limb indices so the limbs
-// live in registers, and every data-dependent shift is a barrel shifter of
-// selects (no dynamic register indexing); 2048-bit values keep their limbs
-// in local memory, loop, and shift by direct limb indexing.
+// MPFR, Section 4.2 of the paper).  One thread owns one value.  Every loop
+// is unrolled over compile-time limb indices so the limbs live in
+// registers, and every data-dependent shift is a barrel shifter of selects
+// (no dynamic register indexing).  At 2048 bits the multiply's first
+// operand is not held in registers but read limb by limb through an
+// accessor (shared or global memory), which keeps a thread's live limbs
+// (second operand, accumulator, high part of the product) within the
+// register file.
 //
 // Value: (-1)^sign * M * 2^(e - p), M in [2^(p-1), 2^p) (limb 0 least
 // significant); zero has flag bit1 and M = 0, e = 0.  Exponents are carried
@@ -16,11 +19,9 @@
 
 namespace mpg {
 
-// Loops over limbs unroll completely while the value fits in registers (up
-// to 32 limbs, 1024 bits); wider values (2048 bits) keep their limbs in
-// local memory and loop.
-#define MP_UNROLL _Pragma("unroll (W > 32 ? 1 : 128)")
-#define MP_UNROLL_N _Pragma("unroll (N > 40 ? 1 : 128)")
+// Loops over limbs unroll completely.
+#define MP_UNROLL _Pragma("unroll")
+#define MP_UNROLL_N _Pragma("unroll")
 
 template <int W>
 struct MPV {
@@ -46,44 +47,31 @@ __device__ __forceinline__ int clamp_exp(long long e, unsigned& status) {
 }
 
 // Shift the N-limb value v right by d >= 0 bits; OR of the dropped bits goes
-// into sticky.  Register-resident values (N <= 40): limb moves by powers of
-// two (selects, no dynamic register indexing), then a funnel shift.  Wider
-// values live in local memory and move limbs by direct indexing.
+// into sticky.  Limbs move by powers of two (selects, no dynamic register
+// indexing), then a funnel shift.
 template <int N>
 __device__ __forceinline__ void shr_sticky(uint32_t (&v)[N], int d, uint32_t& sticky) {
     int q = d >> 5;
-    if constexpr (N > 40) {
-        if (q >= N) {
-            for (int i = 0; i < N; i++) {
-                sticky |= v[i];
-                v[i] = 0u;
-            }
-        } else if (q > 0) {
-            for (int i = 0; i < q; i++) sticky |= v[i];
-            for (int i = 0; i < N; i++) v[i] = i + q < N ? v[i + q] : 0u;
+#pragma unroll
+    for (int st = 1; st < N; st <<= 1) {
+        bool on = (q & st) != 0;
+        uint32_t drop = 0;
+#pragma unroll
+        for (int i = 0; i < st && i < N; i++) drop |= v[i];
+        sticky |= on ? drop : 0u;
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            uint32_t nv = (i + st < N) ? v[i + st] : 0u;
+            v[i] = on ? nv : v[i];
         }
-    } else {
+    }
+    if (q >= N) {   // everything shifted out
+        uint32_t all = 0;
 #pragma unroll
-        for (int st = 1; st < N; st <<= 1) {
-            bool on = (q & st) != 0;
-            uint32_t drop = 0;
+        for (int i = 0; i < N; i++) all |= v[i];
+        sticky |= all;
 #pragma unroll
-            for (int i = 0; i < st && i < N; i++) drop |= v[i];
-            sticky |= on ? drop : 0u;
-#pragma unroll
-            for (int i = 0; i < N; i++) {
-                uint32_t nv = (i + st < N) ? v[i + st] : 0u;
-                v[i] = on ? nv : v[i];
-            }
-        }
-        if (q >= N) {   // everything shifted out
-            uint32_t all = 0;
-#pragma unroll
-            for (int i = 0; i < N; i++) all |= v[i];
-            sticky |= all;
-#pragma unroll
-            for (int i = 0; i < N; i++) v[i] = 0u;
-        }
+        for (int i = 0; i < N; i++) v[i] = 0u;
     }
     int r = d & 31;
     sticky |= r ? (v[0] << (32 - r)) : 0u;
@@ -96,18 +84,13 @@ __device__ __forceinline__ void shr_sticky(uint32_t (&v)[N], int d, uint32_t& st
 template <int N>
 __device__ __forceinline__ void shl(uint32_t (&v)[N], int s) {
     int q = s >> 5;
-    if constexpr (N > 40) {
-        if (q > 0)
-            for (int i = N - 1; i >= 0; i--) v[i] = i - q >= 0 ? v[i - q] : 0u;
-    } else {
 #pragma unroll
-        for (int st = 1; st < N; st <<= 1) {
-            bool on = (q & st) != 0;
+    for (int st = 1; st < N; st <<= 1) {
+        bool on = (q & st) != 0;
 #pragma unroll
-            for (int i = N - 1; i >= 0; i--) {
-                uint32_t nv = (i - st >= 0) ? v[i - st] : 0u;
-                v[i] = on ? nv : v[i];
-            }
+        for (int i = N - 1; i >= 0; i--) {
+            uint32_t nv = (i - st >= 0) ? v[i - st] : 0u;
+            v[i] = on ? nv : v[i];
         }
     }
     int r = s & 31;
@@ -129,40 +112,168 @@ MP_UNROLL
     return c != 0u;
 }
 
-// r = RN_p(x * y).
-template <int W>
-__device__ __forceinline__ void mp_mul(const MPV<W>& x, const MPV<W>& y, MPV<W>& r, unsigned& status) {
-    unsigned sign = (x.f ^ y.f) & 1u;
-    if ((x.f | y.f) & 2u) {
-        mp_set_zero(r, sign);
-        return;
-    }
+// Exact product x y of two W-limb mantissas (limb 0 least significant),
+// rounded to nearest even to W limbs: M, the normalising shift sh (0 or 1)
+// and whether M must be incremented (before the carry out of round_up).
+template <int W, bool INLINE_LOOPS>
+__device__ __forceinline__ void mp_mul_exact_body(const uint32_t* xm, const uint32_t* ym, uint32_t* M, int& sh,
+                                                  bool& inc) {
     uint32_t P[2 * W];
-MP_UNROLL
+#pragma unroll(INLINE_LOOPS ? 128 : 1)
     for (int i = 0; i < 2 * W; i++) P[i] = 0u;
-MP_UNROLL
+#pragma unroll(INLINE_LOOPS ? 128 : 1)
     for (int i = 0; i < W; i++) {
         uint32_t carry = 0u;
-MP_UNROLL
+#pragma unroll(INLINE_LOOPS ? 128 : 1)
         for (int j = 0; j < W; j++) {
-            uint64_t t = (uint64_t)x.m[i] * y.m[j] + P[i + j] + carry;
+            uint64_t t = (uint64_t)xm[i] * ym[j] + P[i + j] + carry;
             P[i + j] = (uint32_t)t;
             carry = (uint32_t)(t >> 32);
         }
         P[i + W] = carry;
     }
     // P in [2^(2p-2), 2^(2p)): keep the top p bits after a shift of 0 or 1.
-    int sh = (P[2 * W - 1] >> 31) ? 0 : 1;
-    uint32_t M[W];
-MP_UNROLL
+    sh = (P[2 * W - 1] >> 31) ? 0 : 1;
+#pragma unroll(INLINE_LOOPS ? 128 : 1)
     for (int i = 0; i < W; i++) M[i] = __funnelshift_l(P[W + i - 1], P[W + i], sh);
     uint32_t below = P[W - 1] << sh;          // bits under M, top bit = round bit
     uint32_t rb = below >> 31;
     uint32_t st = below << 1;
-MP_UNROLL
+#pragma unroll(INLINE_LOOPS ? 128 : 1)
     for (int i = 0; i < W - 1; i++) st |= P[i];
-    bool inc = rb && (st != 0u || (M[0] & 1u));
-    long long e = (long long)x.e + y.e - sh;
+    inc = rb && (st != 0u || (M[0] & 1u));
+}
+
+// The same, out of line and on local memory, for the rare products whose
+// high part leaves the rounding open (keeps the common path's registers).
+template <int W>
+__device__ __noinline__ void mp_mul_exact_slow(const uint32_t* xm, const uint32_t* ym, uint32_t* M, int* sh,
+                                               int* inc) {
+    int s;
+    bool i;
+    mp_mul_exact_body<W, false>(xm, ym, M, s, i);
+    *sh = s;
+    *inc = i ? 1 : 0;
+}
+
+// Limb accessors for the multiply's operands: limb(i), and quad(q) = limbs
+// 4q .. 4q+3.
+template <int W>
+struct RegLimbs {   // limbs in registers
+    static constexpr bool kQuads = false;
+    const uint32_t (&m)[W];
+    __device__ __forceinline__ uint32_t limb(int i) const { return m[i]; }
+    __device__ __forceinline__ uint4 quad(int q) const {
+        return make_uint4(m[4 * q], m[4 * q + 1], m[4 * q + 2], m[4 * q + 3]);
+    }
+};
+
+struct SmemLimbs {  // limbs contiguous in shared memory, 16-byte aligned
+    static constexpr bool kQuads = true;   // the multiply reads y four limbs per load
+    const uint32_t* p;
+    // volatile: every use loads again, so the operand never occupies registers
+    __device__ __forceinline__ uint32_t limb(int i) const {
+        uint32_t v;
+        asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p + i)));
+        return v;
+    }
+    __device__ __forceinline__ uint4 quad(int q) const {
+        uint4 v;
+        asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "r"((unsigned)__cvta_generic_to_shared(p + 4 * q)));
+        return v;
+    }
+};
+
+// r = RN_p(x * y).  From W = 8 limbs up the high part of the product comes
+// first: only the limb products of columns >= W - 2 (about half of the W^2),
+// summed exactly.  The dropped products add less than W units of limb W - 1
+// and limb W - 2 less than one more, so when limb W - 1's bits below M sit
+// more than W + 1 units away from the half-ulp and from the next ulp, the
+// rounding direction and M are those of the exact product (the test MPFR
+// applies to its short products, Brent and Zimmermann, Modern Computer
+// Arithmetic, Section 3.3.2); otherwise the full product is formed.
+// The operands are given by exponent, flags and a limb accessor.
+template <int W, class XA, class YA>
+__device__ __forceinline__ void mp_mul_acc(int xe, unsigned xf, const XA& xa, int ye, unsigned yf, const YA& ya,
+                                           MPV<W>& r, unsigned& status) {
+    unsigned sign = (xf ^ yf) & 1u;
+    if ((xf | yf) & 2u) {
+        mp_set_zero(r, sign);
+        return;
+    }
+    uint32_t M[W];
+    int sh;
+    bool inc;
+    if constexpr (W >= 8) {
+        static_assert(W % 4 == 0, "limb quads");
+        uint32_t H[W + 2];   // limbs W-2 .. 2W-1 of the high part
+MP_UNROLL
+        for (int i = 0; i < W + 2; i++) H[i] = 0u;
+MP_UNROLL
+        for (int i = 0; i < W; i++) {
+            const uint32_t xi = xa.limb(i);
+            uint32_t carry = 0u;
+MP_UNROLL
+            for (int q = 0; q < W / 4; q++) {
+                if (i + 4 * q + 3 >= W - 2) {   // constant after unrolling
+                    uint32_t yv[4];
+                    if constexpr (YA::kQuads) {
+                        const uint4 y4 = ya.quad(q);
+                        yv[0] = y4.x;
+                        yv[1] = y4.y;
+                        yv[2] = y4.z;
+                        yv[3] = y4.w;
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; u++) yv[u] = ya.limb(4 * q + u);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int j = 4 * q + u;
+                        if (i + j >= W - 2) {
+                            uint64_t t = (uint64_t)xi * yv[u] + H[i + j - (W - 2)] + carry;
+                            H[i + j - (W - 2)] = (uint32_t)t;
+                            carry = (uint32_t)(t >> 32);
+                        }
+                    }
+                }
+            }
+            H[i + 2] = carry;
+        }
+        sh = (H[W + 1] >> 31) ? 0 : 1;
+        const uint32_t ulp1 = sh ? 0x7FFFFFFFu : 0xFFFFFFFFu;   // one ulp of M, minus 1, in limb W-1
+        const uint32_t half = sh ? 0x40000000u : 0x80000000u;
+        const uint32_t u = H[1] & ulp1;                          // bits of limb W-1 below M
+        if (u <= half - (W + 1) || (u > half && u <= ulp1 - W)) {
+            inc = u > half;
+MP_UNROLL
+            for (int i = 0; i < W; i++) M[i] = __funnelshift_l(H[i + 1], H[i + 2], sh);
+        } else {
+            uint32_t xs[W], ys[W], Ms[W];
+            int s2, i2;
+MP_UNROLL
+            for (int i = 0; i < W; i++) {
+                xs[i] = xa.limb(i);
+                ys[i] = ya.limb(i);
+            }
+            mp_mul_exact_slow<W>(xs, ys, Ms, &s2, &i2);
+MP_UNROLL
+            for (int i = 0; i < W; i++) M[i] = Ms[i];
+            sh = s2;
+            inc = i2 != 0;
+        }
+    } else {
+        uint32_t xm[W], ym[W];
+MP_UNROLL
+        for (int i = 0; i < W; i++) {
+            xm[i] = xa.limb(i);
+            ym[i] = ya.limb(i);
+        }
+        mp_mul_exact_body<W, true>(xm, ym, M, sh, inc);
+    }
+    long long e = (long long)xe + ye - sh;
     if (round_up(M, inc)) {
         M[W - 1] = 0x80000000u;
         e += 1;
@@ -171,6 +282,11 @@ MP_UNROLL
     r.f = sign;
 MP_UNROLL
     for (int i = 0; i < W; i++) r.m[i] = M[i];
+}
+
+template <int W>
+__device__ __forceinline__ void mp_mul(const MPV<W>& x, const MPV<W>& y, MPV<W>& r, unsigned& status) {
+    mp_mul_acc<W>(x.e, x.f, RegLimbs<W>{x.m}, y.e, y.f, RegLimbs<W>{y.m}, r, status);
 }
 
 // r = RN_p(a + b).

@@ -181,17 +181,34 @@ __device__ __forceinline__ void mp_mac(MPV<W>& c, const MPV<W>& a, const MPV<W>&
     c = s;
 }
 
+// Operands of this width and up are not held in registers: the block
+// kernel's multiply reads both from shared memory.
+constexpr int MP_STREAM_LIMBS = 64;
+
+// Shared memory (words) of one mp_block_tile: two KT-deep panels of 16
+// elements, each [exponent, flags, (pad, pad,) W limbs]; streamed operands
+// put their limbs at a 16-byte boundary.
+template <int W>
+__host__ __device__ constexpr int mp_tile_limb_offset() {
+    return W >= MP_STREAM_LIMBS ? 4 : 2;
+}
+template <int W, int KT>
+__host__ __device__ constexpr int mp_tile_words() {
+    return 2 * KT * 16 * (mp_tile_limb_offset<W>() + W);
+}
+
 // One 16 x 16 block of C (one output per thread, 256 threads) with A rows and
 // B columns staged KT elements deep through shared memory `sm`
-// (2 * KT * 16 * (2 + W) words) as [k][row][word]; device-side flags are
-// ORed into `st`.
+// (mp_tile_words<W, KT>() words, 16-byte aligned) as [k][row][word];
+// device-side flags are ORed into `st`.
 template <int W, int KT>
 __device__ __forceinline__ void mp_block_tile(int64_t m, int64_t l, int64_t n, const View<const uint32_t>& A,
                                               const View<const uint32_t>& B, const View<uint32_t>& C, int64_t z,
                                               int64_t i0, int64_t j0, uint32_t* sm, unsigned& st) {
     constexpr int BM = 16;
-    constexpr int E = 2 + W;
-    constexpr int WORDS = BM * KT * E;
+    constexpr int OFF = mp_tile_limb_offset<W>();
+    constexpr int E = OFF + W;            // words per staged element
+    constexpr int WORDS = BM * KT * (2 + W);
     auto As = reinterpret_cast<uint32_t (*)[BM][E]>(sm);
     auto Bs = reinterpret_cast<uint32_t (*)[BM][E]>(sm + KT * BM * E);
     const int tid = threadIdx.x, ty = tid / BM, tx = tid % BM;
@@ -200,29 +217,40 @@ __device__ __forceinline__ void mp_block_tile(int64_t m, int64_t l, int64_t n, c
     for (int64_t k0 = 0; k0 < l; k0 += KT) {
         for (int idx = tid; idx < WORDS; idx += 256) {
             int q = idx / (BM * KT), rem = idx % (BM * KT);
+            int slot = q < 2 ? q : q - 2 + OFF;
             int r = rem / KT, cc = rem % KT;          // A: row r, k = k0 + cc
             int64_t i = i0 + r, k = k0 + cc;
             uint32_t va = (i < m && k < l) ? __ldg(A.at(z, q, i, k)) : (q == 1 ? 2u : 0u);
-            As[cc][r][q] = va;
+            As[cc][r][slot] = va;
             int rb = rem / BM, cb = rem % BM;         // B: k = k0 + rb, column cb
             int64_t kb = k0 + rb, j = j0 + cb;
             uint32_t vb = (kb < l && j < n) ? __ldg(B.at(z, q, kb, j)) : (q == 1 ? 2u : 0u);
-            Bs[rb][cb][q] = vb;
+            Bs[rb][cb][slot] = vb;
         }
         __syncthreads();
         const int kmax = (l - k0) < KT ? (int)(l - k0) : KT;
         for (int kk = 0; kk < kmax; kk++) {
-            MPV<W> a, b;
-            a.e = (int)As[kk][ty][0];
-            a.f = As[kk][ty][1];
-            b.e = (int)Bs[kk][tx][0];
-            b.f = Bs[kk][tx][1];
+            const uint32_t* ar = &As[kk][ty][0];
+            const uint32_t* br = &Bs[kk][tx][0];
+            MPV<W> t;
+            if constexpr (W >= MP_STREAM_LIMBS) {
+                mp_mul_acc<W>((int)ar[0], ar[1], SmemLimbs{ar + OFF}, (int)br[0], br[1], SmemLimbs{br + OFF}, t, st);
+            } else {
+                MPV<W> a, b;
+                a.e = (int)ar[0];
+                a.f = ar[1];
+                b.e = (int)br[0];
+                b.f = br[1];
 MP_UNROLL
-            for (int w = 0; w < W; w++) {
-                a.m[w] = As[kk][ty][2 + w];
-                b.m[w] = Bs[kk][tx][2 + w];
+                for (int w = 0; w < W; w++) {
+                    a.m[w] = ar[OFF + w];
+                    b.m[w] = br[OFF + w];
+                }
+                mp_mul<W>(a, b, t, st);
             }
-            mp_mac(c, a, b, st);
+            MPV<W> s;
+            mp_add<W>(c, t, s, st);
+            c = s;
         }
         __syncthreads();
     }

@@ -133,6 +133,22 @@ def mp_random(rows: int, cols: int, w: int, seed: int, emin: int = -64, emax: in
     return out
 
 
+def mp_structured(rows: int, cols: int, w: int, seed: int, emin: int = -8, emax: int = 8) -> np.ndarray:
+    """MP planes like mp_random, but every limb drawn from {0, 1, 2^31 - 1,
+    2^31, 2^32 - 1, uniform}: products with long runs of zeros or ones,
+    near-ties and exact ties below the rounding position."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((2 + w, rows, cols), dtype=np.uint32)
+    out[0] = rng.integers(emin, emax + 1, size=(rows, cols)).astype(np.int32).view(np.uint32)
+    out[1] = rng.integers(0, 2, size=(rows, cols), dtype=np.uint32)
+    special = np.array([0, 1, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFF], dtype=np.uint64)
+    pick = rng.integers(0, 6, size=(w, rows, cols))
+    uni = rng.integers(0, 2**32, size=(w, rows, cols), dtype=np.uint64)
+    out[2:] = np.where(pick < 5, special[np.minimum(pick, 4)], uni).astype(np.uint32)
+    out[2 + w - 1] |= np.uint32(0x80000000)
+    return out
+
+
 def dd_rowcol_scaled(m: int, l: int, n: int, seed: int, spread: int = 16, inner_spread: int = 0):
     """Split-precision workload: DD A (m x l) with row i scaled by 2^{r_i},
     DD B (l x n) with column j scaled by 2^{c_j}; optional inner-dimension

@@ -118,6 +118,35 @@ def test_mp_large_config_sampled_rows(w, n):
         assert np.array_equal(C[:, r0], Co[:, r0]), r0
 
 
+def _set_mantissas(P, w, mask, values, rng):
+    """Write mantissas (Python ints in [2^(p-1), 2^p)) drawn from `values`
+    into the entries of the MP planes P where mask is set."""
+    for r, c in zip(*np.nonzero(mask)):
+        v = values[int(rng.integers(0, len(values)))]
+        for q in range(w):
+            P[2 + q, r, c] = (v >> (32 * q)) & 0xFFFFFFFF
+
+
+@pytest.mark.parametrize("w", [4, 8, 16, 32, 64])
+@pytest.mark.parametrize("algo", ["simple", "block"])
+def test_mp_short_product_branches_bit_exact(w, algo):
+    # the multiply's high-part product decides most roundings and leaves
+    # ties and near-ties to the full product: structured limbs and
+    # mantissas whose products are exact ties, near-ties and near the next
+    # ulp reach both branches; bit-identical to the oracle
+    p = 32 * w
+    m, l, n = 19, 21, 17
+    rng = np.random.default_rng(4100 + w)
+    A, B = I.mp_structured(m, l, w, 4200 + w), I.mp_structured(l, n, w, 4300 + w)
+    tie_makers = [(1 << (p - 1)) + 1, 3 << (p - 2), (1 << (p - 1)) + 3, (1 << p) - 1, 1 << (p - 1),
+                  (1 << (p - 1)) + (1 << (p // 2))]
+    _set_mantissas(A, w, rng.random((m, l)) < 0.5, tie_makers, rng)
+    _set_mantissas(B, w, rng.random((l, n)) < 0.5, tie_makers, rng)
+    C = host(mpg.gemm_mp(dev(A), dev(B), p, algo=algo, n_min=16), mp=True)
+    assert np.array_equal(C, oracle.mp_gemm(A, B, prec_bits=p))
+    assert mpg.stream_status() == 0
+
+
 def test_mp_cancellation_and_zeros():
     # rows of A that are negatives of each other, zero entries, equal exponents
     w = 4
