@@ -34,10 +34,18 @@ __global__ void __launch_bounds__(256) k_mp_simple(int64_t m, int64_t l, int64_t
     if (st) atomicOr(status, st);
 }
 
+// Resident CTAs per SM the block kernel's register budget is sized for
+// (0: the compiler's choice).  With their operands streamed from shared
+// memory, 512- and 1024-bit tiles fit 3 and 2 CTAs per SM.
+template <int W>
+constexpr int mp_block_min_ctas() {
+    return W == 16 ? 3 : W == 32 ? 2 : W == 64 ? 1 : 0;
+}
+
 // CTA = 16 x 16 outputs (mp_block_tile); CTA order follows the super-tile
 // raster with group G.
 template <int W, int KT>
-__global__ void __launch_bounds__(256) k_mp_block(int64_t m, int64_t l, int64_t n, View<const uint32_t> A,
+__global__ void __launch_bounds__(256, mp_block_min_ctas<W>()) k_mp_block(int64_t m, int64_t l, int64_t n, View<const uint32_t> A,
                                                   View<const uint32_t> B, View<uint32_t> C, unsigned G,
                                                   unsigned* status) {
     constexpr int BM = 16;

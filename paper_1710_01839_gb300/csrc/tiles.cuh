@@ -182,8 +182,9 @@ __device__ __forceinline__ void mp_mac(MPV<W>& c, const MPV<W>& a, const MPV<W>&
 }
 
 // Operands of this width and up are not held in registers: the block
-// kernel's multiply reads both from shared memory.
-constexpr int MP_STREAM_LIMBS = 64;
+// kernel's multiply reads both from shared memory (fewer live registers, so
+// more resident CTAs per SM).
+constexpr int MP_STREAM_LIMBS = 16;
 
 // Shared memory (words) of one mp_block_tile: two KT-deep panels of 16
 // elements, each [exponent, flags, (pad, pad,) W limbs]; streamed operands
