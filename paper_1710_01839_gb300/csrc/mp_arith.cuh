@@ -100,16 +100,22 @@ __device__ __forceinline__ void shl(uint32_t (&v)[N], int s) {
 }
 
 // Round-to-nearest-even increment of a W-limb mantissa; returns the carry out.
+// The carry leaves limb 0 only when limb 0 was all ones (rare), so the walk
+// over the upper limbs sits behind a branch.
 template <int W>
 __device__ __forceinline__ bool round_up(uint32_t (&M)[W], bool inc) {
-    uint32_t c = inc ? 1u : 0u;
+    M[0] += inc ? 1u : 0u;
+    if (inc && M[0] == 0u) {
+        uint32_t c = 1u;
 MP_UNROLL
-    for (int i = 0; i < W; i++) {
-        uint32_t s = M[i] + c;
-        c = (c && s == 0u) ? 1u : 0u;
-        M[i] = s;
+        for (int i = 1; i < W; i++) {
+            uint32_t s = M[i] + c;
+            c = (c && s == 0u) ? 1u : 0u;
+            M[i] = s;
+        }
+        return c != 0u;
     }
-    return c != 0u;
+    return false;
 }
 
 // Exact product x y of two W-limb mantissas (limb 0 least significant),

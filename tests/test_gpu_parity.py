@@ -147,6 +147,53 @@ def test_mp_short_product_branches_bit_exact(w, algo):
     assert mpg.stream_status() == 0
 
 
+def _mp_planes(entries, w):
+    """MP planes (2 + w, rows, cols) from a nested list of (sign, e, M)."""
+    rows, cols = len(entries), len(entries[0])
+    P = np.zeros((2 + w, rows, cols), dtype=np.uint32)
+    for r in range(rows):
+        for c in range(cols):
+            sgn, e, M = entries[r][c]
+            P[0, r, c] = np.int32(e).view(np.uint32)
+            P[1, r, c] = sgn
+            for q in range(w):
+                P[2 + q, r, c] = (M >> (32 * q)) & 0xFFFFFFFF
+    return P
+
+
+@pytest.mark.parametrize("w", [1, 2, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("algo", ["simple", "block"])
+def test_mp_round_carry_out_bit_exact(w, algo):
+    # roundings that carry out of the top limb (M all ones rounds up to
+    # 2^p): in the multiply (a product just below 2^(2p-1) within half an
+    # ulp) and in the add (1 - 2^-p plus just over half an ulp, plus an
+    # exact tie with odd M); bit-identical to the oracle
+    p = 32 * w
+    x = (1 << (p - 1)) + 12345
+    while True:    # y with x y in [2^(2p-1) - 2^(p-2), 2^(2p-1))
+        y = ((1 << (2 * p - 1)) - 1) // x
+        if 0 < (1 << (2 * p - 1)) - x * y <= (1 << (p - 2)) and y >= (1 << (p - 1)):
+            break
+        x += 1
+    one = (0, 1, 1 << (p - 1))
+    ones = (0, 0, (1 << p) - 1)                       # 1 - 2^-p
+    over_half = (0, -p, (1 << (p - 1)) + 1)           # 2^(-p-1) + 2^(-2p)
+    tie = (0, -p, 1 << (p - 1))                       # 2^(-p-1)
+    zero = (0, 0, 0)
+    A = _mp_planes([[(0, 0, x), zero], [ones, over_half], [ones, tie]], w)
+    A[1, 0, 1] = 2                                    # the zero flag
+    B = _mp_planes([[(0, 0, y), one], [one, one]], w)
+    C = host(mpg.gemm_mp(dev(A), dev(B), p, algo=algo, n_min=16), mp=True)
+    assert np.array_equal(C, oracle.mp_gemm(A, B, prec_bits=p))
+    # x y rounds up to 1/2; 1 - 2^-p plus over half an ulp, and plus an
+    # exact tie (odd M), round up to 1
+    top = C[2 + w - 1].astype(np.int64)
+    low = C[2:2 + w - 1].astype(np.int64)
+    for (r, c), e in (((0, 0), 0), ((1, 1), 1), ((2, 1), 1)):
+        assert C[0, r, c].view(np.int32) == e and top[r, c] == 0x80000000 and not low[:, r, c].any()
+    assert mpg.stream_status() == 0
+
+
 def test_mp_cancellation_and_zeros():
     # rows of A that are negatives of each other, zero entries, equal exponents
     w = 4
