@@ -263,6 +263,70 @@ def qd_split_extra(args, stream):
     return out
 
 
+def via_mp_extra(args, stream, fp64_dd_gflops):
+    """DD (at --n, 128-bit limbs) and QD (at --qd-split-n, 256-bit limbs)
+    GEMMs on the integer pipe (mpgemm_dd_via_mp / mpgemm_qd_via_mp) on the
+    same inputs as the FP64-pipe kernels: the multi-limb algorithm and n_min
+    come from the Section 3 tuner run on the converted operands, and each
+    timed call includes both conversions.  Accuracy (far inside the DD / QD
+    bounds; bit-identical to the oracle) is asserted by the parity tests."""
+    import ctypes
+    import torch
+    import paper_1710_01839_gb300 as mpg
+    from paper_1710_01839_gb300 import tuner
+    L = mpg.lib()
+    out = {}
+    for fmt, n, bits, ref in (("dd", args.n, 128, fp64_dd_gflops), ("qd", args.qd_split_n, 256, None)):
+        A, B = inputs_for(fmt, n)
+        Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        Cd = torch.empty_like(Ad)
+        Am, Bm = mpg.to_mp(Ad, bits), mpg.to_mp(Bd, bits)
+        Cm = torch.empty_like(Am)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        choice, _ = tuner.tune("mp", Am, Bm, Cm, flags=tuner.QUICK, prec_bits=bits, stream=stream)
+        t_tune = time.perf_counter() - t0
+        del Am, Bm, Cm
+        algo, n_min, depth = choice["algo"], choice["n_min"], choice["depth"]
+        call = lambda: mpg.gemm_via_mp(Ad, Bd, bits, Cd, algo=algo, n_min=n_min, depth=depth, stream=stream)
+        call()
+        torch.cuda.synchronize()
+        reps = 3
+        L.mpgemm_profile(1)
+        L.mpgemm_profile_read(None, None)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, kl = ctypes.c_double(), ctypes.c_int()
+        L.mpgemm_profile_read(ctypes.byref(kms), ctypes.byref(kl))
+        L.mpgemm_profile(0)
+        ms = e0.elapsed_time(e1) / reps
+        status = mpg.stream_status()
+        if status != 0:
+            raise RuntimeError(f"device status {status}: {mpg.strerror(status)}")
+        flops = 2.0 * n ** 3
+        leaf = (n + (1 << depth) - 1) >> depth if algo == "strassen" else n
+        macs = (7 ** depth if algo == "strassen" else 1) * float(leaf) ** 3
+        k_ms = kms.value / max(kl.value, 1)
+        ipm = MP_INSTR_PER_MAC[bits]
+        achieved = macs * ipm / 32.0 / (k_ms * 1e-3) / 1e9
+        out[fmt] = {"workload": f"{fmt.upper()} m=l=n={n} (inputs of the FP64-pipe {fmt.upper()} GEMM), "
+                                f"{bits}-bit limbs", "prec_bits": bits,
+                    "choice": {"algo": algo, "n_min": n_min, "depth": depth}, "tuning_s": round(t_tune, 3),
+                    "gflops": flops / (ms * 1e-3) / 1e9, "ms": ms,
+                    "roofline": {"bound": "alu", "unit": "G warp-instructions/s (issue)", "achieved": achieved,
+                                 "peak": ISSUE_PEAK_GWIPS, "frac": achieved / ISSUE_PEAK_GWIPS,
+                                 "kernel": f"{bits}-bit {'leaf ' if algo == 'strassen' else ''}GEMM, {macs:.3g} MACs "
+                                           f"x {ipm} thread-instructions", "kernel_ms": k_ms,
+                                 "kernel_share": k_ms / ms}}
+        if ref is not None:
+            out[fmt]["speedup_vs_fp64_pipe"] = out[fmt]["gflops"] / ref
+    return out
+
+
 def batched_extra(args, stream):
     """512 GEMMs, m, l, n log-uniform in [16, 1024], format uniform over
     {DD, QD, 256-bit}: one persistent graph-replayed launch with tiles from
@@ -626,10 +690,14 @@ def main():
                "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(Ch.numel() * Ch.element_size()),
                "ms_per_step": e_ms / args.steps}
 
-    extras = bextra = qextra = None
+    extras = bextra = qextra = vextra = None
     if not args.no_extras and fmt == "dd":
         extras = split_precision_extra(args, stream)
         qextra = qd_split_extra(args, stream)
+        vextra = via_mp_extra(args, stream, value / world)
+        if qextra is not None and "qd" in vextra:
+            vextra["qd"]["speedup_vs_fp64_pipe"] = vextra["qd"]["gflops"] / max(qextra["plain_qd_block_gflops"],
+                                                                                qextra["plain_qd_strassen3_gflops"])
         bextra = batched_extra(args, stream)
 
     if dist:
@@ -658,6 +726,8 @@ def main():
         line["split_precision"] = extras
     if qextra is not None:
         line["qd_split_precision"] = qextra
+    if vextra is not None:
+        line["integer_pipe"] = vextra
     if bextra is not None:
         line["batched"] = bextra
     print(json.dumps(line), flush=True)

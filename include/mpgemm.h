@@ -53,7 +53,8 @@ typedef enum {
     MPGEMM_EUNSUPPORTED = -2, /* valid but not supported (precision not built, size       */
                               /* beyond a kernel's limits)                                 */
     MPGEMM_ECUDA = -3,        /* a CUDA call failed; mpgemm_last_cuda_error() has it       */
-    MPGEMM_EOVERFLOW = -4,    /* device: a multi-limb exponent left the int32 range        */
+    MPGEMM_EOVERFLOW = -4,    /* device: a multi-limb exponent left the int32 range (or a  */
+                              /* conversion to double left the normal double range)        */
     MPGEMM_ETIMEOUT = -5,     /* device: a bounded wait gave up                            */
     MPGEMM_ENOMEM = -6        /* workspace allocation failed or is too small               */
 } mpgemm_status;
@@ -195,6 +196,44 @@ int mpgemm_ozaki_split_terms(int terms, int by_col, int64_t rows, int64_t cols, 
  * ------------------------------------------------------------------------- */
 int mpgemm_dd_strassen_noalloc(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C,
                                int n_min, int strassen_depth, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * DD and QD GEMMs on the integer pipe (an extension: the paper computes its
+ * DD / QD products with the QD library's floating-point algorithms).  The
+ * operands are rounded to p-bit multi-limb numbers, C := AB runs as the
+ * multi-limb GEMM (Eqs 1-3, every multiply and add rounded to p bits, as
+ * mpgemm_mp), and C is rounded back to 2 (DD) or 4 (QD) doubles.  On GB300
+ * the FP64 pipe executes 2 operations per clock per SM, so 128-bit limbs
+ * give DD about 1.5x and 256-bit limbs QD about 7x the rate of mpgemm_dd /
+ * mpgemm_qd, with a much smaller error (2^-128 / 2^-256 per operation
+ * instead of the DD / QD bounds 4 l 2^-104 |A||B| and 4 l 2^-208 |A||B|).
+ *   Conversion to p bits (mpgemm_terms_to_mp): c = +0, then for t = 0..T-1
+ *     c = RN_p(c + x_t) with the double x_t taken exactly.
+ *   Conversion back (mpgemm_mp_to_terms): r = c, then for t = 0..T-1
+ *     x_t = RN_53(r) (round to nearest even double) and r = r - x_t (exact):
+ *     the greedy expansion of c.
+ *   Layouts: A, B, C as for mpgemm_dd (T = 2 planes) or mpgemm_qd (T = 4);
+ *   multi-limb planes as for mpgemm_mp.  prec_bits = 32 w, w in {2, 4, 8,
+ *   16} (MPGEMM_EUNSUPPORTED otherwise).  algo, n_min, strassen_depth as for
+ *   mpgemm_mp at prec_bits (MPGEMM_AUTO uses the multi-limb tuning at
+ *   prec_bits).
+ *   Workspace: mpgemm_via_mp_workspace_size bytes (the multi-limb copies of
+ *   A, B and C plus Strassen's workspace), from mpgemm_set_workspace's
+ *   buffer else allocated stream-ordered.
+ *   Device status (mpgemm_stream_status): an infinite or NaN input gives
+ *   MPGEMM_EINVAL; a result term outside the normal double range is written
+ *   as zero and gives MPGEMM_EOVERFLOW.
+ * ------------------------------------------------------------------------- */
+int mpgemm_dd_via_mp(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int prec_bits,
+                     int algo, int n_min, int strassen_depth, void* stream);
+int mpgemm_qd_via_mp(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int prec_bits,
+                     int algo, int n_min, int strassen_depth, void* stream);
+size_t mpgemm_via_mp_workspace_size(int prec_bits, int64_t m, int64_t l, int64_t n, int algo, int strassen_depth);
+/* The two conversions alone, over `count` elements: X is terms planes of
+   count doubles each (terms = 2 or 4), Y is 2 + prec_bits/32 planes of count
+   words.  Device pointers; asynchronous on stream. */
+int mpgemm_terms_to_mp(int terms, int64_t count, const double* X, int prec_bits, uint32_t* Y, void* stream);
+int mpgemm_mp_to_terms(int terms, int64_t count, int prec_bits, const uint32_t* Y, double* X, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched GEMMs of uneven sizes and mixed precisions in one persistent launch

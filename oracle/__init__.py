@@ -68,6 +68,8 @@ def _declare(L):
     L.or_round_terms.argtypes = [_P, _I, _P, _I]
     L.or_mp_mul.argtypes = [_I, _P, _P, _P]
     L.or_mp_add.argtypes = [_I, _P, _P, _P]
+    L.or_terms_to_mp.argtypes = [_I, _I64, _P, _I, _P]
+    L.or_mp_to_terms.argtypes = [_I, _I64, _I, _P, _P]
     for name in ("or_dd_gemm", "or_qd_gemm"):
         f = getattr(L, name)
         f.argtypes = [_I, _I64, _I64, _I64, _P, _P, _P, _I64, _I, _I64, _I64]
@@ -206,6 +208,37 @@ def qd_gemm(A, B, algo="simple", n_min=64, depth=0, rows=None):
 def mp_gemm(A, B, prec_bits, algo="simple", n_min=64, depth=0, rows=None):
     w = prec_bits // 32
     return _gemm(lib().or_mp_gemm, A, B, np.uint32, 2 + w, algo, n_min, depth, rows, extra=(int(prec_bits),))
+
+
+def terms_to_mp(X, prec_bits):
+    """DD / QD planes (T, rows, cols) -> multi-limb planes (2 + w, rows,
+    cols): c = +0, c = RN_p(c + x_t) for t = 0..T-1."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    T, r, c = X.shape
+    w = prec_bits // 32
+    Y = np.zeros((2 + w, r, c), dtype=np.uint32)
+    lib().or_terms_to_mp(T, r * c, _ptr(X), w, _ptr(Y))
+    return Y
+
+
+def mp_to_terms(Y, prec_bits, terms):
+    """Multi-limb planes -> the greedy expansion in `terms` doubles:
+    x_t = RN_53(r), r = r - x_t."""
+    w = prec_bits // 32
+    Y = np.ascontiguousarray(Y, dtype=np.uint32)
+    assert Y.shape[0] == 2 + w
+    X = np.zeros((terms, Y.shape[1], Y.shape[2]))
+    lib().or_mp_to_terms(terms, Y.shape[1] * Y.shape[2], w, _ptr(Y), _ptr(X))
+    return X
+
+
+def gemm_via_mp(A, B, prec_bits, algo="simple", n_min=64, depth=0):
+    """DD / QD C := AB computed in prec_bits-bit multi-limb arithmetic: the
+    conversions above around the multi-limb GEMM."""
+    T = A.shape[0]
+    Cm = mp_gemm(terms_to_mp(A, prec_bits), terms_to_mp(B, prec_bits), prec_bits, algo=algo, n_min=n_min,
+                 depth=depth)
+    return mp_to_terms(Cm, prec_bits, T)
 
 
 def exact_check(A, B, C, ii, jj):

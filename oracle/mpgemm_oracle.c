@@ -536,6 +536,79 @@ OR_API void or_mp_add(int w, const uint32_t *x, const uint32_t *y, uint32_t *z) 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Conversions between T-term double expansions (DD: T = 2, QD: T = 4) and  */
+/* p-bit multi-limb numbers, for the DD / QD GEMM computed in multi-limb     */
+/* arithmetic (an extension of Section 2's GEMM, not in the paper):          */
+/*   to p bits:   c = +0, then c = RN_p(c + x_t) for t = 0..T-1, each double */
+/*                x_t taken exactly (p >= 64 bits hold its 53);              */
+/*   from p bits: for t = 0..T-1: x_t = RN_53(r) (nearest double, ties to    */
+/*                even), r = r - x_t (exact): the greedy expansion of c.     */
+/* ------------------------------------------------------------------------ */
+
+/* The double x exactly as a w-limb value, w >= 2. */
+static mp_t mp_of_double(double x, int w) {
+    mp_t r;
+    int ex;
+    if (!isfinite(x)) die("conversion of a non-finite double");
+    if (x == 0.0) return mp_zero(signbit(x) ? 1 : 0);
+    double f = frexp(fabs(x), &ex);                 /* |x| = f 2^ex, f in [1/2, 1) */
+    uint64_t top = (uint64_t)ldexp(f, 64);          /* f 2^64: an integer below 2^64 */
+    memset(&r, 0, sizeof r);
+    r.m[w - 1] = (uint32_t)(top >> 32);             /* M = top 2^(p - 64) */
+    r.m[w - 2] = (uint32_t)top;
+    r.e = ex;                                       /* |x| = M 2^(ex - p) */
+    r.s = signbit(x) ? 1 : 0;
+    r.z = 0;
+    return r;
+}
+
+/* RN_53 of a w-limb value as a double (the result must be a normal double). */
+static double mp_round_double(const mp_t *v, int w) {
+    if (v->z) return v->s ? -0.0 : 0.0;
+    int p = 32 * w;
+    uint64_t top = ((uint64_t)v->m[w - 1] << 32) | v->m[w - 2];    /* M >> (p - 64) */
+    uint64_t q = top >> 11;                                         /* M >> (p - 53), 53 bits */
+    int rbit = (int)((top >> 10) & 1);
+    int sticky = (top & 0x3FFu) != 0 || bi_any_below(v->m, w, (int64_t)p - 64);
+    if (rbit && (sticky || (q & 1))) q += 1;                        /* q in [2^52, 2^53] */
+    int64_t e = v->e - 53;                                          /* value = q 2^e */
+    int64_t lead = e + (q >> 53 ? 53 : 52);                         /* exponent of the leading bit */
+    if (lead < -1022 || lead > 1023) die("conversion to double outside the normal range");
+    double d = ldexp((double)q, (int)e);
+    return v->s ? -d : d;
+}
+
+OR_API void or_terms_to_mp(int T, int64_t count, const double *X, int w, uint32_t *Y) {
+    uint32_t tmp[2 + MP_WMAX];
+    if (w < 2 || w > MP_WMAX) die("conversion width");
+    for (int64_t i = 0; i < count; i++) {
+        mp_t c = mp_zero(0);
+        for (int t = 0; t < T; t++) {
+            mp_t x = mp_of_double(X[t * count + i], w);
+            c = mp_add(&c, &x, w);
+        }
+        mp_store(tmp, &c, w);
+        for (int q = 0; q < 2 + w; q++) Y[q * count + i] = tmp[q];
+    }
+}
+
+OR_API void or_mp_to_terms(int T, int64_t count, int w, const uint32_t *Y, double *X) {
+    uint32_t tmp[2 + MP_WMAX];
+    if (w < 2 || w > MP_WMAX) die("conversion width");
+    for (int64_t i = 0; i < count; i++) {
+        mp_t r;
+        for (int q = 0; q < 2 + w; q++) tmp[q] = Y[q * count + i];
+        mp_load(&r, tmp, w);
+        for (int t = 0; t < T; t++) {
+            double d = mp_round_double(&r, w);
+            X[t * count + i] = d;
+            mp_t x = mp_of_double(-d, w);
+            r = mp_add(&r, &x, w);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Format-generic element operations for the GEMM algorithms.               */
 /* Elements live in AoS buffers of `esz` bytes inside the oracle.           */
 /* ------------------------------------------------------------------------ */

@@ -17,7 +17,7 @@ import os
 
 from ._lib import (ALGO, KIND, MpgemmError, check, lib, lib_path)  # noqa: F401
 
-__all__ = ["gemm_dd", "gemm_qd", "gemm_mp", "gemm_split", "workspace_size", "set_workspace", "stream_status", "strerror",
+__all__ = ["gemm_dd", "gemm_qd", "gemm_mp", "gemm_split", "gemm_via_mp", "to_mp", "from_mp", "workspace_size", "set_workspace", "stream_status", "strerror",
            "Partition", "PrecisionChoice", "precision_log2_bound", "select_precision", "exponent_spread",
            "MpgemmError", "ALGO", "KIND", "lib", "lib_path"]
 
@@ -95,6 +95,47 @@ def gemm_mp(A, B, prec_bits, C=None, algo="block", n_min=0, depth=0, stream=None
                          ctypes.c_void_p(C.data_ptr()), _algo(algo), int(n_min), int(depth), _stream_ptr(stream))
     check(rc)
     return C
+
+
+def gemm_via_mp(A, B, prec_bits=0, C=None, algo="block", n_min=0, depth=0, stream=None):
+    """C := AB for DD (2 planes) or QD (4 planes) computed on the integer
+    pipe in prec_bits-bit multi-limb arithmetic (mpgemm_dd_via_mp /
+    mpgemm_qd_via_mp); prec_bits = 0 picks 128 for DD and 256 for QD."""
+    T = A.shape[0]
+    if T not in (2, 4):
+        raise ValueError("A must hold 2 (DD) or 4 (QD) planes")
+    bits = int(prec_bits) or (128 if T == 2 else 256)
+    L = lib()
+    fn = L.mpgemm_dd_via_mp if T == 2 else L.mpgemm_qd_via_mp
+    return _ddqd(lambda *a: fn(*a[:6], bits, *a[6:]), T, A, B, C, algo, n_min, depth, stream)
+
+
+def to_mp(X, prec_bits, Y=None, stream=None):
+    """DD / QD planes X (T, rows, cols) -> multi-limb planes (2 + w, rows,
+    cols), c = RN_p(...RN_p(x_0 + x_1)... + x_(T-1)) (mpgemm_terms_to_mp)."""
+    torch = _torch()
+    T = X.shape[0]
+    _check_tensor(X, T, (torch.float64,), "X")
+    w = int(prec_bits) // 32
+    if Y is None:
+        Y = torch.empty((2 + w, X.shape[1], X.shape[2]), dtype=torch.int32, device=X.device)
+    check(lib().mpgemm_terms_to_mp(T, X.shape[1] * X.shape[2], ctypes.c_void_p(X.data_ptr()), int(prec_bits),
+                                   ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)))
+    return Y
+
+
+def from_mp(Y, prec_bits, terms, X=None, stream=None):
+    """Multi-limb planes -> greedy expansion in `terms` doubles (2: DD,
+    4: QD), x_t = RN_53(r), r -= x_t (mpgemm_mp_to_terms)."""
+    torch = _torch()
+    w = int(prec_bits) // 32
+    dt = (torch.int32, torch.uint32) if hasattr(torch, "uint32") else (torch.int32,)
+    _check_tensor(Y, 2 + w, dt, "Y")
+    if X is None:
+        X = torch.empty((terms, Y.shape[1], Y.shape[2]), dtype=torch.float64, device=Y.device)
+    check(lib().mpgemm_mp_to_terms(int(terms), Y.shape[1] * Y.shape[2], int(prec_bits), ctypes.c_void_p(Y.data_ptr()),
+                                   ctypes.c_void_p(X.data_ptr()), _stream_ptr(stream)))
+    return X
 
 
 def gemm_split(A, B, C=None, slices=0, digits="e4m3", stream=None):

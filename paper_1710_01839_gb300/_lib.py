@@ -79,6 +79,11 @@ SIGNATURES = {
     "mpgemm_predict_time": (ctypes.c_double, [ctypes.c_double, _I64, _I64]),
     "mpgemm_sample_rows": (_I64, [_I, _I64, _I64, _I, _I]),
     "mpgemm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "mpgemm_dd_via_mp": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _I, _I, _I, _P]),
+    "mpgemm_qd_via_mp": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _I, _I, _I, _P]),
+    "mpgemm_via_mp_workspace_size": (_SZ, [_I, _I64, _I64, _I64, _I, _I]),
+    "mpgemm_terms_to_mp": (_I, [_I, _I64, _P, _I, _P, _P]),
+    "mpgemm_mp_to_terms": (_I, [_I, _I64, _I, _P, _P, _P]),
 }
 
 

@@ -226,7 +226,7 @@ int mpgemm_stream_status(void* stream) {
     }
     if (v & DEV_EXP_OVERFLOW) return MPGEMM_EOVERFLOW;
     if (v & DEV_TIMEOUT) return MPGEMM_ETIMEOUT;
-    if (v & DEV_BAD_DESC) return MPGEMM_EINVAL;
+    if (v & (DEV_BAD_DESC | DEV_NONFINITE)) return MPGEMM_EINVAL;
     return MPGEMM_OK;
 }
 

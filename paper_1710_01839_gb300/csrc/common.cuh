@@ -35,9 +35,11 @@ __host__ __device__ inline View<T> planes_view(T* p, int64_t rows, int64_t cols)
 // Device-side status word (bits of MPGEMM_DEV_*), one per device, read and
 // cleared by mpgemm_stream_status().
 enum : unsigned {
-    DEV_EXP_OVERFLOW = 1u,   // a multi-limb exponent left the int32 range
+    DEV_EXP_OVERFLOW = 1u,   // a multi-limb exponent left the int32 range (or a
+                             // conversion to double left the normal range)
     DEV_TIMEOUT = 2u,        // a bounded wait in a persistent kernel gave up
     DEV_BAD_DESC = 4u,       // a batched descriptor failed a device-side check
+    DEV_NONFINITE = 8u,      // a conversion to multi-limb met an infinity or NaN
 };
 
 unsigned* device_status_ptr();   // address of this device's status word

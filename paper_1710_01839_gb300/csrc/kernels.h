@@ -24,4 +24,9 @@ int ddqd_addsub(int kind, int64_t r, int64_t c, int64_t batch, View<double> Z, V
 int mp_addsub(int w, int64_t r, int64_t c, int64_t batch, View<uint32_t> Z, View<const uint32_t> X,
               View<const uint32_t> Y, int sub, cudaStream_t s);
 
+// Host-checkable argument errors of a GEMM call (sizes, algo, n_min, depth,
+// null or overlapping buffers of elem_bytes per element); MPGEMM_OK if none.
+int check_common(int64_t m, int64_t l, int64_t n, size_t elem_bytes, const void* A, const void* B, const void* C,
+                 int algo, int n_min, int depth);
+
 }  // namespace mpg

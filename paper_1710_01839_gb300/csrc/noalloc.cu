@@ -13,7 +13,9 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "kernels.h"
 #include "strassen.h"
+#include "tune.h"
 
 namespace mpg {
 
@@ -41,10 +43,6 @@ static int noalloc_scratch(void** out) {
     *out = g_na_ptr[dev];
     return MPGEMM_OK;
 }
-
-int check_common(int64_t m, int64_t l, int64_t n, size_t elem_bytes, const void* A, const void* B, const void* C,
-                 int algo, int n_min, int depth);
-int default_n_min(int kind);
 
 }  // namespace mpg
 

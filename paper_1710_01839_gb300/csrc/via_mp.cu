@@ -1,0 +1,265 @@
+// DD and QD GEMMs on the integer pipe: the operands are rounded to p-bit
+// multi-limb numbers, multiplied by the multi-limb GEMM (simple, block or
+// Strassen, Eqs 1-3) and the product is rounded back to T doubles.
+//
+// Why: on GB300 the FP64 pipe delivers 2 operations per clock per SM
+// (629 G op/s), while the integer pipes issue 128 thread-instructions per
+// clock per SM.  A DD multiply-accumulate costs 9.4 FP64 operations and a
+// QD one 75.75; a 128-bit multi-limb one about 290 integer instructions and
+// a 256-bit one about 450, so the multi-limb path runs DD about 1.5x and QD
+// about 7x faster, with every operation rounded to p >= 128 / 256 bits
+// (far inside the DD and QD error bounds).
+//
+// Conversions (the definitions the oracle restates):
+//   to p bits:   c = +0; for t = 0..T-1: c = RN_p(c + x_t), x_t taken exactly
+//                (a double fits in p >= 64 bits);
+//   from p bits: r = c; for t = 0..T-1: x_t = RN_53(r); r = r - x_t (exact),
+//                i.e. the greedy expansion of the multi-limb value.
+// Non-finite inputs set the invalid-input status bit; results outside the
+// normal double range set the exponent-range bit.
+#include "common.cuh"
+#include "kernels.h"
+#include "mp_arith.cuh"
+#include "strassen.h"
+#include "tune.h"
+
+namespace mpg {
+
+// x exactly as a W-limb value (W >= 2); non-finite x flags DEV_NONFINITE.
+template <int W>
+__device__ __forceinline__ void mp_from_double(double x, MPV<W>& r, unsigned& status) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 63);
+    const int ef = (int)((b >> 52) & 0x7ff);
+    uint64_t m = b & 0xFFFFFFFFFFFFFull;
+    if (ef == 0x7ff) {
+        status |= DEV_NONFINITE;
+        mp_set_zero(r, sign);
+        return;
+    }
+    if (ef == 0 && m == 0) {
+        mp_set_zero(r, sign);
+        return;
+    }
+    int k;   // x = m 2^k
+    if (ef) {
+        m |= 1ull << 52;
+        k = ef - 1075;
+    } else {
+        k = -1074;
+    }
+    const int lz = __clzll((long long)m);
+    m <<= lz;   // top bit at 63: x = m 2^(k - lz), and M = m 2^(p - 64)
+#pragma unroll
+    for (int i = 0; i < W - 2; i++) r.m[i] = 0u;
+    r.m[W - 2] = (uint32_t)m;
+    r.m[W - 1] = (uint32_t)(m >> 32);
+    r.e = k - lz + 64;
+    r.f = sign;
+}
+
+// RN_53 of a W-limb value (W >= 2).  The top 64 bits of M with the OR of
+// the rest in bit 0 round to 53 bits exactly as M does (11 > 2 bits below
+// the rounding position), and __ull2double_rn rounds to nearest even; the
+// exponent field is then moved by e - 64.  Outside the normal range: ±0
+// and DEV_EXP_OVERFLOW.
+template <int W>
+__device__ __forceinline__ double mp_to_double(const MPV<W>& v, unsigned& status) {
+    if (v.f & 2u) return (v.f & 1u) ? -0.0 : 0.0;
+    uint64_t top = ((uint64_t)v.m[W - 1] << 32) | v.m[W - 2];
+    uint32_t st = 0u;
+#pragma unroll
+    for (int i = 0; i < W - 2; i++) st |= v.m[i];
+    top |= st ? 1ull : 0ull;
+    const double d = __ull2double_rn(top);   // in [2^63, 2^64]
+    const uint64_t db = (uint64_t)__double_as_longlong(d);
+    const long long field = (long long)((db >> 52) & 0x7ff) + (long long)v.e - 64;
+    if (field < 1 || field > 2046) {
+        status |= DEV_EXP_OVERFLOW;
+        return (v.f & 1u) ? -0.0 : 0.0;
+    }
+    const uint64_t out = (db & ~(0x7ffull << 52)) | ((uint64_t)field << 52) | ((uint64_t)(v.f & 1u) << 63);
+    return __longlong_as_double((long long)out);
+}
+
+template <int W, int T>
+__global__ void k_terms_to_mp(int64_t count, const double* __restrict__ X, uint32_t* __restrict__ Y,
+                              unsigned* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    unsigned st = 0u;
+    MPV<W> c;
+    mp_set_zero(c, 0u);
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        MPV<W> x, s;
+        mp_from_double<W>(X[t * count + i], x, st);
+        mp_add<W>(c, x, s, st);
+        c = s;
+    }
+    Y[i] = (uint32_t)c.e;
+    Y[count + i] = c.f;
+#pragma unroll
+    for (int q = 0; q < W; q++) Y[(2 + q) * count + i] = c.m[q];
+    if (st) atomicOr(status, st);
+}
+
+template <int W, int T>
+__global__ void k_mp_to_terms(int64_t count, const uint32_t* __restrict__ Y, double* __restrict__ X,
+                              unsigned* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    unsigned st = 0u;
+    MPV<W> r;
+    r.e = (int)Y[i];
+    r.f = Y[count + i];
+#pragma unroll
+    for (int q = 0; q < W; q++) r.m[q] = Y[(2 + q) * count + i];
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        const double d = mp_to_double<W>(r, st);
+        X[t * count + i] = d;
+        if (t + 1 < T) {
+            MPV<W> x, s;
+            mp_from_double<W>(-d, x, st);
+            mp_add<W>(r, x, s, st);   // exact: r - RN_53(r) fits in p bits
+            r = s;
+        }
+    }
+    if (st) atomicOr(status, st);
+}
+
+template <int W>
+static int convert_w(int dir, int T, int64_t count, const double* X, uint32_t* Y, double* Xo, cudaStream_t s) {
+    unsigned* status = device_status_ptr();
+    if (!status) return MPGEMM_ECUDA;
+    const unsigned grid = ceil_div(count, 128);
+    if (dir == 0) {
+        if (T == 2) k_terms_to_mp<W, 2><<<grid, 128, 0, s>>>(count, X, Y, status);
+        else k_terms_to_mp<W, 4><<<grid, 128, 0, s>>>(count, X, Y, status);
+    } else {
+        if (T == 2) k_mp_to_terms<W, 2><<<grid, 128, 0, s>>>(count, Y, Xo, status);
+        else k_mp_to_terms<W, 4><<<grid, 128, 0, s>>>(count, Y, Xo, status);
+    }
+    return check_launch();
+}
+
+// dir 0: T-term planes X (T x count doubles) -> multi-limb planes Y
+// ((2 + w) x count words); dir 1: Y -> Xo.
+static int convert(int dir, int T, int w, int64_t count, const double* X, uint32_t* Y, double* Xo, cudaStream_t s) {
+    if (count == 0) return MPGEMM_OK;
+    switch (w) {
+        case 2: return convert_w<2>(dir, T, count, X, Y, Xo, s);
+        case 4: return convert_w<4>(dir, T, count, X, Y, Xo, s);
+        case 8: return convert_w<8>(dir, T, count, X, Y, Xo, s);
+        case 16: return convert_w<16>(dir, T, count, X, Y, Xo, s);
+        default: return MPGEMM_EUNSUPPORTED;
+    }
+}
+
+static bool via_mp_width(int prec_bits, int* w) {
+    if (prec_bits <= 0 || prec_bits % 32) return false;
+    *w = prec_bits / 32;
+    return *w == 2 || *w == 4 || *w == 8 || *w == 16;
+}
+
+static size_t mp_words(int w, int64_t r, int64_t c) { return (size_t)(2 + w) * (size_t)(r * c); }
+
+size_t via_mp_workspace_bytes(int w, int64_t m, int64_t l, int64_t n, int algo, int depth) {
+    size_t b = sizeof(uint32_t) * (mp_words(w, m, l) + mp_words(w, l, n) + mp_words(w, m, n));
+    if (algo == MPGEMM_STRASSEN && depth > 0) b += strassen_workspace_bytes(sizeof(uint32_t) * (size_t)(2 + w), m, l, n, depth);
+    return b;
+}
+
+static int via_mp_entry(int T, int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C,
+                        int prec_bits, int algo, int n_min, int depth, void* stream) {
+    int w = 0;
+    if (!via_mp_width(prec_bits, &w)) return MPGEMM_EUNSUPPORTED;
+    int rc = check_common(m, l, n, sizeof(double) * T, A, B, C, algo, n_min, depth);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    PartitionScope pscope(s);
+    if (m == 0 || n == 0) return MPGEMM_OK;
+    if (l == 0) {
+        MPG_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)T * (size_t)(m * n), s));
+        return MPGEMM_OK;
+    }
+    if (algo == MPGEMM_AUTO) {
+        Choice ch;
+        rc = auto_choice(MPGEMM_KIND_MP, prec_bits, m, l, n, stream_sms(s), &ch);
+        if (rc) return rc;
+        algo = ch.algo;
+        n_min = ch.n_min;
+        depth = ch.depth;
+    }
+    if (n_min <= 0) n_min = default_n_min(MPGEMM_KIND_MP);
+    const bool strassen = algo == MPGEMM_STRASSEN && depth > 0;
+    const size_t bytes = via_mp_workspace_bytes(w, m, l, n, strassen ? MPGEMM_STRASSEN : algo, depth);
+    void* ws = nullptr;
+    bool owned = false;
+    rc = workspace_get(bytes, s, &ws, &owned);
+    if (rc) return rc;
+    uint32_t* Am = static_cast<uint32_t*>(ws);
+    uint32_t* Bm = Am + mp_words(w, m, l);
+    uint32_t* Cm = Bm + mp_words(w, l, n);
+    uint32_t* rest = Cm + mp_words(w, m, n);
+    rc = convert(0, T, w, m * l, A, Am, nullptr, s);
+    if (!rc) rc = convert(0, T, w, l * n, B, Bm, nullptr, s);
+    if (!rc) {
+        View<const uint32_t> a = planes_view<const uint32_t>(Am, m, l), b = planes_view<const uint32_t>(Bm, l, n);
+        View<uint32_t> c = planes_view(Cm, m, n);
+        if (strassen) {
+            const size_t sb = strassen_workspace_bytes(sizeof(uint32_t) * (size_t)(2 + w), m, l, n, depth);
+            rc = strassen_mp_ws(w, m, l, n, a, b, c, n_min, depth, rest, sb, s);
+        } else {
+            rc = mp_gemm(w, algo == MPGEMM_SIMPLE ? MPGEMM_SIMPLE : MPGEMM_BLOCK, m, l, n, 1, a, b, c, n_min, s);
+        }
+    }
+    if (!rc) rc = convert(1, T, w, m * n, nullptr, Cm, C, s);
+    int rc2 = workspace_release(ws, owned, s);
+    return rc ? rc : rc2;
+}
+
+}  // namespace mpg
+
+using namespace mpg;
+
+extern "C" {
+
+int mpgemm_dd_via_mp(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int prec_bits,
+                     int algo, int n_min, int strassen_depth, void* stream) {
+    return via_mp_entry(2, m, l, n, A, B, C, prec_bits, algo, n_min, strassen_depth, stream);
+}
+
+int mpgemm_qd_via_mp(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int prec_bits,
+                     int algo, int n_min, int strassen_depth, void* stream) {
+    return via_mp_entry(4, m, l, n, A, B, C, prec_bits, algo, n_min, strassen_depth, stream);
+}
+
+size_t mpgemm_via_mp_workspace_size(int prec_bits, int64_t m, int64_t l, int64_t n, int algo, int strassen_depth) {
+    int w = 0;
+    if (!via_mp_width(prec_bits, &w) || m < 0 || l < 0 || n < 0) return 0;
+    return via_mp_workspace_bytes(w, m, l, n, algo, strassen_depth);
+}
+
+int mpgemm_terms_to_mp(int terms, int64_t count, const double* X, int prec_bits, uint32_t* Y, void* stream) {
+    int w = 0;
+    if (terms != 2 && terms != 4) return MPGEMM_EINVAL;
+    if (!via_mp_width(prec_bits, &w)) return MPGEMM_EUNSUPPORTED;
+    if (count < 0 || (count && (!X || !Y))) return MPGEMM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    PartitionScope pscope(s);
+    return convert(0, terms, w, count, X, Y, nullptr, s);
+}
+
+int mpgemm_mp_to_terms(int terms, int64_t count, int prec_bits, const uint32_t* Y, double* X, void* stream) {
+    int w = 0;
+    if (terms != 2 && terms != 4) return MPGEMM_EINVAL;
+    if (!via_mp_width(prec_bits, &w)) return MPGEMM_EUNSUPPORTED;
+    if (count < 0 || (count && (!X || !Y))) return MPGEMM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    PartitionScope pscope(s);
+    return convert(1, terms, w, count, nullptr, const_cast<uint32_t*>(Y), X, s);
+}
+
+}  // extern "C"
