@@ -244,7 +244,16 @@ int mpgemm_mp_to_terms(int terms, int64_t count, int prec_bits, const uint32_t* 
  *               kernel)
  *   tile        edge of the C tile one CTA computes: 16 or 32 for DD / QD
  *               (0 = the cost model's choice when one is installed, else
- *               32), always 16 for multi-limb
+ *               32), always 16 for multi-limb and for engine = 1
+ *   engine      0: the format's own arithmetic (FP64 for DD / QD);
+ *               1 (DD / QD only, MPGEMM_EINVAL otherwise): the integer
+ *               pipe, as mpgemm_dd_via_mp / mpgemm_qd_via_mp with 128 /
+ *               256-bit limbs, MPGEMM_BLOCK and n_min = 16.  The plan then
+ *               owns multi-limb copies of A, B and C (cudaMalloc at plan
+ *               time); each run converts every such A and B in one pass per
+ *               format before the persistent kernel and every C in one pass
+ *               per format after it (inside the captured graph of
+ *               mpgemm_batched_run_graph).
  * mpgemm_batched_plan validates the descriptors, builds the table of work
  * items (one per C tile, heaviest first) and copies it to the device
  * (cudaMalloc + synchronous copies: plan outside hot loops).  The plan keeps
@@ -258,7 +267,8 @@ int mpgemm_mp_to_terms(int terms, int64_t count, int prec_bits, const uint32_t* 
  * mpgemm_batched_sequential runs the same descriptors as one ordinary launch
  * per GEMM (block algorithm, n_min = tile): the baseline.
  * Results are bit-identical to mpgemm_dd / mpgemm_qd / mpgemm_mp with
- * MPGEMM_BLOCK and n_min = tile.
+ * MPGEMM_BLOCK and n_min = tile (engine 1: to mpgemm_dd_via_mp /
+ * mpgemm_qd_via_mp as above).
  * ------------------------------------------------------------------------- */
 typedef struct {
     int kind;
@@ -268,7 +278,7 @@ typedef struct {
     const void* B;
     void* C;
     int tile;
-    int reserved;
+    int engine;
 } mpgemm_desc;
 typedef struct mpgemm_plan_s* mpgemm_plan;
 int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* plan);

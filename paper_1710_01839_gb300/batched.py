@@ -11,7 +11,7 @@ from ._lib import KIND, check, lib
 class Desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("prec_bits", ctypes.c_int), ("m", ctypes.c_int64),
                 ("l", ctypes.c_int64), ("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
-                ("C", ctypes.c_void_p), ("tile", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("C", ctypes.c_void_p), ("tile", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 def _stream(stream):
@@ -20,14 +20,17 @@ def _stream(stream):
     return ctypes.c_void_p(int(s.cuda_stream))
 
 
-def make_descs(problems, tiles=None):
+def make_descs(problems, tiles=None, integer_pipe=False):
     """problems: list of (fmt, A, B, C) with device tensors; fmt in
-    {'dd', 'qd', 'mp256'}.  tiles: optional list of tile edges."""
+    {'dd', 'qd', 'mp256'}.  tiles: optional list of tile edges.
+    integer_pipe: run the DD and QD problems on the integer pipe (128 / 256-bit
+    limbs; engine = 1)."""
     arr = (Desc * len(problems))()
     for i, (fmt, A, B, C) in enumerate(problems):
         kind = KIND["mp" if fmt.startswith("mp") else fmt]
+        engine = 1 if integer_pipe and kind != 2 else 0
         arr[i] = Desc(kind, 256 if kind == 2 else 0, A.shape[1], A.shape[2], B.shape[2], A.data_ptr(), B.data_ptr(),
-                      C.data_ptr(), 0 if tiles is None else int(tiles[i]), 0)
+                      C.data_ptr(), 0 if tiles is None else int(tiles[i]), engine)
     return arr
 
 

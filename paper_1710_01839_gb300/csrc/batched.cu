@@ -9,6 +9,13 @@
 // CTA ever waits for another: the only shared state is the counter.  The
 // launch (counter reset + kernel) can be captured once into a CUDA graph and
 // replayed.
+//
+// A DD or QD descriptor with engine = 1 runs on the integer pipe: the plan
+// owns 128-bit (DD) or 256-bit (QD) multi-limb copies of its A, B and C;
+// before the persistent launch one conversion pass per format rounds every
+// such A and B into them, the persistent kernel computes the multi-limb
+// tiles, and one pass per format rounds C back to doubles (the definitions
+// of mpgemm_dd_via_mp / mpgemm_qd_via_mp).
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -16,12 +23,13 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "mp_convert.cuh"
 #include "profile.h"
 #include "tiles.cuh"
 
 namespace mpg {
 
-enum TileKind : int { T_DD16 = 0, T_DD32 = 1, T_QD16 = 2, T_QD32 = 3, T_MP256 = 4 };
+enum TileKind : int { T_DD16 = 0, T_DD32 = 1, T_QD16 = 2, T_QD32 = 3, T_MP256 = 4, T_MP128 = 5 };
 
 struct DevDesc {
     int tk;
@@ -54,11 +62,14 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
         const Work w = work[it];
         const DevDesc d = descs[w.desc];
         const int64_t i0 = (int64_t)w.tm * d.tile, j0 = (int64_t)w.tn * d.tile;
-        if (d.tk == T_MP256) {
+        if (d.tk == T_MP256 || d.tk == T_MP128) {
             View<const uint32_t> a = planes_view((const uint32_t*)d.A, d.m, d.l);
             View<const uint32_t> b = planes_view((const uint32_t*)d.B, d.l, d.n);
             View<uint32_t> c = planes_view((uint32_t*)d.C, d.m, d.n);
-            mp_block_tile<8, 8>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
+            if (d.tk == T_MP256)
+                mp_block_tile<8, 8>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
+            else
+                mp_block_tile<4, 8>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
         } else {
             View<const double> a = planes_view((const double*)d.A, d.m, d.l);
             View<const double> b = planes_view((const double*)d.B, d.l, d.n);
@@ -74,21 +85,87 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
     if (st) atomicOr(status, st);
 }
 
-// Relative cost of one multiply-accumulate, for ordering work items only
-// (FP64 operations per MAC for DD / QD; the 256-bit multi-limb MAC measured
-// against DD on this GPU).
+// Relative cost of one multiply-accumulate, for ordering work items only:
+// time per MAC of each tile's kernel at full occupancy on GB300, DD = 9.4
+// (FP64 operations: DD 9.4, QD 76; the 128- and 256-bit multi-limb MACs
+// issue 290 and 452 instructions, about 0.6 and 0.95 of a DD MAC's time).
 static double mac_cost(int tk) {
     switch (tk) {
         case T_DD16: case T_DD32: return 9.4;
         case T_QD16: case T_QD32: return 76.0;
-        default: return 40.0;
+        case T_MP128: return 6.0;
+        default: return 9.0;
     }
 }
+
+// One conversion job of the integer-pipe descriptors: `count` elements
+// between T-term double planes and (2 + W)-word multi-limb planes.
+struct ConvJob {
+    const double* x;   // to multi-limb: source; from: unused
+    double* xo;        // from multi-limb: destination
+    uint32_t* y;       // multi-limb planes
+    int64_t count;
+    int64_t first;     // prefix sum of the counts before this job
+};
+
+// Element i of the concatenated jobs: its job by binary search on `first`.
+__device__ __forceinline__ int conv_job_of(const ConvJob* jobs, int njobs, int64_t i) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].first <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int W, int T>
+__global__ void k_batched_to_mp(const ConvJob* __restrict__ jobs, int njobs, int64_t total, unsigned* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const ConvJob j = jobs[conv_job_of(jobs, njobs, i)];
+    const int64_t e = i - j.first, cnt = j.count;
+    unsigned st = 0u;
+    MPV<W> c;
+    terms_to_mp<W, T>(j.x + e, cnt, c, st);
+    j.y[e] = (uint32_t)c.e;
+    j.y[cnt + e] = c.f;
+#pragma unroll
+    for (int q = 0; q < W; q++) j.y[(2 + q) * cnt + e] = c.m[q];
+    if (st) atomicOr(status, st);
+}
+
+template <int W, int T>
+__global__ void k_batched_from_mp(const ConvJob* __restrict__ jobs, int njobs, int64_t total, unsigned* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const ConvJob j = jobs[conv_job_of(jobs, njobs, i)];
+    const int64_t e = i - j.first, cnt = j.count;
+    unsigned st = 0u;
+    MPV<W> r;
+    r.e = (int)j.y[e];
+    r.f = j.y[cnt + e];
+#pragma unroll
+    for (int q = 0; q < W; q++) r.m[q] = j.y[(2 + q) * cnt + e];
+    mp_to_terms<W, T>(r, j.xo + e, cnt, st);
+    if (st) atomicOr(status, st);
+}
+
+// A conversion pass: its device job table and total element count.
+struct ConvPass {
+    ConvJob* d_jobs = nullptr;
+    int njobs = 0;
+    int64_t total = 0;
+};
 
 }  // namespace mpg
 
 struct mpgemm_plan_s {
     int count = 0, nwork = 0, grid = 0, device = 0;
+    // conversion passes of the integer-pipe descriptors: [0] DD in, [1] QD
+    // in, [2] DD out, [3] QD out; the multi-limb copies live in d_limbs
+    mpg::ConvPass conv[4];
+    uint32_t* d_limbs = nullptr;
     mpg::DevDesc* d_descs = nullptr;
     mpg::Work* d_work = nullptr;
     unsigned* d_counter = nullptr;
@@ -119,6 +196,18 @@ static size_t desc_elem_bytes(const mpgemm_desc& d) {
 
 extern "C" {
 
+static void plan_free(mpgemm_plan P) {
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->cap) cudaStreamDestroy(P->cap);
+    cudaFree(P->d_descs);
+    cudaFree(P->d_work);
+    cudaFree(P->d_counter);
+    cudaFree(P->d_limbs);
+    for (auto& c : P->conv) cudaFree(c.d_jobs);
+    delete P;
+}
+
 int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
     if (!out || count < 0 || (count > 0 && !descs)) return MPGEMM_EINVAL;
     *out = nullptr;
@@ -132,13 +221,18 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
         double cost;
     };
     std::vector<Item> items;
+    std::vector<int64_t> limb_off(count, -1);   // word offset of an integer-pipe descriptor's copies
+    int64_t limb_words = 0;
     for (int i = 0; i < count; i++) {
         const mpgemm_desc& d = descs[i];
-        if (d.m < 0 || d.l < 0 || d.n < 0 || d.m > 65535 * 64 || d.n > 65535 * 64) {
+        if (d.m < 0 || d.l < 0 || d.n < 0 || d.m > 65535 * 64 || d.n > 65535 * 64 || d.engine < 0 || d.engine > 1 ||
+            (d.engine == 1 && d.kind == MPGEMM_KIND_MP)) {
             delete P;
             return MPGEMM_EINVAL;
         }
-        int tile = d.kind == MPGEMM_KIND_MP ? 16 : (d.tile == 16 || d.tile == 32 ? d.tile : (d.tile == 0 ? 0 : -1));
+        int tile = d.kind == MPGEMM_KIND_MP || d.engine == 1
+                       ? 16
+                       : (d.tile == 16 || d.tile == 32 ? d.tile : (d.tile == 0 ? 0 : -1));
         if (tile == 0) {   // the cost model's choice when one is installed, else 32
             tile = cost_model_tile(d.kind, d.prec_bits, d.m, d.l, d.n);
             if (tile == 0) tile = 32;
@@ -148,16 +242,21 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
             return MPGEMM_EINVAL;
         }
         int tk;
-        if (int rc = desc_tile_kind(d, tile, &tk)) {
+        if (d.engine == 1) {
+            tk = d.kind == MPGEMM_KIND_DD ? T_MP128 : T_MP256;
+        } else if (int rc = desc_tile_kind(d, tile, &tk)) {
             delete P;
             return rc;
         }
-        size_t eb = desc_elem_bytes(d);
         if ((d.m * d.l && !d.A) || (d.l * d.n && !d.B) || (d.m * d.n && !d.C)) {
             delete P;
             return MPGEMM_EINVAL;
         }
-        (void)eb;
+        if (d.engine == 1) {
+            const int64_t words = 2 + (d.kind == MPGEMM_KIND_DD ? 4 : 8);
+            limb_off[i] = limb_words;
+            limb_words += words * (d.m * d.l + d.l * d.n + d.m * d.n);
+        }
         P->tiles.push_back(tile);
         dd[i] = DevDesc{tk, tile, d.m, d.l, d.n, d.A, d.B, d.C};
         int64_t tm = (d.m + tile - 1) / tile, tn = (d.n + tile - 1) / tile;
@@ -172,10 +271,43 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
     int rc = MPGEMM_OK;
     auto fail = [&](cudaError_t e) {
         set_last_cuda_error(e);
-        rc = MPGEMM_ECUDA;
+        rc = e == cudaErrorMemoryAllocation ? MPGEMM_ENOMEM : MPGEMM_ECUDA;
     };
     cudaError_t e;
-    if ((e = cudaGetDevice(&P->device)) != cudaSuccess) fail(e);
+    if (limb_words && (e = cudaMalloc(&P->d_limbs, sizeof(uint32_t) * (size_t)limb_words)) != cudaSuccess) fail(e);
+    // point the integer-pipe descriptors at their copies; conversion jobs
+    std::vector<ConvJob> jobs[4];
+    for (int i = 0; i < count && !rc; i++) {
+        if (limb_off[i] < 0) continue;
+        const mpgemm_desc& d = descs[i];
+        const bool is_dd = d.kind == MPGEMM_KIND_DD;
+        const int64_t words = 2 + (is_dd ? 4 : 8);
+        uint32_t* Am = P->d_limbs + limb_off[i];
+        uint32_t* Bm = Am + words * d.m * d.l;
+        uint32_t* Cm = Bm + words * d.l * d.n;
+        dd[i].A = Am;
+        dd[i].B = Bm;
+        dd[i].C = Cm;
+        const int in = is_dd ? 0 : 1, outp = is_dd ? 2 : 3;
+        if (d.m * d.l) jobs[in].push_back(ConvJob{(const double*)d.A, nullptr, Am, d.m * d.l, 0});
+        if (d.l * d.n) jobs[in].push_back(ConvJob{(const double*)d.B, nullptr, Bm, d.l * d.n, 0});
+        if (d.m * d.n) jobs[outp].push_back(ConvJob{nullptr, (double*)d.C, Cm, d.m * d.n, 0});
+    }
+    for (int k = 0; k < 4 && !rc; k++) {
+        int64_t first = 0;
+        for (auto& j : jobs[k]) {
+            j.first = first;
+            first += j.count;
+        }
+        P->conv[k].njobs = (int)jobs[k].size();
+        P->conv[k].total = first;
+        if (jobs[k].empty()) continue;
+        if ((e = cudaMalloc(&P->conv[k].d_jobs, sizeof(ConvJob) * jobs[k].size())) != cudaSuccess) fail(e);
+        else if ((e = cudaMemcpy(P->conv[k].d_jobs, jobs[k].data(), sizeof(ConvJob) * jobs[k].size(),
+                                 cudaMemcpyHostToDevice)) != cudaSuccess)
+            fail(e);
+    }
+    if (!rc && (e = cudaGetDevice(&P->device)) != cudaSuccess) fail(e);
     int sms = 0, occ = 0;
     if (!rc && (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device)) != cudaSuccess) fail(e);
     if (!rc && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, 256, 0)) != cudaSuccess) fail(e);
@@ -189,27 +321,53 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
         fail(e);
     if (!rc && (e = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking)) != cudaSuccess) fail(e);
     if (rc) {
-        cudaFree(P->d_descs);
-        cudaFree(P->d_work);
-        cudaFree(P->d_counter);
-        if (P->cap) cudaStreamDestroy(P->cap);
-        delete P;
+        plan_free(P);
         return rc;
     }
     *out = P;
     return MPGEMM_OK;
 }
 
+// Conversion pass k of a plan (0 / 1: DD / QD operands in, 2 / 3: DD / QD
+// products out).
+static int launch_conv(mpgemm_plan P, int k, cudaStream_t s, unsigned* status) {
+    const ConvPass& c = P->conv[k];
+    if (c.total == 0) return MPGEMM_OK;
+    const unsigned grid = ceil_div(c.total, 128);
+    switch (k) {
+        case 0: k_batched_to_mp<4, 2><<<grid, 128, 0, s>>>(c.d_jobs, c.njobs, c.total, status); break;
+        case 1: k_batched_to_mp<8, 4><<<grid, 128, 0, s>>>(c.d_jobs, c.njobs, c.total, status); break;
+        case 2: k_batched_from_mp<4, 2><<<grid, 128, 0, s>>>(c.d_jobs, c.njobs, c.total, status); break;
+        default: k_batched_from_mp<8, 4><<<grid, 128, 0, s>>>(c.d_jobs, c.njobs, c.total, status); break;
+    }
+    return check_launch();
+}
+
+// The plan's launches on stream s: counter reset, operand conversions, the
+// persistent kernel (bracketed for mpgemm_profile when `prof`), product
+// conversions.
+static int plan_launches(mpgemm_plan P, cudaStream_t s, unsigned* status, bool prof) {
+    MPG_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(unsigned), s));
+    for (int k = 0; k < 2; k++)
+        if (int rc = launch_conv(P, k, s, status)) return rc;
+    if (prof) {
+        ProfScope ps(s);
+        k_batched<<<P->grid, 256, 0, s>>>(P->d_descs, P->d_work, P->nwork, P->d_counter, status);
+    } else {
+        k_batched<<<P->grid, 256, 0, s>>>(P->d_descs, P->d_work, P->nwork, P->d_counter, status);
+    }
+    if (int rc = check_launch()) return rc;
+    for (int k = 2; k < 4; k++)
+        if (int rc = launch_conv(P, k, s, status)) return rc;
+    return MPGEMM_OK;
+}
+
 int mpgemm_batched_run(mpgemm_plan P, void* stream) {
     if (!P) return MPGEMM_EINVAL;
     if (P->nwork == 0) return MPGEMM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     unsigned* status = device_status_ptr();
     if (!status) return MPGEMM_ECUDA;
-    MPG_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(unsigned), s));
-    ProfScope ps(s);
-    k_batched<<<P->grid, 256, 0, s>>>(P->d_descs, P->d_work, P->nwork, P->d_counter, status);
-    return check_launch();
+    return plan_launches(P, (cudaStream_t)stream, status, true);
 }
 
 int mpgemm_batched_run_graph(mpgemm_plan P, void* stream) {
@@ -219,15 +377,13 @@ int mpgemm_batched_run_graph(mpgemm_plan P, void* stream) {
         unsigned* status = device_status_ptr();   // resolve before capture
         if (!status) return MPGEMM_ECUDA;
         MPG_CUDA(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e1 = cudaMemsetAsync(P->d_counter, 0, sizeof(unsigned), P->cap);
-        k_batched<<<P->grid, 256, 0, P->cap>>>(P->d_descs, P->d_work, P->nwork, P->d_counter, status);
-        cudaError_t e2 = cudaGetLastError();
+        int rc = plan_launches(P, P->cap, status, false);
         cudaGraph_t g = nullptr;
         cudaError_t e3 = cudaStreamEndCapture(P->cap, &g);
-        if (e1 || e2 || e3) {
+        if (rc || e3) {
             if (g) cudaGraphDestroy(g);
-            set_last_cuda_error(e1 ? e1 : e2 ? e2 : e3);
-            return MPGEMM_ECUDA;
+            if (e3) set_last_cuda_error(e3);
+            return rc ? rc : MPGEMM_ECUDA;
         }
         cudaError_t e4 = cudaGraphInstantiate(&P->exec, g, 0);
         if (e4) {
@@ -243,13 +399,7 @@ int mpgemm_batched_run_graph(mpgemm_plan P, void* stream) {
 
 int mpgemm_batched_destroy(mpgemm_plan P) {
     if (!P) return MPGEMM_OK;
-    if (P->exec) cudaGraphExecDestroy(P->exec);
-    if (P->graph) cudaGraphDestroy(P->graph);
-    if (P->cap) cudaStreamDestroy(P->cap);
-    cudaFree(P->d_descs);
-    cudaFree(P->d_work);
-    cudaFree(P->d_counter);
-    delete P;
+    plan_free(P);
     return MPGEMM_OK;
 }
 
@@ -269,7 +419,13 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
         const mpgemm_desc& d = descs[i];
         int tile = d.tile == 16 || d.tile == 32 ? d.tile : 32;
         int rc;
-        if (d.kind == MPGEMM_KIND_DD)
+        if (d.engine == 1 && d.kind == MPGEMM_KIND_DD)
+            rc = mpgemm_dd_via_mp(d.m, d.l, d.n, (const double*)d.A, (const double*)d.B, (double*)d.C, 128,
+                                  MPGEMM_BLOCK, 16, 0, stream);
+        else if (d.engine == 1 && d.kind == MPGEMM_KIND_QD)
+            rc = mpgemm_qd_via_mp(d.m, d.l, d.n, (const double*)d.A, (const double*)d.B, (double*)d.C, 256,
+                                  MPGEMM_BLOCK, 16, 0, stream);
+        else if (d.kind == MPGEMM_KIND_DD)
             rc = mpgemm_dd(d.m, d.l, d.n, (const double*)d.A, (const double*)d.B, (double*)d.C, MPGEMM_BLOCK, tile, 0,
                            stream);
         else if (d.kind == MPGEMM_KIND_QD)

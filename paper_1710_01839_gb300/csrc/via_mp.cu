@@ -20,67 +20,11 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "mp_arith.cuh"
+#include "mp_convert.cuh"
 #include "strassen.h"
 #include "tune.h"
 
 namespace mpg {
-
-// x exactly as a W-limb value (W >= 2); non-finite x flags DEV_NONFINITE.
-template <int W>
-__device__ __forceinline__ void mp_from_double(double x, MPV<W>& r, unsigned& status) {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const unsigned sign = (unsigned)(b >> 63);
-    const int ef = (int)((b >> 52) & 0x7ff);
-    uint64_t m = b & 0xFFFFFFFFFFFFFull;
-    if (ef == 0x7ff) {
-        status |= DEV_NONFINITE;
-        mp_set_zero(r, sign);
-        return;
-    }
-    if (ef == 0 && m == 0) {
-        mp_set_zero(r, sign);
-        return;
-    }
-    int k;   // x = m 2^k
-    if (ef) {
-        m |= 1ull << 52;
-        k = ef - 1075;
-    } else {
-        k = -1074;
-    }
-    const int lz = __clzll((long long)m);
-    m <<= lz;   // top bit at 63: x = m 2^(k - lz), and M = m 2^(p - 64)
-#pragma unroll
-    for (int i = 0; i < W - 2; i++) r.m[i] = 0u;
-    r.m[W - 2] = (uint32_t)m;
-    r.m[W - 1] = (uint32_t)(m >> 32);
-    r.e = k - lz + 64;
-    r.f = sign;
-}
-
-// RN_53 of a W-limb value (W >= 2).  The top 64 bits of M with the OR of
-// the rest in bit 0 round to 53 bits exactly as M does (11 > 2 bits below
-// the rounding position), and __ull2double_rn rounds to nearest even; the
-// exponent field is then moved by e - 64.  Outside the normal range: ±0
-// and DEV_EXP_OVERFLOW.
-template <int W>
-__device__ __forceinline__ double mp_to_double(const MPV<W>& v, unsigned& status) {
-    if (v.f & 2u) return (v.f & 1u) ? -0.0 : 0.0;
-    uint64_t top = ((uint64_t)v.m[W - 1] << 32) | v.m[W - 2];
-    uint32_t st = 0u;
-#pragma unroll
-    for (int i = 0; i < W - 2; i++) st |= v.m[i];
-    top |= st ? 1ull : 0ull;
-    const double d = __ull2double_rn(top);   // in [2^63, 2^64]
-    const uint64_t db = (uint64_t)__double_as_longlong(d);
-    const long long field = (long long)((db >> 52) & 0x7ff) + (long long)v.e - 64;
-    if (field < 1 || field > 2046) {
-        status |= DEV_EXP_OVERFLOW;
-        return (v.f & 1u) ? -0.0 : 0.0;
-    }
-    const uint64_t out = (db & ~(0x7ffull << 52)) | ((uint64_t)field << 52) | ((uint64_t)(v.f & 1u) << 63);
-    return __longlong_as_double((long long)out);
-}
 
 template <int W, int T>
 __global__ void k_terms_to_mp(int64_t count, const double* __restrict__ X, uint32_t* __restrict__ Y,
@@ -89,14 +33,7 @@ __global__ void k_terms_to_mp(int64_t count, const double* __restrict__ X, uint3
     if (i >= count) return;
     unsigned st = 0u;
     MPV<W> c;
-    mp_set_zero(c, 0u);
-#pragma unroll
-    for (int t = 0; t < T; t++) {
-        MPV<W> x, s;
-        mp_from_double<W>(X[t * count + i], x, st);
-        mp_add<W>(c, x, s, st);
-        c = s;
-    }
+    terms_to_mp<W, T>(X + i, count, c, st);
     Y[i] = (uint32_t)c.e;
     Y[count + i] = c.f;
 #pragma unroll
@@ -115,17 +52,7 @@ __global__ void k_mp_to_terms(int64_t count, const uint32_t* __restrict__ Y, dou
     r.f = Y[count + i];
 #pragma unroll
     for (int q = 0; q < W; q++) r.m[q] = Y[(2 + q) * count + i];
-#pragma unroll
-    for (int t = 0; t < T; t++) {
-        const double d = mp_to_double<W>(r, st);
-        X[t * count + i] = d;
-        if (t + 1 < T) {
-            MPV<W> x, s;
-            mp_from_double<W>(-d, x, st);
-            mp_add<W>(r, x, s, st);   // exact: r - RN_53(r) fits in p bits
-            r = s;
-        }
-    }
+    mp_to_terms<W, T>(r, X + i, count, st);
     if (st) atomicOr(status, st);
 }
 

@@ -110,3 +110,60 @@ def test_plan_rejects_bad_descriptors():
     d[0].prec_bits = 256
     d[0].m = -1
     assert mpg.lib().mpgemm_batched_plan(d, 1, ctypes.byref(h)) == -1
+
+
+def test_integer_pipe_engine_equals_sequential_graph_and_oracle():
+    # DD and QD descriptors with engine = 1 (128 / 256-bit limbs, conversion
+    # passes around the persistent kernel) beside ordinary 256-bit ones:
+    # persistent == graph replay == one mpgemm_*_via_mp launch per GEMM ==
+    # the oracle's conversion + multi-limb GEMM, bit for bit
+    from paper_1710_01839_gb300 import batched
+    rng = np.random.default_rng(9)
+    shapes = [(int(rng.integers(1, 90)), int(rng.integers(0, 90)), int(rng.integers(1, 90)),
+               ["dd", "qd", "mp256"][i % 3]) for i in range(24)]
+    shapes += [(40, 1, 23, "dd"), (1, 1, 1, "qd"), (17, 0, 9, "dd")]
+    probs, hostdata = _problems(shapes, 300)
+    descs = batched.make_descs(probs, integer_pipe=True)
+    assert [d.engine for d in descs] == [0 if p == "mp256" else 1 for p, _, _, _ in probs]
+    batched.sequential(descs)
+    ref = _snapshot(probs)
+    plan = batched.Plan(descs)
+    assert set(plan.info()["tiles"]) == {16}
+    for _, _, _, C in probs:
+        C.zero_()
+    plan.run()
+    got = _snapshot(probs)
+    for r, g in zip(ref, got):
+        assert np.array_equal(r.view(np.uint8), g.view(np.uint8))
+    for _ in range(2):
+        for _, _, _, C in probs:
+            C.zero_()
+        plan.run_graph()
+        for r, g in zip(ref, _snapshot(probs)):
+            assert np.array_equal(r.view(np.uint8), g.view(np.uint8))
+    plan.close()
+    assert mpg.stream_status() == 0
+    for (prec, _, _, _), (A, B), C in zip(probs, hostdata, got):
+        if prec == "mp256":
+            assert np.array_equal(C, oracle.mp_gemm(A, B, prec_bits=256))
+        elif A.shape[2] == 0:
+            assert not C.any()
+        else:
+            bits = 128 if prec == "dd" else 256
+            Co = oracle.gemm_via_mp(A, B, bits, algo="block", n_min=16)
+            assert np.array_equal(C.view(np.uint64), Co.view(np.uint64))
+
+
+def test_plan_rejects_bad_engine():
+    import ctypes
+    from paper_1710_01839_gb300 import batched
+    import torch
+    A = torch.zeros((6 + 4, 4, 4), dtype=torch.int32, device="cuda")
+    D = torch.zeros((2, 4, 4), dtype=torch.float64, device="cuda")
+    h = ctypes.c_void_p()
+    d = batched.make_descs([("mp256", A, A, A)])
+    d[0].engine = 1               # the integer pipe is for DD / QD descriptors
+    assert mpg.lib().mpgemm_batched_plan(d, 1, ctypes.byref(h)) == -1
+    d = batched.make_descs([("dd", D, D, D)])
+    d[0].engine = 2
+    assert mpg.lib().mpgemm_batched_plan(d, 1, ctypes.byref(h)) == -1
