@@ -6,6 +6,7 @@ launch list or capture can be reproduced from the command line alone.
     python -m paper_1710_01839_gb300.profile_cases mp --bits 128,256,512,1024 --n 256 --reps 2
     python -m paper_1710_01839_gb300.profile_cases split --fmt qd --n 1024 --reps 3
     python -m paper_1710_01839_gb300.profile_cases gemm --fmt qd --n 512 --algo block --n_min 32
+    python -m paper_1710_01839_gb300.profile_cases via --fmt dd --bits 128 --n 2048 --algo strassen --n_min 512 --depth 3
 
 Inputs: multi-limb mantissas uniform with exponents U{-64..64}
 (inputs.mp_random, seeds 5 and 6); DD / QD entries with per-element
@@ -39,6 +40,16 @@ def _gemm(args, mpg, I, torch):
         f(A, B, C, algo=args.algo, n_min=args.n_min, depth=args.depth)
 
 
+def _via(args, mpg, I, torch):
+    gen = I.dd_random if args.fmt == "dd" else I.qd_random
+    A = torch.from_numpy(gen(args.n, args.n, I.seed_for(1, 0), exp_spread=20)).cuda()
+    B = torch.from_numpy(gen(args.n, args.n, I.seed_for(1, 1), exp_spread=20)).cuda()
+    C = torch.empty_like(A)
+    bits = int(str(args.bits).split(",")[0])
+    for _ in range(args.reps):
+        mpg.gemm_via_mp(A, B, bits, C, algo=args.algo, n_min=args.n_min, depth=args.depth)
+
+
 def _split(args, mpg, I, torch):
     if args.fmt == "qd":
         A = I.qd_random(args.n, args.n, I.seed_for(1, 0), exp_spread=20)
@@ -53,9 +64,9 @@ def _split(args, mpg, I, torch):
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("case", choices=["mp", "gemm", "split"])
-    ap.add_argument("--fmt", default="dd", choices=["dd", "qd"], help="gemm / split: element format")
-    ap.add_argument("--bits", default="256", help="mp: precision(s) in bits, comma separated")
+    ap.add_argument("case", choices=["mp", "gemm", "split", "via"])
+    ap.add_argument("--fmt", default="dd", choices=["dd", "qd"], help="gemm / split / via: element format")
+    ap.add_argument("--bits", default="256", help="mp: precision(s) in bits, comma separated; via: limb precision")
     ap.add_argument("--n", type=int, default=512, help="m = l = n")
     ap.add_argument("--algo", default="block", choices=["simple", "block", "strassen"])
     ap.add_argument("--n_min", type=int, default=16)
@@ -67,7 +78,7 @@ def main():
     import torch
     import paper_1710_01839_gb300 as mpg
     from paper_1710_01839_gb300 import inputs as I
-    {"mp": _mp, "gemm": _gemm, "split": _split}[args.case](args, mpg, I, torch)
+    {"mp": _mp, "gemm": _gemm, "split": _split, "via": _via}[args.case](args, mpg, I, torch)
     torch.cuda.synchronize()
     print("ok")
 
