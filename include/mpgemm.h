@@ -414,13 +414,18 @@ int mpgemm_selftest_wait_timeout(int limit_ms, void* stream);
  *       beta = 2t + t^2 + (S+1) c 2^(2 spread + 2 - bS) + 2^-106
  *       (b = 7 / 5, c = 1.02 / 1.07: the truncation of both operands, the
  *       dropped triangle s + t > S + 1, the final DD rounding).
+ *   MPGEMM_SEL_DD_VIA_MP / _QD_VIA_MP  DD / QD on the integer pipe with
+ *       p-bit limbs (prec_bits; 0 = 128 / 256): gamma_l(p) + 2^(1-p) (the
+ *       operands' rounding) + 2^(-53 T) (the final T-term expansion,
+ *       T = 2 / 4), with a 2^-40 relative allowance for second-order terms.
  * Strassen is not offered (its bound is normwise, not elementwise).
  *   mpgemm_precision_log2_bound  log2(beta) of one configuration (NaN for
  *                                invalid arguments).
  *   mpgemm_select_precision      the configurations with log2(beta) <=
  *                                log2_target (split precision with the
  *                                fewest slices; the QD split only when
- *                                no DD split meets the target; the
+ *                                no DD split meets the target; DD / QD on
+ *                                the integer pipe at 128 / 256 bits; the
  *                                smallest multi-limb
  *                                precision of 128..1024 bits), fastest
  *                                first by predicted time (the installed cost
@@ -439,11 +444,13 @@ enum {
     MPGEMM_SEL_MP = 2,
     MPGEMM_SEL_OZAKI_INT8 = 3,
     MPGEMM_SEL_OZAKI_E4M3 = 4,
-    MPGEMM_SEL_OZAKI_QD = 5   /* split-precision QD (mpgemm_qd_ozaki), e4m3 digits, final rounding 2^-211 */
+    MPGEMM_SEL_OZAKI_QD = 5,  /* split-precision QD (mpgemm_qd_ozaki), e4m3 digits, final rounding 2^-211 */
+    MPGEMM_SEL_DD_VIA_MP = 6, /* mpgemm_dd_via_mp, 128-bit limbs                                           */
+    MPGEMM_SEL_QD_VIA_MP = 7  /* mpgemm_qd_via_mp, 256-bit limbs                                           */
 };
 typedef struct {
     int method;          /* MPGEMM_SEL_*                                  */
-    int prec_bits;       /* multi-limb precision (MPGEMM_SEL_MP), else 0   */
+    int prec_bits;       /* limb precision (MPGEMM_SEL_MP, _VIA_MP), else 0 */
     int num_slices;      /* split-precision S, else 0                      */
     double log2_bound;   /* log2 of the a-priori bound beta                */
     double est_ms;       /* predicted time                                 */

@@ -190,7 +190,8 @@ def strerror(status):
     return lib().mpgemm_strerror(int(status)).decode()
 
 
-SEL_METHOD = {0: "dd", 1: "qd", 2: "mp", 3: "ozaki_int8", 4: "ozaki_e4m3", 5: "ozaki_qd"}
+SEL_METHOD = {0: "dd", 1: "qd", 2: "mp", 3: "ozaki_int8", 4: "ozaki_e4m3", 5: "ozaki_qd", 6: "dd_via_mp",
+              7: "qd_via_mp"}
 _SEL_CODE = {v: k for k, v in SEL_METHOD.items()}
 
 

@@ -18,6 +18,12 @@
 //                           for b = 7 / 5), the final DD rounding 2^-106:
 //                           beta = 2t + t^2 + triangle + 2^-106 (DD result;
 //                           2^-211 for the QD result of the QD split).
+//   DD / QD on the integer pipe  (p-bit limbs, T = 2 / 4 result terms)
+//                           gamma_l(p) for the multi-limb GEMM, 2^(1-p) for
+//                           rounding both operands to p bits, 2^(-53 T) for
+//                           the final greedy expansion (each term takes all
+//                           but 2^-53 of the remainder), each to first order
+//                           (a 2^-40 relative allowance covers the rest).
 // Strassen is left out: its bound (2^-96 l max|A| max|B| for DD) is not
 // elementwise.  Predicted times: the installed cost model's best simple /
 // block configuration for DD, QD and multi-limb, else the block rates
@@ -68,6 +74,25 @@ double static_block_gflops(int method, int bits) {
         case 512: return 27.0;
         default: return 7.5;   // 1024
     }
+}
+
+double mp_gamma_log2(int64_t l, int prec_bits) {
+    const double lu = std::log2((double)l) - prec_bits;   // log2(l u)
+    return lu >= -1.0 ? INFINITY : lu - std::log2(1.0 - std::exp2(lu));
+}
+
+double via_mp_log2_bound(int terms, int prec_bits, int64_t l) {
+    const double g = mp_gamma_log2(l, prec_bits);
+    if (!std::isfinite(g)) return INFINITY;
+    const double slack = std::log2(1.0 + std::exp2(-40.0));
+    return log2_sum({g, 1.0 - prec_bits, -53.0 * terms}) + slack;
+}
+
+// The two conversion passes of mpgemm_{dd,qd}_via_mp, per element as
+// measured on GB300 (DD 128-bit: 10 / 12 ps in / out; QD 256-bit: 35 / 43).
+double via_mp_convert_ms(int terms, int64_t m, int64_t l, int64_t n) {
+    const double tin = terms == 2 ? 10e-12 : 35e-12, tout = terms == 2 ? 12e-12 : 43e-12;
+    return 1e3 * (((double)m * l + (double)l * n) * tin + (double)m * n * tout) + 0.01;
 }
 
 double split_ms(int digit_bits, int S, int64_t m, int64_t l, int64_t n, int terms = 2) {
@@ -147,10 +172,14 @@ double mpgemm_precision_log2_bound(int method, int prec_bits, int num_slices, in
     switch (method) {
         case MPGEMM_SEL_DD: return 2.0 + ll - 104.0;
         case MPGEMM_SEL_QD: return 2.0 + ll - 208.0;
-        case MPGEMM_SEL_MP: {
-            if (prec_bits <= 0) return NAN;
-            const double lu = ll - prec_bits;   // log2(l u)
-            return lu >= -1.0 ? INFINITY : lu - std::log2(1.0 - std::exp2(lu));
+        case MPGEMM_SEL_MP:
+            return prec_bits <= 0 ? NAN : mp_gamma_log2(l, prec_bits);
+        case MPGEMM_SEL_DD_VIA_MP:
+        case MPGEMM_SEL_QD_VIA_MP: {
+            const int terms = method == MPGEMM_SEL_DD_VIA_MP ? 2 : 4;
+            const int bits = prec_bits > 0 ? prec_bits : (terms == 2 ? 128 : 256);
+            if (bits % 32 || bits < 64 || bits > 512) return NAN;
+            return via_mp_log2_bound(terms, bits, l);
         }
         case MPGEMM_SEL_OZAKI_INT8:
             return (num_slices >= 1 && num_slices <= 18) ? split_log2_bound(7, num_slices, spread) : NAN;
@@ -240,6 +269,14 @@ int mpgemm_select_precision(double log2_target, int64_t m, int64_t l, int64_t n,
     for (int method : {MPGEMM_SEL_DD, MPGEMM_SEL_QD}) {
         const double b = mpgemm_precision_log2_bound(method, 0, 0, l, 0);
         if (b <= log2_target) cs.push_back({method, 0, 0, b, timed(method, 0)});
+    }
+    // DD / QD on the integer pipe (DD / QD operands and result)
+    for (int terms : {2, 4}) {
+        const int method = terms == 2 ? MPGEMM_SEL_DD_VIA_MP : MPGEMM_SEL_QD_VIA_MP;
+        const int bits = terms == 2 ? 128 : 256;
+        const double b = via_mp_log2_bound(terms, bits, l);
+        if (b <= log2_target)
+            cs.push_back({method, bits, 0, b, timed(MPGEMM_SEL_MP, bits) + via_mp_convert_ms(terms, m, l, n)});
     }
     for (int bits : {128, 256, 512, 1024}) {   // the smallest multi-limb precision that meets the target
         const double b = mpgemm_precision_log2_bound(MPGEMM_SEL_MP, bits, 0, l, 0);

@@ -51,10 +51,12 @@ def test_selected_configurations_meet_target(target):
     ii, jj = sample_indices(m, n, 300, seed=-target)
     sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     for c in choices:
-        if c["method"] not in ("ozaki_e4m3", "ozaki_int8", "dd"):
+        if c["method"] not in ("ozaki_e4m3", "ozaki_int8", "dd", "dd_via_mp"):
             continue
         if c["method"] == "dd":
             C = host(mpg.gemm_dd(Ad, Bd, algo="block"))
+        elif c["method"] == "dd_via_mp":
+            C = host(mpg.gemm_via_mp(Ad, Bd, c["prec_bits"], algo="block", n_min=16))
         else:
             Cd = torch.empty((2, m, n), dtype=torch.float64, device="cuda")
             kind = 1 if c["method"] == "ozaki_e4m3" else 0

@@ -4,7 +4,8 @@ model loaded: measured static rates rank the candidates).
 The a-priori bounds reproduce the library's defaults from first principles:
 at a 2^-100 target with entries within one binade of their row / column
 maxima, FP8 digits need S = 22 and int8 digits S = 16; DD's bound is
-4 l 2^-104, QD's 4 l 2^-208, p-bit multi-limb gamma_l = l 2^-p / (1 - l 2^-p)."""
+4 l 2^-104, QD's 4 l 2^-208, p-bit multi-limb gamma_l = l 2^-p / (1 - l 2^-p);
+DD / QD on the integer pipe gamma_l(p) + 2^(1-p) + 2^(-53 T)."""
 
 import math
 
@@ -42,6 +43,26 @@ def test_split_bounds_fall_with_slices_and_rise_with_spread(built, method, bits)
         prev = b
     assert built.precision_log2_bound(method, 4096, num_slices=12, spread=5) > \
         built.precision_log2_bound(method, 4096, num_slices=12, spread=0) + 9
+
+
+def test_integer_pipe_bounds(built):
+    def via(l, p, T):
+        lu = math.log2(l) - p
+        g = 2.0 ** (lu - math.log2(1 - 2.0 ** lu))
+        return math.log2((g + 2.0 ** (1 - p) + 2.0 ** (-53 * T)) * (1 + 2.0 ** -40))
+    for l in (16, 1024, 1 << 20):
+        assert built.precision_log2_bound("dd_via_mp", l) == pytest.approx(via(l, 128, 2), abs=1e-9)
+        assert built.precision_log2_bound("qd_via_mp", l) == pytest.approx(via(l, 256, 4), abs=1e-9)
+        assert built.precision_log2_bound("dd_via_mp", l, prec_bits=256) == pytest.approx(via(l, 256, 2), abs=1e-9)
+    # the final expansion dominates: about 2^-106 (DD) and 2^-212 (QD), for any l
+    assert -106.01 < built.precision_log2_bound("dd_via_mp", 4096) < -105.9
+    assert -212.1 < built.precision_log2_bound("qd_via_mp", 4096) < -211.5
+    assert math.isnan(built.precision_log2_bound("dd_via_mp", 64, prec_bits=96 + 1))
+    # a DD target the FP64 kernels miss (4 l 2^-104 = 2^-92 at l = 1024) is met on the integer pipe
+    sel = {c["method"]: c for c in built.select_precision(-104, 1024, 1024, 1024)}
+    assert "dd" not in sel and sel["dd_via_mp"]["prec_bits"] == 128
+    sel = {c["method"]: c for c in built.select_precision(-205, 1024, 1024, 1024)}
+    assert "qd" not in sel and sel["qd_via_mp"]["prec_bits"] == 256
 
 
 def test_defaults_reproduced(built):
