@@ -62,6 +62,21 @@ def test_qd_via_mp_bit_exact(algo, depth, bits):
     assert mpg.stream_status() == 0
 
 
+def test_dd_via_mp_full_size_rows_bit_exact():
+    # the bench's DD 2048^3 inputs through the block algorithm: three full
+    # rows of C bit-identical to the oracle's conversion + multi-limb rows
+    n, bits = 2048, 128
+    A = I.dd_random(n, n, I.seed_for(1, 0), exp_spread=20)
+    B = I.dd_random(n, n, I.seed_for(1, 1), exp_spread=20)
+    C = mpg.gemm_via_mp(dev(A), dev(B), bits, algo="block", n_min=16).cpu().numpy()
+    Am, Bm = oracle.terms_to_mp(A, bits), oracle.terms_to_mp(B, bits)
+    for r0 in (0, 1023, n - 1):
+        Cm = oracle.mp_gemm(Am, Bm, prec_bits=bits, algo="block", n_min=16, rows=(r0, r0 + 1))
+        Co = oracle.mp_to_terms(np.ascontiguousarray(Cm[:, r0:r0 + 1]), bits, 2)
+        assert np.array_equal(C[:, r0:r0 + 1].view(np.uint64), Co.view(np.uint64)), r0
+    assert mpg.stream_status() == 0
+
+
 def _within_limb_bound(A, B, C, ii, jj, p, last):
     """|c - c_exact| <= 2^-last |c| (the final rounding to T doubles) +
     (2 l + 4) 2^-p sum|a||b| (p-bit conversions and arithmetic)."""
