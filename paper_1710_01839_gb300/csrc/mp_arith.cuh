@@ -99,6 +99,29 @@ __device__ __forceinline__ void shl(uint32_t (&v)[N], int s) {
     v[0] = v[0] << r;
 }
 
+// S = X + Y over N limbs with one carry chain (add.cc / addc); the carry out
+// of limb N - 1 is dropped (callers keep a zero top limb).
+template <int N>
+__device__ __forceinline__ void add_limbs(const uint32_t (&X)[N], const uint32_t (&Y)[N], uint32_t (&S)[N]) {
+    asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(S[0]) : "r"(X[0]), "r"(Y[0]));
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(S[i]) : "r"(X[i]), "r"(Y[i]));
+    asm volatile("addc.u32 %0, %1, %2;" : "=r"(S[N - 1]) : "r"(X[N - 1]), "r"(Y[N - 1]));
+}
+
+// S = X - Y - b (b in {0, 1}) as X + ~Y + (1 - b) on one carry chain;
+// returns 1 when the difference is negative (no carry out).
+template <int N>
+__device__ __forceinline__ uint32_t sub_limbs(const uint32_t (&X)[N], const uint32_t (&Y)[N], uint32_t b,
+                                              uint32_t (&S)[N]) {
+    uint32_t dummy, cout;
+    asm volatile("add.cc.u32 %0, %1, 0xFFFFFFFF;" : "=r"(dummy) : "r"(1u - b));   // carry = 1 - b
+#pragma unroll
+    for (int i = 0; i < N; i++) asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(S[i]) : "r"(X[i]), "r"(~Y[i]));
+    asm volatile("addc.u32 %0, 0, 0;" : "=r"(cout));
+    return 1u - cout;
+}
+
 // Round-to-nearest-even increment of a W-limb mantissa; returns the carry out.
 // The carry leaves limb 0 only when limb 0 was all ones (rare), so the walk
 // over the upper limbs sits behind a branch.
@@ -345,23 +368,11 @@ MP_UNROLL
     uint32_t S[N];
     unsigned sign = sx;
     if (sx == sy) {
-        uint32_t c = 0u;
-MP_UNROLL
-        for (int i = 0; i < N; i++) {
-            uint64_t t = (uint64_t)X[i] + Y[i] + c;
-            S[i] = (uint32_t)t;
-            c = (uint32_t)(t >> 32);
-        }
+        add_limbs<N>(X, Y, S);
     } else {
         // S = X - Y - stk; the dropped part of y then leaves a positive
         // remainder below S's last bit, kept as sticky.
-        uint32_t br = stk ? 1u : 0u;
-MP_UNROLL
-        for (int i = 0; i < N; i++) {
-            uint64_t t = (uint64_t)X[i] - Y[i] - br;
-            S[i] = (uint32_t)t;
-            br = (uint32_t)(t >> 63);
-        }
+        const uint32_t br = sub_limbs<N>(X, Y, stk ? 1u : 0u, S);
         if (br) {   // only when d == 0 and My > Mx (exact): negate
             uint32_t c = 1u;
 MP_UNROLL

@@ -139,3 +139,25 @@ def test_via_mp_rejects_bad_precision_and_flags_nonfinite():
     mpg.gemm_via_mp(A2, B, 128)
     assert mpg.stream_status() == -1     # MPGEMM_EINVAL: an input was not finite
     assert mpg.stream_status() == 0      # read and cleared
+
+
+def test_via_mp_results_outside_the_double_range_are_flagged():
+    # 2^600 x 2^600 overflows a double; 2^-500 (1 + 2^-50) squared leaves a
+    # second DD term near 2^-1100, below the normal range: both are written
+    # as zero and reported as MPGEMM_EOVERFLOW, without a fault
+    big = np.zeros((2, 1, 1))
+    big[0] = 2.0 ** 600
+    C = mpg.gemm_via_mp(dev(big), dev(big), 128).cpu().numpy()
+    assert not C.any()
+    assert mpg.stream_status() == -4
+    small = np.zeros((2, 1, 1))
+    small[0] = 2.0 ** -500 * (1 + 2.0 ** -50)
+    C = mpg.gemm_via_mp(dev(small), dev(small), 128).cpu().numpy()
+    assert C[0, 0, 0] == 2.0 ** -1000 * (1 + 2.0 ** -49) and C[1, 0, 0] == 0.0
+    assert mpg.stream_status() == -4
+    # in range again: no flag
+    ok = np.zeros((2, 1, 1))
+    ok[0] = 3.0
+    C = mpg.gemm_via_mp(dev(ok), dev(ok), 128).cpu().numpy()
+    assert C[0, 0, 0] == 9.0 and C[1, 0, 0] == 0.0
+    assert mpg.stream_status() == 0
