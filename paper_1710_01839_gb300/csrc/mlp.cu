@@ -417,7 +417,9 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
         int64_t m = (int64_t)std::lround(std::exp(U(rng))), l = (int64_t)std::lround(std::exp(U(rng))),
                 n = (int64_t)std::lround(std::exp(U(rng)));
         int kind = (int)(rng() % 3);
-        int prec = kind == MPGEMM_KIND_MP ? 256 : 0;
+        // multi-limb: 256 bits (the batched workload's width) or 128 bits
+        // (the width of the integer-pipe DD GEMM)
+        int prec = kind == MPGEMM_KIND_MP ? (rng() % 2 ? 256 : 128) : 0;
         if (rng() % 3 == 0) {   // a third of the shapes even enough for Strassen
             m &= ~7LL;
             l &= ~7LL;
@@ -429,7 +431,7 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
         std::vector<Cand> cs = candidates(kind, m, l, n);
         Cand c = cs[rng() % cs.size()];
         // operands
-        int planes = kind == MPGEMM_KIND_DD ? 2 : kind == MPGEMM_KIND_QD ? 4 : 10;
+        int planes = kind == MPGEMM_KIND_DD ? 2 : kind == MPGEMM_KIND_QD ? 4 : 2 + prec / 32;
         size_t ea = (size_t)(m * l) * planes, eb = (size_t)(l * n) * planes;
         if (kind != MPGEMM_KIND_MP) {
             k_fill_random<<<ceil_div((int64_t)ea, 256), 256, 0, s>>>((double*)A, ea, seed + 2 * i, 0, planes);
@@ -440,8 +442,9 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
             // exponent plane 0, flags plane 0, top limb with its high bit set
             MPG_CUDA(cudaMemsetAsync(A, 0, sizeof(uint32_t) * 2 * (size_t)(m * l), s));
             MPG_CUDA(cudaMemsetAsync(B, 0, sizeof(uint32_t) * 2 * (size_t)(l * n), s));
-            fill_u32((uint32_t*)A + 9 * (size_t)(m * l), (size_t)(m * l), 0x80000001u, s);
-            fill_u32((uint32_t*)B + 9 * (size_t)(l * n), (size_t)(l * n), 0x80000001u, s);
+            const size_t top = (size_t)(1 + prec / 32);   // plane of the top limb
+            fill_u32((uint32_t*)A + top * (size_t)(m * l), (size_t)(m * l), 0x80000001u, s);
+            fill_u32((uint32_t*)B + top * (size_t)(l * n), (size_t)(l * n), 0x80000001u, s);
         }
         auto run = [&]() -> int {
             if (kind == MPGEMM_KIND_DD)

@@ -4,7 +4,7 @@ to paper_1710_01839_gb300/data/cost_model_gb300.bin (or --out).
     python -m paper_1710_01839_gb300.train_cost_model [--count 5000] [--epochs 200]
 
 Steps: mpgemm_cost_collect times `count` random configurations (shapes
-log-uniform in [16, max_dim], DD / QD / 256-bit multi-limb, every valid
+log-uniform in [16, max_dim], DD / QD / 128- and 256-bit multi-limb, every valid
 algorithm / tile / Strassen depth); 90 % train the model (mpgemm_cost_train),
 10 % measure its held-out error.  Then, for a set of random shapes, the
 configuration the model picks is timed against every candidate timed
@@ -51,7 +51,7 @@ def regret_study(shapes_seed=99, count=12, max_dim=1024):
     rng = np.random.default_rng(shapes_seed)
     rows = []
     for i in range(count):
-        fmt = ["dd", "qd", "mp"][i % 3]
+        fmt, bits = [("dd", 0), ("qd", 0), ("mp", 256), ("mp", 128)][i % 4]
         dims = [int(x) // 8 * 8 for x in np.exp(rng.uniform(np.log(64), np.log(max_dim), 3))]
         m, l, n = (max(d, 16) for d in dims)
         if fmt == "dd":
@@ -59,7 +59,7 @@ def regret_study(shapes_seed=99, count=12, max_dim=1024):
         elif fmt == "qd":
             A, B = I.qd_random(m, l, i), I.qd_random(l, n, i + 1)
         else:
-            A, B = I.mp_random(m, l, 8, i), I.mp_random(l, n, 8, i + 1)
+            A, B = I.mp_random(m, l, bits // 32, i), I.mp_random(l, n, bits // 32, i + 1)
         Ad = torch.from_numpy(A.view(np.int32) if fmt == "mp" else A).cuda()
         Bd = torch.from_numpy(B.view(np.int32) if fmt == "mp" else B).cuda()
 
@@ -68,19 +68,19 @@ def regret_study(shapes_seed=99, count=12, max_dim=1024):
                 return lambda: mpg.gemm_dd(Ad, Bd, algo=algo, n_min=tile, depth=depth)
             if fmt == "qd":
                 return lambda: mpg.gemm_qd(Ad, Bd, algo=algo, n_min=tile, depth=depth)
-            return lambda: mpg.gemm_mp(Ad, Bd, 256, algo=algo, n_min=tile, depth=depth)
+            return lambda: mpg.gemm_mp(Ad, Bd, bits, algo=algo, n_min=tile, depth=depth)
 
         tmax = {"dd": 64, "qd": 32, "mp": 16}[fmt]
         cands = [("simple", 16, 0)] + [("block", t, 0) for t in (16, 32, 64) if t <= tmax]
         for d in (1, 2, 3):
             if all(x % (1 << d) == 0 and (x >> d) >= 16 for x in (m, l, n)):
                 cands += [("strassen", t, d) for t in (16, 32, 64) if t <= tmax]
-        F = np.array([cm.features(fmt, m, l, n, a, t, d, prec_bits=256 if fmt == "mp" else 0) for a, t, d in cands])
+        F = np.array([cm.features(fmt, m, l, n, a, t, d, prec_bits=bits) for a, t, d in cands])
         pred = cm.predict(F)
         pick = int(np.argmin(pred))
         meas = [_time(run(*c)) for c in cands]
         best = int(np.argmin(meas))
-        rows.append({"fmt": fmt, "m": m, "l": l, "n": n, "model_pick": cands[pick], "best": cands[best],
+        rows.append({"fmt": fmt if fmt != "mp" else f"mp{bits}", "m": m, "l": l, "n": n, "model_pick": cands[pick], "best": cands[best],
                      "t_model_ms": meas[pick], "t_best_ms": meas[best], "regret": meas[pick] / meas[best] - 1,
                      "pred_ms_of_pick": float(pred[pick])})
     reg = [r["regret"] for r in rows]
