@@ -327,6 +327,49 @@ def via_mp_extra(args, stream, fp64_dd_gflops):
     return out
 
 
+def paper_matrices_extra(args, stream):
+    """The paper's own workload (Section 4): A = [sqrt(5)(i+j-1)], B =
+    [sqrt(3)(n-i)] at n = 1024 in DD and QD, each timed with the Section 3
+    tuner's choice, and the largest relative error of sampled entries
+    against the closed form c_ij = sqrt(15) n(n-1)(3i+n-2)/6 (sqrt(15) to
+    300 bits)."""
+    import math
+    from fractions import Fraction
+    import torch
+    import paper_1710_01839_gb300 as mpg
+    from paper_1710_01839_gb300 import inputs as I, tuner
+    n = 1024
+    r15 = Fraction(math.isqrt(15 << 600), 1 << 300)
+    out = {"workload": f"Section 4 matrices A = sqrt(5)(i+j-1), B = sqrt(3)(n-i), n = {n}"}
+    for fmt in ("dd", "qd"):
+        A, B = I.paper_matrices(n, fmt)
+        Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        Cd = torch.empty_like(Ad)
+        torch.cuda.synchronize()
+        choice, _ = tuner.tune(fmt, Ad, Bd, Cd, flags=tuner.QUICK, stream=stream)
+        f = mpg.gemm_dd if fmt == "dd" else mpg.gemm_qd
+        call = lambda: f(Ad, Bd, Cd, algo=choice["algo"], n_min=choice["n_min"], depth=choice["depth"], stream=stream)
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        C = Cd.cpu().numpy()
+        worst = 0.0
+        for i in (1, 2, n // 2, n):
+            truth = r15 * I.paper_closed_form(n, i)
+            for j in (0, n // 3, n - 1):
+                got = sum((Fraction(float(C[t, i - 1, j])) for t in range(C.shape[0])), Fraction(0))
+                worst = max(worst, float(abs(got - truth) / truth))
+        out[fmt] = {"choice": choice, "gflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "ms": ms,
+                    "max_rel_err_vs_closed_form": worst}
+    return out
+
+
 def batched_extra(args, stream):
     """512 GEMMs, m, l, n log-uniform in [16, 1024], format uniform over
     {DD, QD, 256-bit}: one persistent graph-replayed launch with tiles from
@@ -703,11 +746,12 @@ def main():
                "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(Ch.numel() * Ch.element_size()),
                "ms_per_step": e_ms / args.steps}
 
-    extras = bextra = qextra = vextra = None
+    extras = bextra = qextra = vextra = pextra = None
     if not args.no_extras and fmt == "dd":
         extras = split_precision_extra(args, stream)
         qextra = qd_split_extra(args, stream)
         vextra = via_mp_extra(args, stream, value / world)
+        pextra = paper_matrices_extra(args, stream)
         if qextra is not None and "qd" in vextra:
             vextra["qd"]["speedup_vs_fp64_pipe"] = vextra["qd"]["gflops"] / max(qextra["plain_qd_block_gflops"],
                                                                                 qextra["plain_qd_strassen3_gflops"])
@@ -741,6 +785,8 @@ def main():
         line["qd_split_precision"] = qextra
     if vextra is not None:
         line["integer_pipe"] = vextra
+    if pextra is not None:
+        line["paper_matrices"] = pextra
     if bextra is not None:
         line["batched"] = bextra
     print(json.dumps(line), flush=True)
