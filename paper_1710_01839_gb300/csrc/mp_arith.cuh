@@ -322,7 +322,7 @@ __device__ __forceinline__ void mp_mul(const MPV<W>& x, const MPV<W>& y, MPV<W>&
 template <int W>
 __device__ __forceinline__ void mp_add(const MPV<W>& a, const MPV<W>& b, MPV<W>& r, unsigned& status) {
     constexpr int p = 32 * W;
-    constexpr int N = W + 3;   // [guard, guard, M (W limbs), carry]
+    constexpr int N = W + 2;   // [guard, M (W limbs), carry]
     if (a.f & 2u) {
         if (b.f & 2u) {
             mp_set_zero(r, a.f & b.f & 1u);
@@ -344,18 +344,18 @@ __device__ __forceinline__ void mp_add(const MPV<W>& a, const MPV<W>& b, MPV<W>&
         return;
     }
     uint32_t X[N], Y[N];
-    X[0] = X[1] = 0u;
-    Y[0] = Y[1] = 0u;
+    X[0] = 0u;
+    Y[0] = 0u;
 MP_UNROLL
     for (int i = 0; i < W; i++) {
-        X[i + 2] = sw ? b.m[i] : a.m[i];
-        Y[i + 2] = sw ? a.m[i] : b.m[i];
+        X[i + 1] = sw ? b.m[i] : a.m[i];
+        Y[i + 1] = sw ? a.m[i] : b.m[i];
     }
     X[N - 1] = 0u;
     Y[N - 1] = 0u;
     uint32_t sticky = 0u;
     if (d < 32) {
-        // the common GEMM case: no limb moves, and the two guard limbs keep
+        // the common GEMM case: no limb moves, and the guard limb keeps
         // every shifted-out bit (no sticky)
         const int r = (int)d;
 MP_UNROLL
@@ -399,8 +399,11 @@ MP_UNROLL
         S[N - 1] >>= 1;
         e = (long long)ex + 1;
     } else {
-        // leading bit to position p + 63 (top of limb N-2); a shift of 0 or 1
-        // (no cancellation of the leading bits) is the common case
+        // leading bit to the top of limb N-2; a shift of 0 or 1 (no
+        // cancellation of the leading bits) is the common case, and a larger
+        // one happens only for d <= 1, where the sum is exact (the guard
+        // limb then holds every bit, and with d >= 2 the shift is at most 1
+        // with at least two guard bits below the round bit)
         int s;
         if (S[N - 2] >> 30) {
             s = (S[N - 2] >> 31) ? 0 : 1;
@@ -414,7 +417,7 @@ MP_UNROLL
 MP_UNROLL
             for (int i = 0; i < N - 1; i++)
                 if (S[i]) L = 32 * i + 32 - __clz(S[i]);
-            s = p + 64 - L;
+            s = 32 * (N - 1) - L;
             shl<N>(S, s);
         }
         e = (long long)ex - s;
@@ -422,9 +425,9 @@ MP_UNROLL
     }
     uint32_t M[W];
 MP_UNROLL
-    for (int i = 0; i < W; i++) M[i] = S[i + 2];
-    uint32_t rb = S[1] >> 31;
-    uint32_t st = (S[1] << 1) | S[0] | sticky | (stk ? 1u : 0u);
+    for (int i = 0; i < W; i++) M[i] = S[i + 1];
+    uint32_t rb = S[0] >> 31;
+    uint32_t st = (S[0] << 1) | sticky | (stk ? 1u : 0u);
     bool inc = rb && (st != 0u || (M[0] & 1u));
     if (round_up(M, inc)) {
         M[W - 1] = 0x80000000u;
