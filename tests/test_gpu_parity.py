@@ -423,3 +423,25 @@ def test_mp256_bench_configuration_sampled():
         i, j = int(rng.integers(0, n)), int(rng.integers(0, n))
         ex = sum((fa(A, i, k) * fa(B, k, j) for k in range(n)), Fraction(0))
         assert abs(mp_words_to_fraction(C[:, i, j], w) - ex) <= tol
+
+
+@pytest.mark.parametrize("w", [1, 4, 8, 64])
+@pytest.mark.parametrize("algo", ["simple", "block"])
+def test_mp_exponent_range_is_flagged(w, algo):
+    # exponents are int32: a product past 2^31 - 1 (or below -2^31), and a
+    # sum whose rounding carries the exponent of 2^31 - 1 one further, set
+    # MPGEMM_EOVERFLOW; in-range neighbours of the same calls do not
+    p = 32 * w
+    top = 2 ** 31 - 1
+    one = (0, 1, 1 << (p - 1))
+    cases = {
+        "mul_over": ([[(0, top - 5, 1 << (p - 1))]], [[(0, 10, 1 << (p - 1))]]),
+        "mul_under": ([[(1, -2 ** 31 + 5, 1 << (p - 1))]], [[(0, -10, 1 << (p - 1))]]),
+        "add_carry": ([[(0, top, (1 << p) - 1), (0, top - p, (1 << (p - 1)) + 1)]], [[one], [one]]),
+        "in_range": ([[(0, top - 20, 1 << (p - 1))]], [[(0, 10, 1 << (p - 1))]]),
+    }
+    for name, (a, b) in cases.items():
+        A, B = _mp_planes(a, w), _mp_planes(b, w)
+        mpg.gemm_mp(dev(A), dev(B), p, algo=algo, n_min=16)
+        want = 0 if name == "in_range" else -4
+        assert mpg.stream_status() == want, name
