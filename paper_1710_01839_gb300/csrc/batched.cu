@@ -44,11 +44,16 @@ struct Work {
     int desc, tm, tn, pad;
 };
 
+// MP_ONLY: the instantiation for plans whose tiles are all multi-limb (its
+// registers and shared memory are those of the multi-limb tiles alone, so
+// more CTAs fit per SM); a DD / QD tile reaching it is flagged and skipped.
+template <bool MP_ONLY>
 __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ descs, const Work* __restrict__ work,
                                                  int nwork, unsigned* counter, unsigned* status) {
-    constexpr int SMD = ddqd_tile_doubles<DDFmt, 32, 16>() > ddqd_tile_doubles<QDFmt, 32, 8>()
-                            ? ddqd_tile_doubles<DDFmt, 32, 16>()
-                            : ddqd_tile_doubles<QDFmt, 32, 8>();
+    constexpr int SMD_DDQD = ddqd_tile_doubles<DDFmt, 32, 16>() > ddqd_tile_doubles<QDFmt, 32, 8>()
+                                 ? ddqd_tile_doubles<DDFmt, 32, 16>()
+                                 : ddqd_tile_doubles<QDFmt, 32, 8>();
+    constexpr int SMD = MP_ONLY ? (mp_tile_words<8, 8>() + 1) / 2 : SMD_DDQD;
     static_assert(SMD * 8 >= mp_tile_words<8, 8>() * 4, "the 256-bit tile's staging fits too");
     __shared__ __align__(16) double sm[SMD];   // the largest tile's staging
     __shared__ int s_item;
@@ -70,7 +75,7 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
                 mp_block_tile<8, 8>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
             else
                 mp_block_tile<4, 8>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
-        } else {
+        } else if constexpr (!MP_ONLY) {
             View<const double> a = planes_view((const double*)d.A, d.m, d.l);
             View<const double> b = planes_view((const double*)d.B, d.l, d.n);
             View<double> c = planes_view((double*)d.C, d.m, d.n);
@@ -80,6 +85,8 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
                 case T_QD16: ddqd_block_tile<QDFmt, 16, 1, 16>(d.m, d.l, d.n, a, b, c, 0, i0, j0, sm); break;
                 default: ddqd_block_tile<QDFmt, 32, 2, 8>(d.m, d.l, d.n, a, b, c, 0, i0, j0, sm); break;
             }
+        } else {
+            st |= DEV_BAD_DESC;
         }
     }
     if (st) atomicOr(status, st);
@@ -162,6 +169,7 @@ struct ConvPass {
 
 struct mpgemm_plan_s {
     int count = 0, nwork = 0, grid = 0, device = 0;
+    bool mp_only = false;   // every tile multi-limb: the k_batched<true> instantiation
     // conversion passes of the integer-pipe descriptors: [0] DD in, [1] QD
     // in, [2] DD out, [3] QD out; the multi-limb copies live in d_limbs
     mpg::ConvPass conv[4];
@@ -310,7 +318,12 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
     if (!rc && (e = cudaGetDevice(&P->device)) != cudaSuccess) fail(e);
     int sms = 0, occ = 0;
     if (!rc && (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device)) != cudaSuccess) fail(e);
-    if (!rc && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, 256, 0)) != cudaSuccess) fail(e);
+    P->mp_only = count > 0;
+    for (int i = 0; i < count; i++) P->mp_only &= dd[i].tk == T_MP128 || dd[i].tk == T_MP256;
+    if (!rc && (e = P->mp_only ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<true>, 256, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<false>, 256, 0)) !=
+                   cudaSuccess)
+        fail(e);
     P->grid = std::max(1, sms * std::max(occ, 1));
     if (!rc && count && (e = cudaMalloc(&P->d_descs, sizeof(DevDesc) * count)) != cudaSuccess) fail(e);
     if (!rc && P->nwork && (e = cudaMalloc(&P->d_work, sizeof(Work) * P->nwork)) != cudaSuccess) fail(e);
@@ -350,11 +363,15 @@ static int plan_launches(mpgemm_plan P, cudaStream_t s, unsigned* status, bool p
     MPG_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(unsigned), s));
     for (int k = 0; k < 2; k++)
         if (int rc = launch_conv(P, k, s, status)) return rc;
+    auto launch = [&]() {
+        if (P->mp_only) k_batched<true><<<P->grid, 256, 0, s>>>(P->d_descs, P->d_work, P->nwork, P->d_counter, status);
+        else k_batched<false><<<P->grid, 256, 0, s>>>(P->d_descs, P->d_work, P->nwork, P->d_counter, status);
+    };
     if (prof) {
         ProfScope ps(s);
-        k_batched<<<P->grid, 256, 0, s>>>(P->d_descs, P->d_work, P->nwork, P->d_counter, status);
+        launch();
     } else {
-        k_batched<<<P->grid, 256, 0, s>>>(P->d_descs, P->d_work, P->nwork, P->d_counter, status);
+        launch();
     }
     if (int rc = check_launch()) return rc;
     for (int k = 2; k < 4; k++)
