@@ -167,3 +167,27 @@ def test_plan_rejects_bad_engine():
     d = batched.make_descs([("dd", D, D, D)])
     d[0].engine = 2
     assert mpg.lib().mpgemm_batched_plan(d, 1, ctypes.byref(h)) == -1
+
+
+def test_mixed_engines_in_one_plan():
+    # engine 0 and engine 1 descriptors of the same formats in one plan: the
+    # full persistent kernel runs FP64 DD / QD tiles beside 128- and 256-bit
+    # ones; each result equals its own engine's sequential launch
+    from paper_1710_01839_gb300 import batched
+    shapes = [(37, 29, 23, "dd"), (40, 33, 17, "qd"), (25, 31, 19, "dd"), (18, 26, 30, "qd"), (20, 20, 20, "mp256")]
+    probs, _ = _problems(shapes, 500)
+    descs = batched.make_descs(probs, [32] * len(probs))
+    for i, d in enumerate(descs):
+        if i in (2, 3):
+            d.engine = 1
+    batched.sequential(descs)
+    ref = _snapshot(probs)
+    for _, _, _, C in probs:
+        C.zero_()
+    plan = batched.Plan(descs)
+    assert plan.info()["tiles"] == [32, 32, 16, 16, 16]
+    plan.run_graph()
+    for r, g in zip(ref, _snapshot(probs)):
+        assert np.array_equal(r.view(np.uint8), g.view(np.uint8))
+    plan.close()
+    assert mpg.stream_status() == 0

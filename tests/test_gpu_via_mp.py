@@ -161,3 +161,35 @@ def test_via_mp_results_outside_the_double_range_are_flagged():
     C = mpg.gemm_via_mp(dev(ok), dev(ok), 128).cpu().numpy()
     assert C[0, 0, 0] == 9.0 and C[1, 0, 0] == 0.0
     assert mpg.stream_status() == 0
+
+
+def test_via_mp_caller_workspace_and_partition():
+    # the conversions' copies and Strassen's workspace from one caller
+    # buffer of exactly mpgemm_via_mp_workspace_size bytes (too small:
+    # MPGEMM_ENOMEM before any launch), and the same call on an SM partition
+    import torch
+    m, l, n, bits, depth = 72, 88, 56, 128, 2
+    A = I.dd_random(m, l, 730, exp_spread=20)
+    B = I.dd_random(l, n, 731, exp_spread=20)
+    Co = oracle.gemm_via_mp(A, B, bits, algo="strassen", n_min=16, depth=depth)
+    L = mpg.lib()
+    need = L.mpgemm_via_mp_workspace_size(bits, m, l, n, 2, depth)
+    assert need >= 4 * (2 + bits // 32) * (m * l + l * n + m * n)
+    assert L.mpgemm_via_mp_workspace_size(96, m, l, n, 2, depth) == 0
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    try:
+        mpg.set_workspace(ws)
+        C = mpg.gemm_via_mp(dev(A), dev(B), bits, algo="strassen", n_min=16, depth=depth).cpu().numpy()
+        assert np.array_equal(C.view(np.uint64), Co.view(np.uint64))
+        mpg.set_workspace(ws[: need - 256])
+        with pytest.raises(mpg.MpgemmError) as e:
+            mpg.gemm_via_mp(dev(A), dev(B), bits, algo="strassen", n_min=16, depth=depth)
+        assert e.value.status == -6
+    finally:
+        mpg.set_workspace(None)
+    with mpg.Partition(24) as part:
+        Ad, Bd = dev(A), dev(B)
+        torch.cuda.synchronize()
+        C = mpg.gemm_via_mp(Ad, Bd, bits, algo="strassen", n_min=16, depth=depth, stream=part.stream)
+        assert mpg.stream_status(part.stream) == 0
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), Co.view(np.uint64))
