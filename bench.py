@@ -40,11 +40,12 @@ if ROOT not in sys.path:
 
 METRIC = "DD/QD GEMM GFLOP/s (2mnl/t) & roofline %; Ozaki vs plain DD at ≤2^-100 rel err"
 # FP64-pipe operations per multiply-accumulate of the kernels (see ddqd.cuh;
-# TwoSum costs 3 FP64 operations there, its operand ordering runs on the
-# integer pipe):
-#   DD: DMUL + 3 DFMA + TwoSum (3) + 2 DADD = 9, plus a 3-op TwoSum every 8 steps
-#   QD: 72 per step plus a 15-op renormalisation every 4 steps
-FP64_OPS_PER_MAC = {"dd": 9.0 + 3.0 / 8.0, "qd": 72.0 + 15.0 / 4.0}
+# TwoSum's operand ordering runs on the integer pipe, and so does its error
+# term except in the QD MAC's nine order-2 TwoSums: 1 FP64 operation per
+# TwoSum, 3 for those nine):
+#   DD: DMUL + 3 DFMA + TwoSum (1) + 2 DADD = 7, plus a 1-op TwoSum every 8 steps
+#   QD: 62 per step plus a 5-op renormalisation every 4 steps
+FP64_OPS_PER_MAC = {"dd": 7.0 + 1.0 / 8.0, "qd": 62.0 + 5.0 / 4.0}
 # FP64 pipe: 2 operations / clock / SM (measured 1.91 DFMA/clk/SM at 2.07 GHz by
 # a dependent-chain-free DFMA loop) x 152 SMs x 2070 MHz maximum SM clock.
 FP64_PEAK_GOPS = 2 * 152 * 2.070

@@ -400,6 +400,13 @@ int mpgemm_stream_status(void* stream);
    MPGEMM_ETIMEOUT is the expected result (the status word is cleared and
    the context stays usable).  MPGEMM_EINVAL for a limit out of range. */
 int mpgemm_selftest_wait_timeout(int limit_ms, void* stream);
+/* Self-test of the DD / QD kernels' TwoSum: for i < count, out[i] =
+   RN(a[i] + b[i]), out[count + i] = its rounding error as the kernels
+   compute it (the integer-pipe form) and out[2 count + i] = the same error
+   by the FP64 formula y - (s - x).  The two error planes are equal bit for
+   bit for every pair of doubles.  Device pointers (out: 3 count doubles);
+   asynchronous on stream; MPGEMM_EINVAL for bad arguments. */
+int mpgemm_selftest_two_sum(int64_t count, const double* a, const double* b, double* out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Precision selection from an accuracy target (the paper's outlook: choose

@@ -7,9 +7,9 @@
 //   DD:  state (s, t).  p = RN(ah bh) and its exact error e from one FMA,
 //        the two cross products accumulated into t with two more FMAs, then
 //        (s, r) = TwoSum(s, p) and t <- t + (e + r).  Every DD_RENORM steps
-//        (s, t) = TwoSum(s, t).  9 FP64 operations per step with the
-//        exponent-ordered TwoSum below (the library DD add + multiply pair
-//        costs 27).
+//        (s, t) = TwoSum(s, t).  7 FP64 operations per step with the
+//        exponent-ordered TwoSum below, whose error term runs on the integer
+//        pipe (the library DD add + multiply pair costs 27).
 //        Worst-case error after l steps: about (DD_RENORM + 3) l u^2 sum|a||b|
 //        plus O(u^2) per product, inside the required 16 l u^2 |A||B|
 //        (= 4 l 2^-104 |A||B|) for DD_RENORM = 8.
@@ -18,7 +18,9 @@
 //        every term of order <= 2 enters its level through TwoSum, its
 //        rounding error going one level down; order-3 terms are added
 //        plainly into s3 (their errors are order 4).  Every QD_RENORM steps
-//        the levels are renormalised.  Worst case about
+//        the levels are renormalised.  63.25 FP64 operations per step (the
+//        TwoSum errors of orders 0 and 1 and of the renormalisation on the
+//        integer pipe).  Worst case about
 //        (10 QD_RENORM + 10) l u^4 sum|a||b|, inside 4 l 2^-208 = 64 l u^4.
 #pragma once
 
@@ -35,13 +37,63 @@ namespace mpg {
 
 // ---------------------------------------------------------------- EFTs
 
+// The rounding error r = x + y - s of s = RN(x + y), exactly, for x whose
+// exponent field is at least y's (Dekker's Fast2Sum condition), computed on
+// the integer pipe instead of as y - (s - x) (2 FP64 operations).  With
+// normal x, y, s and e(x) - e(y) <= 54: x, y and s are integer multiples of
+// ulp(y), |r| <= ulp(s)/2 < 2^55 ulp(y), so r / ulp(y) is the 64-bit sum of
+// the three scaled mantissas taken modulo 2^64; r is representable, so its
+// double is assembled from that integer without rounding.  e(x) - e(y) > 54
+// gives s = x and r = y; s below y's binade means the sum was exact (r = +0,
+// as the FP64 formula gives).  Zero, subnormal, infinite or NaN operands and
+// a subnormal r take the FP64 formula.  Bit-identical to y - (s - x)
+// (checked on crafted and random pairs by mpgemm_selftest_two_sum).
+__device__ __forceinline__ double fast_two_sum_err(double x, double y, double s) {
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long by = (unsigned long long)__double_as_longlong(y);
+    const unsigned long long bs = (unsigned long long)__double_as_longlong(s);
+    const int Ex = (int)((bx >> 52) & 0x7ff), Ey = (int)((by >> 52) & 0x7ff), Es = (int)((bs >> 52) & 0x7ff);
+    if (Ey == 0 || Ex == 0x7ff || Es == 0 || Es == 0x7ff) return __dsub_rn(y, __dsub_rn(s, x));
+    const int dxy = Ex - Ey;
+    if (dxy > 54) return y;
+    if (Es < Ey) return 0.0;
+    constexpr unsigned long long MM = (1ull << 52) - 1ull, H = 1ull << 52;
+    unsigned long long X = ((bx & MM) | H) << dxy;          // x / ulp(y) mod 2^64
+    unsigned long long Y = (by & MM) | H;                   // y / ulp(y)
+    unsigned long long S = ((bs & MM) | H) << (Es - Ey);    // s / ulp(y) mod 2^64 (Es - Ey <= 55)
+    if (bx >> 63) X = 0ull - X;
+    if (by >> 63) Y = 0ull - Y;
+    if (bs >> 63) S = 0ull - S;
+    const long long ri = (long long)(X + Y - S);            // r / ulp(y), exact
+    if (ri == 0) return 0.0;
+    const unsigned long long m = ri < 0 ? 0ull - (unsigned long long)ri : (unsigned long long)ri;
+    const int lz = __clzll((long long)m);
+    const int F = Ey + 11 - lz;                             // exponent field of r
+    if (F <= 0) return __dsub_rn(y, __dsub_rn(s, x));
+    const unsigned long long mant = lz >= 11 ? m << (lz - 11) : m >> (11 - lz);
+    return __longlong_as_double(
+        (long long)((ri < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)F << 52) | (mant & MM)));
+}
+
 // TwoSum: s = RN(a + b), e = a + b - s exactly, for any a, b.  Computed as
 // Dekker's Fast2Sum after ordering the operands by their exponent fields,
-// compared on the integer pipe: it returns exactly what Knuth's 6-operation
-// TwoSum returns (both are error-free), with 3 FP64 operations instead of 6.
-// On GB300 the FP64 pipe (2 operations / clock / SM) is the bottleneck and
-// the issue slots for the integer compare and selects are otherwise idle.
+// compared on the integer pipe, with the error term on the integer pipe as
+// well: it returns exactly what Knuth's 6-operation TwoSum returns (both are
+// error-free), with 1 FP64 operation instead of 6.  On GB300 the FP64 pipe
+// (2 operations / clock / SM) is the bottleneck and the integer issue slots
+// are otherwise idle.
 __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+    const int ea = __double2hiint(a) & 0x7ff00000, eb = __double2hiint(b) & 0x7ff00000;
+    const bool sw = eb > ea;
+    const double x = sw ? b : a, y = sw ? a : b;
+    const double r = __dadd_rn(x, y);
+    e = fast_two_sum_err(x, y, r);
+    s = r;
+}
+
+// The FP64 form of the same: the reference for mpgemm_selftest_two_sum, and
+// the QD MAC's order-2 TwoSums (where the integer pipe is already busy).
+__device__ __forceinline__ void two_sum_fp64(double a, double b, double& s, double& e) {
     const int ea = __double2hiint(a) & 0x7ff00000, eb = __double2hiint(b) & 0x7ff00000;
     const bool sw = eb > ea;
     const double x = sw ? b : a, y = sw ? a : b;
@@ -151,23 +203,26 @@ __device__ __forceinline__ void qd_mac(QDAcc& c, const double a[4], const double
     double e10 = __fma_rn(a[1], b[0], -p);
     two_sum(c.s1, p, s, l2d);
     c.s1 = s;
-    // order 2: l2a..l2d, e01, e10, a0 b2, a1 b1, a2 b0 (into s2; errors -> s3)
+    // order 2: l2a..l2d, e01, e10, a0 b2, a1 b1, a2 b0 (into s2; errors -> s3).
+    // These nine TwoSums keep the FP64 error term: with all fourteen on the
+    // integer pipe the QD MAC becomes integer-bound (measured: QD 1024^3
+    // Strassen 99.3 ms all integer, 106.0 all FP64, 95.7 this split).
     double t3 = 0.0;
-    two_sum(c.s2, l2a, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
-    two_sum(c.s2, l2b, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
-    two_sum(c.s2, l2c, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
-    two_sum(c.s2, l2d, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
-    two_sum(c.s2, e01, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
-    two_sum(c.s2, e10, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
+    two_sum_fp64(c.s2, l2a, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
+    two_sum_fp64(c.s2, l2b, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
+    two_sum_fp64(c.s2, l2c, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
+    two_sum_fp64(c.s2, l2d, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
+    two_sum_fp64(c.s2, e01, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
+    two_sum_fp64(c.s2, e10, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
     p = __dmul_rn(a[0], b[2]);
     e = __fma_rn(a[0], b[2], -p);
-    two_sum(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
+    two_sum_fp64(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
     p = __dmul_rn(a[1], b[1]);
     e = __fma_rn(a[1], b[1], -p);
-    two_sum(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
+    two_sum_fp64(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
     p = __dmul_rn(a[2], b[0]);
     e = __fma_rn(a[2], b[0], -p);
-    two_sum(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
+    two_sum_fp64(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
     // order 3: a0 b3 + a1 b2 + a2 b1 + a3 b0, plainly
     double q = __dmul_rn(a[3], b[0]);
     q = __fma_rn(a[2], b[1], q);

@@ -99,4 +99,27 @@ int ddqd_gemm(int kind, int algo, int64_t m, int64_t l, int64_t n, int64_t batch
     return launch_block_cfg<QDFmt, 32, 2, 8>(m, l, n, batch, A, B, C, n_min, s);
 }
 
+// TwoSum with the integer-pipe error term against the FP64 formula, element
+// by element (mpgemm_selftest_two_sum).
+__global__ void k_selftest_two_sum(int64_t count, const double* a, const double* b, double* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double s, e, s2, e2;
+    two_sum(a[i], b[i], s, e);
+    two_sum_fp64(a[i], b[i], s2, e2);
+    out[i] = s;
+    out[count + i] = e;
+    out[2 * count + i] = e2;
+}
+
 }  // namespace mpg
+
+extern "C" int mpgemm_selftest_two_sum(int64_t count, const double* a, const double* b, double* out,
+                                       void* stream) {
+    if (count < 0 || (count && (!a || !b || !out))) return MPGEMM_EINVAL;
+    if (count == 0) return MPGEMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    mpg::PartitionScope pscope(s);
+    mpg::k_selftest_two_sum<<<mpg::ceil_div(count, 256), 256, 0, s>>>(count, a, b, out);
+    return mpg::check_launch();
+}

@@ -1,0 +1,86 @@
+"""The DD / QD kernels' TwoSum computes its error term on the integer pipe;
+it must equal the FP64 formula y - (s - x) bit for bit for every pair of
+doubles (mpgemm_selftest_two_sum runs both on the device).  Pairs: random
+doubles over the whole exponent range, and crafted ones (equal exponents,
+cancellation, powers of two, exponent gaps around 54, zeros of both signs,
+subnormals, infinities, NaN, overflow), plus the accumulator / product
+pairs of a DD multiply-accumulate."""
+
+import numpy as np
+import pytest
+
+from gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+mpg = pytest.importorskip("paper_1710_01839_gb300")
+
+
+def _run(a, b):
+    import ctypes
+    import torch
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = torch.empty(3 * len(a), dtype=torch.float64, device="cuda")
+    ad, bd = dev(a), dev(b)
+    rc = mpg.lib().mpgemm_selftest_two_sum(len(a), ctypes.c_void_p(ad.data_ptr()), ctypes.c_void_p(bd.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == 0
+    o = out.cpu().numpy().reshape(3, -1)
+    return o[0], o[1], o[2]
+
+
+def _bits(x):
+    return np.ascontiguousarray(x).view(np.uint64)
+
+
+def test_random_pairs_over_the_exponent_range():
+    rng = np.random.default_rng(2024)
+    n = 1 << 20
+    bits = rng.integers(0, 2**63, size=(2, n), dtype=np.uint64) | (rng.integers(0, 2, size=(2, n), dtype=np.uint64) << np.uint64(63))
+    a, b = bits[0].view(np.float64), bits[1].view(np.float64)
+    s, e_int, e_fp = _run(a, b)
+    assert np.array_equal(_bits(e_int), _bits(e_fp))
+
+
+@pytest.mark.parametrize("spread", [0, 3, 20, 52, 53, 54, 55, 56, 60, 120])
+def test_random_pairs_with_close_exponents(spread):
+    # exponent gaps up to `spread`, both signs: rounding, cancellation, the
+    # e(x) - e(y) > 54 shortcut and its boundary
+    rng = np.random.default_rng(100 + spread)
+    n = 1 << 18
+    a = rng.uniform(1, 2, n) * np.ldexp(1.0, rng.integers(-900, 900, n))
+    a *= rng.choice([-1.0, 1.0], n)
+    b = rng.uniform(1, 2, n) * np.ldexp(a, -rng.integers(0, spread + 1, n)) * rng.choice([-1.0, 1.0], n)
+    s, e_int, e_fp = _run(np.concatenate([a, b]), np.concatenate([b, a]))
+    assert np.array_equal(_bits(e_int), _bits(e_fp))
+
+
+def test_crafted_pairs():
+    tiny = np.ldexp(1.0, -1074)
+    big = np.finfo(np.float64).max
+    u = 2.0 ** -53
+    vals = [0.0, -0.0, 1.0, -1.0, 1.0 + 2 * u, 1.0 - u, 2.0, 3.0, 0.5, tiny, -tiny, 2 * tiny, np.ldexp(1.0, -1022),
+            np.ldexp(1.0, -1022) * (1 - 2 * u), big, -big, np.inf, -np.inf, np.nan, np.ldexp(1.0, 1023),
+            1.0 + u, np.ldexp(1.0, -52), np.ldexp(1.0, -53), np.ldexp(1.0, -54), np.ldexp(1.0, -55),
+            np.ldexp(1.0, -56), np.ldexp(3.0, -55), np.ldexp(1.0, -1000), np.ldexp(1.0, 1000), 1e-300, 1e300]
+    vals = np.array(vals + [-v for v in vals])
+    a, b = np.meshgrid(vals, vals, indexing="ij")
+    s, e_int, e_fp = _run(a.ravel(), b.ravel())
+    assert np.array_equal(_bits(e_int), _bits(e_fp))
+
+
+def test_multiply_accumulate_pairs():
+    # (accumulator, product) pairs of DD GEMMs on the benchmark's inputs
+    from paper_1710_01839_gb300 import inputs as I
+    A = I.dd_random(64, 256, 5, exp_spread=20)
+    B = I.dd_random(256, 64, 6, exp_spread=20)
+    prods = (A[0][:, :, None] * B[0][None, :, :]).reshape(64, -1)
+    acc = np.cumsum(prods, axis=1)
+    s, e_int, e_fp = _run(acc[:, :-1].ravel(), prods[:, 1:].ravel())
+    assert np.array_equal(_bits(e_int), _bits(e_fp))
+    # and the error is exact: s + e == a + b in higher precision on a sample
+    from fractions import Fraction
+    a, b = acc[:, :-1].ravel()[:500], prods[:, 1:].ravel()[:500]
+    for x, y, ss, ee in zip(a, b, s[:500], e_int[:500]):
+        assert Fraction(float(x)) + Fraction(float(y)) == Fraction(float(ss)) + Fraction(float(ee))
