@@ -93,15 +93,16 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
 }
 
 // Relative cost of one multiply-accumulate, for ordering work items only:
-// time per MAC of each tile's kernel at full occupancy on GB300, DD = 9.4
-// (FP64 operations: DD 9.4, QD 76; the 128- and 256-bit multi-limb MACs
-// issue 290 and 452 instructions, about 0.6 and 0.95 of a DD MAC's time).
+// time per MAC of each tile kind on GB300 in units where a DD MAC is 7.1
+// (its FP64 operations: DD 7.1 and QD 63.25 at 89 / 82 % of the FP64 pipe;
+// the 128- and 256-bit multi-limb MACs issue 265 and 417 instructions at
+// about 44 % of the issue rate).
 static double mac_cost(int tk) {
     switch (tk) {
-        case T_DD16: case T_DD32: return 9.4;
-        case T_QD16: case T_QD32: return 76.0;
-        case T_MP128: return 6.0;
-        default: return 9.0;
+        case T_DD16: case T_DD32: return 7.1;
+        case T_QD16: case T_QD32: return 68.5;
+        case T_MP128: return 8.3;
+        default: return 13.5;
     }
 }
 

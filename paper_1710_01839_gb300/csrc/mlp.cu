@@ -294,11 +294,21 @@ bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n,
     for (size_t i = 0; i < cs.size(); i++)
         encode_features(kind, prec_bits, m, l, n, cs[i].algo, cs[i].tile, cs[i].depth, sms, &F[i * NF]);
     if (predict(F.data(), (int)cs.size(), T.data()) != MPGEMM_OK) return false;
-    size_t best = (size_t)(std::min_element(T.begin(), T.end()) - T.begin());
-    out->algo = cs[best].algo;
-    out->n_min = cs[best].tile;
-    out->depth = cs[best].depth;
-    if (pred_ms) *pred_ms = T[best];
+    const size_t best = (size_t)(std::min_element(T.begin(), T.end()) - T.begin());
+    // Among configurations predicted within 10 % of the best, the one with
+    // the fewest launches: the model's relative error is largest on small,
+    // launch-bound products, where Strassen's 3d + 1 launches decide.
+    auto launches = [](const Cand& c) { return c.algo == MPGEMM_STRASSEN ? 3 * c.depth + 1 : 1; };
+    size_t pick = best;
+    for (size_t i = 0; i < cs.size(); i++) {
+        if (T[i] > 1.10f * T[best]) continue;
+        const int li = launches(cs[i]), lp = launches(cs[pick]);
+        if (li < lp || (li == lp && T[i] < T[pick])) pick = i;
+    }
+    out->algo = cs[pick].algo;
+    out->n_min = cs[pick].tile;
+    out->depth = cs[pick].depth;
+    if (pred_ms) *pred_ms = T[pick];
     return true;
 }
 

@@ -7,9 +7,10 @@ Steps: mpgemm_cost_collect times `count` random configurations (shapes
 log-uniform in [16, max_dim], DD / QD / 128- and 256-bit multi-limb, every valid
 algorithm / tile / Strassen depth); 90 % train the model (mpgemm_cost_train),
 10 % measure its held-out error.  Then, for a set of random shapes, the
-configuration the model picks is timed against every candidate timed
-exhaustively, and the regret (t_model / t_best - 1) is reported.  Prints one
-JSON report.
+configuration the library's choice rule picks with the model
+(mpgemm_cost_choice) is timed against every candidate timed exhaustively,
+and the regret (t_model / t_best - 1) is reported.  Prints one JSON report.
+--evaluate MODEL runs only the regret study of a saved model.
 """
 
 from __future__ import annotations
@@ -75,14 +76,16 @@ def regret_study(shapes_seed=99, count=12, max_dim=1024):
         for d in (1, 2, 3):
             if all(x % (1 << d) == 0 and (x >> d) >= 16 for x in (m, l, n)):
                 cands += [("strassen", t, d) for t in (16, 32, 64) if t <= tmax]
-        F = np.array([cm.features(fmt, m, l, n, a, t, d, prec_bits=bits) for a, t, d in cands])
-        pred = cm.predict(F)
-        pick = int(np.argmin(pred))
+        ch = cm.choice(fmt, m, l, n, prec_bits=bits)      # the library's rule (mpgemm_cost_choice)
+        pick_c = (ch["algo"], ch["n_min"], ch["depth"])
+        if pick_c not in cands:
+            cands.append(pick_c)
+        pick = cands.index(pick_c)
         meas = [_time(run(*c)) for c in cands]
         best = int(np.argmin(meas))
         rows.append({"fmt": fmt if fmt != "mp" else f"mp{bits}", "m": m, "l": l, "n": n, "model_pick": cands[pick], "best": cands[best],
                      "t_model_ms": meas[pick], "t_best_ms": meas[best], "regret": meas[pick] / meas[best] - 1,
-                     "pred_ms_of_pick": float(pred[pick])})
+                     "pred_ms_of_pick": float(ch["pred_ms"])})
     reg = [r["regret"] for r in rows]
     return {"shapes": rows, "mean_regret": float(np.mean(reg)), "median_regret": float(np.median(reg)),
             "max_regret": float(np.max(reg))}
@@ -96,9 +99,16 @@ def main():
     ap.add_argument("--seed", type=int, default=1714)
     ap.add_argument("--out", default=None)
     ap.add_argument("--regret-shapes", type=int, default=12)
+    ap.add_argument("--evaluate", default=None, metavar="MODEL",
+                    help="only load MODEL and run the regret study (no collection or training)")
     args = ap.parse_args()
     import torch  # noqa: F401  (CUDA context, current stream)
     from paper_1710_01839_gb300 import costmodel as cm
+    if args.evaluate:
+        cm.load(args.evaluate)
+        print(json.dumps({"model": args.evaluate,
+                          "regret": regret_study(count=args.regret_shapes, max_dim=args.max_dim)}), flush=True)
+        return
     t0 = time.time()
     F, T = cm.collect(args.count, seed=args.seed, max_dim=args.max_dim)
     t_collect = time.time() - t0
