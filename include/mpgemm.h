@@ -407,6 +407,11 @@ int mpgemm_selftest_wait_timeout(int limit_ms, void* stream);
    bit for every pair of doubles.  Device pointers (out: 3 count doubles);
    asynchronous on stream; MPGEMM_EINVAL for bad arguments. */
 int mpgemm_selftest_two_sum(int64_t count, const double* a, const double* b, double* out, void* stream);
+/* Self-test of the DD kernel's product error term: out[i] = RN(a[i] b[i]),
+   out[count + i] = its rounding error as the kernel computes it (the
+   integer-pipe form) and out[2 count + i] = fma(a[i], b[i], -out[i]).  The
+   two error planes are equal bit for bit for every pair of doubles. */
+int mpgemm_selftest_two_prod(int64_t count, const double* a, const double* b, double* out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Precision selection from an accuracy target (the paper's outlook: choose

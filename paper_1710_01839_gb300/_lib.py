@@ -85,6 +85,7 @@ SIGNATURES = {
     "mpgemm_terms_to_mp": (_I, [_I, _I64, _P, _I, _P, _P]),
     "mpgemm_mp_to_terms": (_I, [_I, _I64, _I, _P, _P, _P]),
     "mpgemm_selftest_two_sum": (_I, [_I64, _P, _P, _P, _P]),
+    "mpgemm_selftest_two_prod": (_I, [_I64, _P, _P, _P, _P]),
 }
 
 

@@ -7,9 +7,9 @@
 //   DD:  state (s, t).  p = RN(ah bh) and its exact error e from one FMA,
 //        the two cross products accumulated into t with two more FMAs, then
 //        (s, r) = TwoSum(s, p) and t <- t + (e + r).  Every DD_RENORM steps
-//        (s, t) = TwoSum(s, t).  7 FP64 operations per step with the
-//        exponent-ordered TwoSum below, whose error term runs on the integer
-//        pipe (the library DD add + multiply pair costs 27).
+//        (s, t) = TwoSum(s, t).  6 FP64 operations per step: the error
+//        terms of the product and of the exponent-ordered TwoSum below run
+//        on the integer pipe (the library DD add + multiply pair costs 27).
 //        Worst-case error after l steps: about (DD_RENORM + 3) l u^2 sum|a||b|
 //        plus O(u^2) per product, inside the required 16 l u^2 |A||B|
 //        (= 4 l 2^-104 |A||B|) for DD_RENORM = 8.
@@ -75,6 +75,33 @@ __device__ __forceinline__ double fast_two_sum_err(double x, double y, double s)
         (long long)((ri < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)F << 52) | (mant & MM)));
 }
 
+// The rounding error e = a b - p of p = RN(a b), exactly (what
+// fma(a, b, -p) returns), computed on the integer pipe: with normal a, b, p
+// the mantissa product Ma Mb (106 bits) and p's mantissa scaled to the same
+// unit (Mp 2^k, k = 52 or 53) differ by at most half an ulp of p, 2^52
+// units, so the difference is the low 64 bits of Ma Mb minus Mp 2^k modulo
+// 2^64, and e is assembled from it without rounding.  Zero, subnormal,
+// infinite or NaN operands or product and a subnormal e take the FMA.
+// Bit-identical to fma(a, b, -p) (checked by mpgemm_selftest_two_prod).
+__device__ __forceinline__ double two_prod_err(double a, double b, double p) {
+    const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
+    const unsigned long long bp = (unsigned long long)__double_as_longlong(p);
+    const int Ea = (int)((ba >> 52) & 0x7ff), Eb = (int)((bb >> 52) & 0x7ff), Ep = (int)((bp >> 52) & 0x7ff);
+    if (Ea == 0 || Eb == 0 || Ep == 0 || Ea == 0x7ff || Eb == 0x7ff || Ep == 0x7ff) return __fma_rn(a, b, -p);
+    constexpr unsigned long long MM = (1ull << 52) - 1ull, H = 1ull << 52;
+    const unsigned long long Ma = (ba & MM) | H, Mb = (bb & MM) | H, Mp = (bp & MM) | H;
+    const int k = Ep - Ea - Eb + 1075;                     // 52, or 53 when p carried into the next binade
+    const long long eu = (long long)(Ma * Mb - (Mp << k)); // (|a b| - |p|) / 2^(Ea + Eb - 2150)
+    if (eu == 0) return 0.0;
+    const unsigned long long m = eu < 0 ? 0ull - (unsigned long long)eu : (unsigned long long)eu;
+    const int lz = __clzll((long long)m);                  // >= 11: |eu| <= 2^52
+    const int F = Ea + Eb - 1064 - lz;                      // exponent field of e
+    if (F <= 0) return __fma_rn(a, b, -p);
+    const unsigned long long sgn = ((ba ^ bb) >> 63) ^ (eu < 0 ? 1ull : 0ull);
+    return __longlong_as_double((long long)((sgn << 63) | ((unsigned long long)F << 52) | ((m << (lz - 11)) & MM)));
+}
+
 // TwoSum: s = RN(a + b), e = a + b - s exactly, for any a, b.  Computed as
 // Dekker's Fast2Sum after ordering the operands by their exponent fields,
 // compared on the integer pipe, with the error term on the integer pipe as
@@ -122,7 +149,7 @@ __device__ __forceinline__ void dd_zero(DDAcc& c) {
 
 __device__ __forceinline__ void dd_mac(DDAcc& c, double ah, double al, double bh, double bl) {
     double p = __dmul_rn(ah, bh);
-    double e = __fma_rn(ah, bh, -p);   // exact error of p
+    double e = two_prod_err(ah, bh, p);   // exact error of p, on the integer pipe
     double t = __fma_rn(ah, bl, c.t);   // cross products straight into the low part
     t = __fma_rn(al, bh, t);
     double s, r;

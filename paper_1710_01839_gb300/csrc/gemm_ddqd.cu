@@ -112,7 +112,28 @@ __global__ void k_selftest_two_sum(int64_t count, const double* a, const double*
     out[2 * count + i] = e2;
 }
 
+// The product error term on the integer pipe against fma(a, b, -p)
+// (mpgemm_selftest_two_prod).
+__global__ void k_selftest_two_prod(int64_t count, const double* a, const double* b, double* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double p = __dmul_rn(a[i], b[i]);
+    out[i] = p;
+    out[count + i] = two_prod_err(a[i], b[i], p);
+    out[2 * count + i] = __fma_rn(a[i], b[i], -p);
+}
+
 }  // namespace mpg
+
+extern "C" int mpgemm_selftest_two_prod(int64_t count, const double* a, const double* b, double* out,
+                                        void* stream) {
+    if (count < 0 || (count && (!a || !b || !out))) return MPGEMM_EINVAL;
+    if (count == 0) return MPGEMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    mpg::PartitionScope pscope(s);
+    mpg::k_selftest_two_prod<<<mpg::ceil_div(count, 256), 256, 0, s>>>(count, a, b, out);
+    return mpg::check_launch();
+}
 
 extern "C" int mpgemm_selftest_two_sum(int64_t count, const double* a, const double* b, double* out,
                                        void* stream) {

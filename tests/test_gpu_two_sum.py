@@ -84,3 +84,45 @@ def test_multiply_accumulate_pairs():
     a, b = acc[:, :-1].ravel()[:500], prods[:, 1:].ravel()[:500]
     for x, y, ss, ee in zip(a, b, s[:500], e_int[:500]):
         assert Fraction(float(x)) + Fraction(float(y)) == Fraction(float(ss)) + Fraction(float(ee))
+
+
+def _run_prod(a, b):
+    import ctypes
+    import torch
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = torch.empty(3 * len(a), dtype=torch.float64, device="cuda")
+    ad, bd = dev(a), dev(b)
+    rc = mpg.lib().mpgemm_selftest_two_prod(len(a), ctypes.c_void_p(ad.data_ptr()), ctypes.c_void_p(bd.data_ptr()),
+                                            ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == 0
+    o = out.cpu().numpy().reshape(3, -1)
+    return o[0], o[1], o[2]
+
+
+def test_product_error_random_pairs():
+    # the DD kernel's product error term on the integer pipe == fma(a, b, -p)
+    rng = np.random.default_rng(77)
+    n = 1 << 20
+    bits = rng.integers(0, 2**63, size=(2, n), dtype=np.uint64) | (rng.integers(0, 2, size=(2, n), dtype=np.uint64) << np.uint64(63))
+    a, b = bits[0].view(np.float64), bits[1].view(np.float64)
+    p, e_int, e_fma = _run_prod(a, b)
+    assert np.array_equal(_bits(e_int), _bits(e_fma))
+    # products near 1 (all carries and roundings of the mantissa product)
+    a = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n) * np.ldexp(1.0, rng.integers(-500, 500, n))
+    b = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n) * np.ldexp(1.0, rng.integers(-500, 500, n))
+    p, e_int, e_fma = _run_prod(a, b)
+    assert np.array_equal(_bits(e_int), _bits(e_fma))
+
+
+def test_product_error_crafted_pairs():
+    tiny = np.ldexp(1.0, -1074)
+    big = np.finfo(np.float64).max
+    u = 2.0 ** -53
+    vals = [0.0, -0.0, 1.0, 1.0 + 2 * u, 1.0 - u, 2.0 - 2 * u, np.sqrt(2.0), 3.0, tiny, np.ldexp(1.0, -1022),
+            np.ldexp(1.0, -600), np.ldexp(1.0, -511), np.ldexp(1.5, -512), big, np.ldexp(1.0, 600),
+            np.ldexp(1.0, 512), np.inf, np.nan, 1.0 / 3.0, np.ldexp(1.0 - u, 1), 1e-300, 1e300]
+    vals = np.array(vals + [-v for v in vals])
+    a, b = np.meshgrid(vals, vals, indexing="ij")
+    p, e_int, e_fma = _run_prod(a.ravel(), b.ravel())
+    assert np.array_equal(_bits(e_int), _bits(e_fma))
