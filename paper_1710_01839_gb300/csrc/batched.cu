@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
 
 // Relative cost of one multiply-accumulate, for ordering work items only:
 // time per MAC of each tile kind on GB300 in units where a DD MAC is 7.1
-// (its FP64 operations: DD 7.1 and QD 63.25 at 89 / 82 % of the FP64 pipe;
+// (about its FP64 operations: DD 6.1 - 7.1 and QD 63.25 at 82 - 89 % of the FP64 pipe;
 // the 128- and 256-bit multi-limb MACs issue 265 and 417 instructions at
 // about 44 % of the issue rate).
 static double mac_cost(int tk) {
