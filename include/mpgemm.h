@@ -204,8 +204,8 @@ int mpgemm_dd_strassen_noalloc(int64_t m, int64_t l, int64_t n, const double* A,
  * multi-limb GEMM (Eqs 1-3, every multiply and add rounded to p bits, as
  * mpgemm_mp), and C is rounded back to 2 (DD) or 4 (QD) doubles.  On GB300
  * the FP64 pipe executes 2 operations per clock per SM, so 128-bit limbs
- * give DD about 1.5x and 256-bit limbs QD about 7x the rate of mpgemm_dd /
- * mpgemm_qd, with a much smaller error (2^-128 / 2^-256 per operation
+ * give DD about 1.3x and 256-bit limbs QD about 7.6x the rate of mpgemm_dd
+ * / mpgemm_qd (measured at 2048^3 / 1024^3), with a much smaller error (2^-128 / 2^-256 per operation
  * instead of the DD / QD bounds 4 l 2^-104 |A||B| and 4 l 2^-208 |A||B|).
  *   Conversion to p bits (mpgemm_terms_to_mp): c = +0, then for t = 0..T-1
  *     c = RN_p(c + x_t) with the double x_t taken exactly.
