@@ -31,23 +31,30 @@ ALGO = {"simple": 0, "block": 1, "strassen": 2}
 _lib = None
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile one C source of the oracle into the shared library `out`."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
+           "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (gcc, OpenMP)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    return compile_source(_SRC, _LIB)
 
 
 def lib():
+    """The compiled oracle.  MPGEMM_ORACLE_LIB names another compiled copy of
+    mpgemm_oracle.c to load instead (the planted-mistake tests use it)."""
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(os.environ.get("MPGEMM_ORACLE_LIB") or build())
         _declare(_lib)
     return _lib
 

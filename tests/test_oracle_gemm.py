@@ -212,6 +212,28 @@ def test_mp_gemm_matches_mpmath_sequence(w):
             assert got == want
 
 
+@pytest.mark.parametrize("algo", ["simple", "block"])
+def test_mp_gemm_zero_signs_follow_ieee_rules(algo):
+    # IEEE 754 round-to-nearest: an exact zero sum of opposite-signed operands
+    # is +0, (-0) + (-0) = -0, and a product's sign is the XOR of its
+    # operands'.  Eq 1's sum starts from the empty sum, +0, so an entry whose
+    # products are all zeros is +0 whatever their signs.  (Eq 3 is left out:
+    # its rounded sums of P1..P7 need not cancel to zero on a zero row.)
+    w, m, l, n = 2, 4, 6, 4
+    A, B = I.mp_random(m, l, w, 91), I.mp_random(l, n, w, 92)
+    A[:, 1, :] = 0
+    A[1, 1, :] = 3                       # row 1 of A: all -0
+    B[:, :, 2] = 0
+    B[1, :, 2] = 2                       # column 2 of B: all +0
+    C = oracle.mp_gemm(A, B, prec_bits=32 * w, algo=algo, n_min=2)
+    for i in range(m):
+        for j in range(n):
+            if i == 1 or j == 2:
+                assert int(C[1, i, j]) == 2, (i, j, int(C[1, i, j]))    # +0
+            else:
+                assert int(C[1, i, j]) & 2 == 0
+
+
 # ---------------------------------------------------------------- the paper's matrices
 
 def _sqrt15_times(q: Fraction, bits=400) -> Fraction:

@@ -38,6 +38,23 @@ def test_exponents_and_scaling():
         assert f[j] == max(_frexp_exp(x) for x in B[0, :, j] if x != 0)
 
 
+def test_exponents_skip_zeros_of_small_rows():
+    # rows and columns of magnitudes far below 1 with zeros among them: the
+    # exponent is the largest over the nonzero entries (negative here), so a
+    # zero must not count as exponent 0
+    A, B = I.dd_rowcol_scaled(6, 8, 5, seed=11)
+    A *= 2.0 ** -40
+    B *= 2.0 ** -40
+    A[:, :, 3] = 0.0
+    B[:, 2, :] = 0.0
+    e = oracle.ozaki_row_expo(A)
+    f = oracle.ozaki_col_expo(B)
+    for i in range(6):
+        assert e[i] == max(_frexp_exp(x) for x in A[0, i] if x != 0) < 0
+    for j in range(5):
+        assert f[j] == max(_frexp_exp(x) for x in B[0, :, j] if x != 0) < 0
+
+
 @pytest.mark.parametrize("S", [1, 3, 8, 16])
 def test_digits_are_exact_truncation(S):
     A, _ = I.dd_rowcol_scaled(6, 10, 4, seed=4)

@@ -72,10 +72,13 @@ def test_two_prod_exact():
 # ------------------------------------------------------------------ DD
 
 def _rand_dd(rng, n, emin=-30, emax=30):
+    # lo = U(-1/2, 1/2) ulp(hi) 2^-j: numpy's uniform doubles sit on a fixed
+    # 2^-53 grid, so without the random shift j every sum of two lo parts
+    # would be exact and a dropped rounding-error term would go unseen
     out = []
     for _ in range(n):
         hi = float(_rand_doubles(rng, 1, emin, emax)[0])
-        lo = float(rng.uniform(-0.5, 0.5)) * float(ulp(hi))
+        lo = float(rng.uniform(-0.5, 0.5)) * float(ulp(hi)) * 2.0 ** -int(rng.integers(0, 12))
         out.append((hi, lo))
     return out
 
@@ -84,10 +87,11 @@ def test_dd_add_error_bound_and_normalised():
     rng = np.random.default_rng(4)
     xs = _rand_dd(rng, 3000)
     ys = _rand_dd(rng, 3000)
-    # cancellation-heavy pairs: y close to -x
+    # cancellation-heavy pairs: y close to -x, the low parts at other exponents
+    # (their sum is then rarely a double, and the result is that sum as a DD)
     for i in range(500):
         hi, lo = xs[i]
-        ys[i] = (-hi, float(rng.uniform(-0.5, 0.5)) * float(ulp(hi)))
+        ys[i] = (-hi, float(rng.uniform(-0.5, 0.5)) * float(ulp(hi)) * 2.0 ** -int(rng.integers(1, 12)))
     worst = Fraction(0)
     for x, y in zip(xs, ys):
         z = oracle.dd_add(x, y)

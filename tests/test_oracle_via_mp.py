@@ -109,6 +109,16 @@ def test_from_mp_is_the_greedy_expansion(bits, T):
     Y[2:, 0, 0] = 0
     Y[2 + w - 1, 0, 0] = 0x80000000         # a power of two
     Y[2:2 + w - 1, 0, 1] = 0xFFFFFFFF       # a run of ones below the top limb
+    # halfway patterns for the first double: the bit below its 53 (index
+    # p - 54) set and the bits under it clear in the top 64, then the lowest
+    # bit of limb 0 set (above halfway: rounds up), clear (a tie: to even), and
+    # an odd last bit with a clear tail (a tie: up to even)
+    p = 32 * w
+    for col, bit_list in ((2, [p - 1, p - 54, 0]), (3, [p - 1, p - 54]), (4, [p - 1, p - 53, p - 54])):
+        M = sum(1 << b for b in bit_list)
+        for q in range(w):
+            Y[2 + q, 0, col] = (M >> (32 * q)) & 0xFFFFFFFF
+        Y[1, 0, col] &= 1
     _check_from_mp(Y, bits, T)
 
 
