@@ -303,8 +303,12 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
  *   mpgemm_cost_features   feature vector (mpgemm_cost_num_features floats)
  *   mpgemm_cost_collect    time `count` random configurations (shapes
  *                          log-uniform in [16, max_dim], formats DD / QD /
- *                          256-bit, valid algorithms); host output arrays;
- *                          synchronous; allocates its own operand buffers
+ *                          128- or 256-bit multi-limb, valid algorithms);
+ *                          host output arrays; synchronous; allocates its
+ *                          own operand buffers and releases them on every
+ *                          path; a failed CUDA call gives MPGEMM_ECUDA, a
+ *                          device-side failure of the timed GEMMs their
+ *                          stream status
  *   mpgemm_cost_train      train a new model (epochs x count/128 Adam steps,
  *                          lr 2e-3) and install it; optional per-epoch loss
  *   mpgemm_cost_predict    predicted milliseconds for host feature vectors

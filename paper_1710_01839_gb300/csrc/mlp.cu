@@ -414,15 +414,21 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
     const size_t maxe = (size_t)max_dim * max_dim;
     const size_t bytes = maxe * 40;   // largest element: 256-bit multi-limb, 10 words
     void *A = nullptr, *B = nullptr, *C = nullptr;
-    MPG_CUDA(cudaMalloc(&A, bytes));
-    MPG_CUDA(cudaMalloc(&B, bytes));
-    MPG_CUDA(cudaMalloc(&C, bytes));
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = MPGEMM_OK;
+    auto ck = [&](cudaError_t e) {   // first failure wins; everything is released below
+        if (e != cudaSuccess && rc == MPGEMM_OK) {
+            set_last_cuda_error(e);
+            rc = MPGEMM_ECUDA;
+        }
+    };
+    ck(cudaMalloc(&A, bytes));
+    ck(cudaMalloc(&B, bytes));
+    ck(cudaMalloc(&C, bytes));
+    ck(cudaEventCreate(&e0));
+    ck(cudaEventCreate(&e1));
     std::mt19937_64 rng(seed);
     std::uniform_real_distribution<double> U(std::log(16.0), std::log((double)max_dim));
-    int rc = MPGEMM_OK;
     for (int i = 0; i < count && rc == MPGEMM_OK; i++) {
         int64_t m = (int64_t)std::lround(std::exp(U(rng))), l = (int64_t)std::lround(std::exp(U(rng))),
                 n = (int64_t)std::lround(std::exp(U(rng)));
@@ -450,12 +456,14 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
             k_fill_random<<<ceil_div((int64_t)(ea / 2), 256), 256, 0, s>>>((double*)A, ea / 2, seed + 2 * i, 1, 1);
             k_fill_random<<<ceil_div((int64_t)(eb / 2), 256), 256, 0, s>>>((double*)B, eb / 2, seed + 2 * i + 1, 1, 1);
             // exponent plane 0, flags plane 0, top limb with its high bit set
-            MPG_CUDA(cudaMemsetAsync(A, 0, sizeof(uint32_t) * 2 * (size_t)(m * l), s));
-            MPG_CUDA(cudaMemsetAsync(B, 0, sizeof(uint32_t) * 2 * (size_t)(l * n), s));
+            ck(cudaMemsetAsync(A, 0, sizeof(uint32_t) * 2 * (size_t)(m * l), s));
+            ck(cudaMemsetAsync(B, 0, sizeof(uint32_t) * 2 * (size_t)(l * n), s));
             const size_t top = (size_t)(1 + prec / 32);   // plane of the top limb
-            fill_u32((uint32_t*)A + top * (size_t)(m * l), (size_t)(m * l), 0x80000001u, s);
-            fill_u32((uint32_t*)B + top * (size_t)(l * n), (size_t)(l * n), 0x80000001u, s);
+            if (rc == MPGEMM_OK) rc = fill_u32((uint32_t*)A + top * (size_t)(m * l), (size_t)(m * l), 0x80000001u, s);
+            if (rc == MPGEMM_OK) rc = fill_u32((uint32_t*)B + top * (size_t)(l * n), (size_t)(l * n), 0x80000001u, s);
         }
+        ck(cudaGetLastError());
+        if (rc != MPGEMM_OK) break;
         auto run = [&]() -> int {
             if (kind == MPGEMM_KIND_DD)
                 return mpgemm_dd(m, l, n, (const double*)A, (const double*)B, (double*)C, c.algo, c.tile, c.depth, s);
@@ -467,21 +475,21 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
         rc = run();
         float t[2] = {0.f, 0.f};
         for (int r = 0; r < 2 && rc == MPGEMM_OK; r++) {
-            cudaEventRecord(e0, s);
-            rc = run();
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&t[r], e0, e1);
+            ck(cudaEventRecord(e0, s));
+            if (rc == MPGEMM_OK) rc = run();
+            ck(cudaEventRecord(e1, s));
+            ck(cudaEventSynchronize(e1));
+            ck(cudaEventElapsedTime(&t[r], e0, e1));
         }
         encode_features(kind, prec, m, l, n, c.algo, c.tile, c.depth, sms, features + (size_t)i * NF);
         times_ms[i] = std::min(t[0], t[1]);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     cudaFree(A);
     cudaFree(B);
     cudaFree(C);
-    if (rc == MPGEMM_OK && mpgemm_stream_status(stream) != MPGEMM_OK) rc = MPGEMM_EOVERFLOW;
+    if (rc == MPGEMM_OK) rc = mpgemm_stream_status(stream);   // a device-side failure of the timed GEMMs
     return rc;
 }
 
