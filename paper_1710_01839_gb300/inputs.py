@@ -49,35 +49,22 @@ def seed_for(config: int, rep: int = 0) -> int:
 
 def _canon_pair(hi: np.ndarray, lo: np.ndarray):
     """Rewrite (hi, lo) as (hi', lo') with hi' + lo' == hi + lo exactly and
-    |lo'| <= ulp(hi')/2, by moving hi one step at a time toward the value.
-    Each step's lo update is exact (Sterbenz): it only changes the
-    representation, not the value."""
-    hi = hi.copy()
-    lo = lo.copy()
-    for _ in range(4):
-        mag = np.abs(hi)
-        up = np.nextafter(mag, np.inf) - mag          # ulp above |hi|
-        half = np.where(mag > 0, up * 0.5, 0.0)
-        s = np.sign(hi)
-        rel = lo * s                                   # lo measured along hi's sign
-        too_big = (mag > 0) & (rel > half)
-        too_neg = (mag > 0) & (rel < -np.where(mag > 0, (mag - np.nextafter(mag, 0)) * 0.5, 0.0))
-        if not (too_big.any() or too_neg.any()):
-            break
-        new_up = np.nextafter(mag, np.inf)
-        new_dn = np.nextafter(mag, 0.0)
-        new_mag = np.where(too_big, new_up, np.where(too_neg, new_dn, mag))
-        delta = new_mag - mag                          # exact: one ulp step
-        rel = rel - delta                              # exact (Sterbenz)
-        hi = s * new_mag
-        lo = s * rel
-    return hi, lo
+    |lo'| <= ulp(hi')/2: hi' = RN(hi + lo) and lo' its exact rounding error
+    (Knuth's TwoSum, six IEEE double operations, no precondition).  Only the
+    representation changes, not the value; a pair that is already canonical
+    is returned unchanged (outside exact half-ulp ties)."""
+    s = hi + lo
+    bv = s - hi
+    av = s - bv
+    return s, (hi - av) + (lo - bv)
 
 
 def _canon_terms(x: np.ndarray) -> np.ndarray:
-    """Apply the pairwise rule top-down until every adjacent pair is canonical."""
+    """Apply the pairwise rule top-down until every adjacent pair is canonical
+    (a rewrite of one pair can unsettle the pair above it, hence the passes;
+    each pass moves value upward, and a few passes settle every element)."""
     x = x.copy()
-    for _ in range(8):
+    for _ in range(64):
         changed = False
         for i in range(x.shape[0] - 1):
             h, l = _canon_pair(x[i], x[i + 1])
@@ -85,8 +72,8 @@ def _canon_terms(x: np.ndarray) -> np.ndarray:
                 changed = True
             x[i], x[i + 1] = h, l
         if not changed:
-            break
-    return x
+            return x
+    raise RuntimeError("expansion did not settle")
 
 
 # ----------------------------------------------------------------------------
