@@ -4,7 +4,8 @@ Each mutant is one plausible slip in oracle/mpgemm_oracle.c: a wrong sign,
 a dropped term, a wrong index or operand, a wrong rounding rule, an
 off-by-one limit.  For each one the test compiles a mutated copy of the
 oracle (CPU only), points the oracle package at it through
-MPGEMM_ORACLE_LIB, runs the oracle's pin tests in a child process and
+MPGEMM_ORACLE_LIB, runs the oracle's pin tests (all but the slow
+million-pair ones) in a child process and
 requires them to fail (a failed assertion, or a loud abort of the oracle's
 own range checks).  The unmutated source, compiled the same way, must pass,
 so that a failure is the mutant's doing and not the harness's.  A mutant
@@ -147,8 +148,9 @@ def _run(name, src_text, workdir):
         fh.write(src_text)
     oracle.compile_source(src, lib)
     env = dict(os.environ, MPGEMM_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
-    p = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
-                        *PINS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    p = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m",
+                        "not gpu and not slow", *PINS], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
     tail = (p.stdout + p.stderr).strip().splitlines()[-3:]
     return p.returncode, tail
 

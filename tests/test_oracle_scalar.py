@@ -69,6 +69,36 @@ def test_two_prod_exact():
         assert F(p) + F(e) == F(x) * F(y)
 
 
+def _scaled(x: float) -> int:
+    """x * 2^1074 as an exact integer (every finite double is a multiple of
+    2^-1074)."""
+    num, den = x.as_integer_ratio()
+    return num << (1075 - den.bit_length())
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("op", ["two_sum", "fast_two_sum", "two_prod"])
+def test_error_free_transformations_on_a_million_pairs(op):
+    # exact integer arithmetic at the scale 2^1074: s + e == a + b (a * b),
+    # s (p) the IEEE round-to-nearest sum (product) that numpy computes
+    rng = np.random.default_rng({"two_sum": 11, "fast_two_sum": 12, "two_prod": 13}[op])
+    n = 1_000_000
+    a = _rand_doubles(rng, n, -60, 60)
+    b = _rand_doubles(rng, n, -60, 60)
+    if op == "fast_two_sum":
+        swap = np.abs(a) < np.abs(b)
+        a, b = np.where(swap, b, a), np.where(swap, a, b)
+    f = getattr(oracle, op)
+    ref = a * b if op == "two_prod" else a + b
+    for x, y, r in zip(a.tolist(), b.tolist(), ref.tolist()):
+        s, e = f(x, y)
+        assert s == r
+        if op == "two_prod":
+            assert _scaled(x) * _scaled(y) == (_scaled(s) + _scaled(e)) << 1074
+        else:
+            assert _scaled(x) + _scaled(y) == _scaled(s) + _scaled(e)
+
+
 # ------------------------------------------------------------------ DD
 
 def _rand_dd(rng, n, emin=-30, emax=30):
