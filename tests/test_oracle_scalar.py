@@ -240,6 +240,26 @@ def test_mp_random_vs_mpmath(w):
         _check_against_refs(w, x, y2, "add")
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("w,n", [(1, 100_000), (2, 100_000), (4, 100_000), (8, 100_000)])
+def test_mp_many_random_pairs_vs_mpmath(w, n):
+    # mpmath's correctly rounded mpf_mul / mpf_add alone (the Fraction
+    # reference is left to the smaller test above), on n random pairs per
+    # width, with exponents close enough for every alignment and
+    # cancellation depth
+    pytest.importorskip("mpmath")
+    from mpmath.libmp import mpf_add, mpf_mul
+    p = 32 * w
+    rng = random.Random(7000 + w)
+    for _ in range(n):
+        x = _rand_mp(rng, w, -4, 4)
+        y = (rng.randint(x[0] - p - 3, x[0] + 2), rng.randint(0, 1), (1 << (p - 1)) | rng.getrandbits(p - 1))
+        xw, yw = mp_words(*x, w), mp_words(*y, w)
+        fx, fy = _to_mpf(*x, w), _to_mpf(*y, w)
+        assert oracle.mp_mul(w, xw, yw).tolist() == mp_words(*mp_from_mpmath(mpf_mul(fx, fy, p, "n"), w), w).tolist()
+        assert oracle.mp_add(w, xw, yw).tolist() == mp_words(*mp_from_mpmath(mpf_add(fx, fy, p, "n"), w), w).tolist()
+
+
 @pytest.mark.parametrize("w", [1, 4, 64])
 def test_mp_constructed_ties_and_carries(w):
     pytest.importorskip("mpmath")
