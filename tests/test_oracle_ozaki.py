@@ -124,6 +124,27 @@ def test_end_to_end_error_bound_and_monotone_in_slices():
     assert errs[8] > 2.0**-100   # too few slices really does lose accuracy
 
 
+@pytest.mark.slow
+def test_error_curve_by_slices():
+    # the split-precision workload's recipe at 64 x 512 x 64: each int8 slice
+    # adds about 7 bits and each FP8 (base-32) slice about 5 until the final
+    # DD rounding (about 2^-110 of |A||B| here) is all that is left; the
+    # defaults S = 16 (int8) and S = 22 (FP8) are inside 2^-100
+    import math
+    A, B = I.dd_rowcol_scaled(64, 512, 64, seed=I.seed_for(3))
+    lg = lambda C: math.log2(_max_rel_err(A, B, C))
+    int8 = {S: lg(oracle.ozaki_gemm(A, B, S)) for S in range(12, 19)}
+    fp8 = {S: lg(oracle.ozaki_gemm_b32(A, B, S)) for S in range(16, 25)}
+    for curve, step, last in ((int8, 7, 15), (fp8, 5, 21)):
+        keys = sorted(curve)
+        assert all(curve[b] <= curve[a] + 1e-9 for a, b in zip(keys, keys[1:]))
+        for S in keys:
+            if S < last:
+                assert abs((curve[S] - curve[S + 1]) - step) < 1.0, (S, curve)
+        assert curve[keys[-1]] > -112
+    assert int8[16] <= -100 and fp8[22] <= -100
+
+
 def test_exact_on_integers():
     a = I.int_matrix(6, 9, 8, -100, 100)
     b = I.int_matrix(9, 5, 9, -100, 100)
