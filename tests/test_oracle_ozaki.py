@@ -143,6 +143,10 @@ def test_error_curve_by_slices():
                 assert abs((curve[S] - curve[S + 1]) - step) < 1.0, (S, curve)
         assert curve[keys[-1]] > -112
     assert int8[16] <= -100 and fp8[22] <= -100
+    # the stress variant: A's columns and B's rows also scaled by 2^q_k,
+    # q ~ U{-8..8}, so entries spread further below their row / column maxima
+    A, B = I.dd_rowcol_scaled(64, 512, 64, seed=I.seed_for(3), inner_spread=8)
+    assert lg(oracle.ozaki_gemm(A, B, 16)) <= -104 and lg(oracle.ozaki_gemm_b32(A, B, 22)) <= -104
 
 
 def test_exact_on_integers():
