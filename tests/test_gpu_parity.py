@@ -445,3 +445,33 @@ def test_mp_exponent_range_is_flagged(w, algo):
         mpg.gemm_mp(dev(A), dev(B), p, algo=algo, n_min=16)
         want = 0 if name == "in_range" else -4
         assert mpg.stream_status() == want, name
+
+
+# ---------------------------------------------------------------- measured margins at the bench's sizes
+
+def test_strassen_error_margins_at_bench_sizes(capsys):
+    # the bench's DD 2048^3 and QD 1024^3 inputs (exponent spread 2^[-20, 20]);
+    # normwise |C - AB| / (l max|A| max|B|) against the Strassen bounds
+    # (2^-96 DD, 2^-200 QD) and elementwise |C - AB| / |A||B| for the block
+    # algorithm, on 512 random entries, row 0, column 0 and the corners
+    import math
+    rows = []
+    for fmt, n, f, bound, cases in (
+            ("dd", 2048, mpg.gemm_dd, 2.0**-96, [("block", 32, 0), ("strassen", 32, 1), ("strassen", 32, 2),
+                                                   ("strassen", 32, 3)]),
+            ("qd", 1024, mpg.gemm_qd, 2.0**-200, [("block", 16, 0), ("strassen", 16, 3)])):
+        gen = I.dd_random if fmt == "dd" else I.qd_random
+        A, B = gen(n, n, I.seed_for(1, 0), exp_spread=20), gen(n, n, I.seed_for(1, 1), exp_spread=20)
+        Ad, Bd = dev(A), dev(B)
+        ii, jj = sample_indices(n, n, 512, seed=5)
+        scale = n * float(np.max(np.abs(A[0]))) * float(np.max(np.abs(B[0])))
+        for algo, nm, d in cases:
+            err, absab = oracle.exact_check(A, B, host(f(Ad, Bd, algo=algo, n_min=nm, depth=d)), ii, jj)
+            norm, elem = float(np.max(err)) / scale, float(np.max(err / absab))
+            assert norm <= bound
+            if algo == "block":
+                assert elem <= (DD_BOUND if fmt == "dd" else QD_BOUND) * n
+            rows.append(f"{fmt} {n}^3 {algo} d={d}: normwise 2^{math.log2(max(norm, 1e-300)):.1f}, "
+                        f"elementwise 2^{math.log2(max(elem, 1e-300)):.1f}")
+    with capsys.disabled():
+        print("\n" + "\n".join(rows))
