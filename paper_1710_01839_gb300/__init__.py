@@ -15,7 +15,8 @@ from __future__ import annotations
 import ctypes
 import os
 
-from ._lib import (ALGO, KIND, MpgemmError, check, lib, lib_path)  # noqa: F401
+from ._lib import (ALGO, KIND, MpgemmError, check, check_planes, int_dtypes, lib, lib_path,  # noqa: F401
+                   require_cuda)
 
 __all__ = ["gemm_dd", "gemm_qd", "gemm_mp", "gemm_split", "gemm_via_mp", "to_mp", "from_mp", "workspace_size", "set_workspace", "stream_status", "strerror",
            "Partition", "PrecisionChoice", "precision_log2_bound", "select_precision", "exponent_spread",
@@ -34,16 +35,16 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(stream.cuda_stream))
 
 
-def _check_tensor(t, planes, dtypes, name):
-    torch = _torch()
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dtype not in dtypes:
-        raise TypeError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
-    if t.dim() != 3 or t.shape[0] != planes:
-        raise ValueError(f"{name} must have shape ({planes}, rows, cols), got {tuple(t.shape)}")
-    if not t.is_contiguous():
-        raise ValueError(f"{name} must be contiguous")
+_check_tensor = check_planes
+
+
+def _operands(A, B, planes, dtypes):
+    """Check the structure of A (planes, m, l) and B (planes, l, n); return
+    (m, l, n)."""
+    _check_tensor(A, planes, dtypes, "A")
+    m, l = A.shape[1], A.shape[2]
+    _check_tensor(B, planes, dtypes, "B", rows=l)
+    return m, l, B.shape[2]
 
 
 def _algo(a):
@@ -52,15 +53,11 @@ def _algo(a):
 
 def _ddqd(fn, planes, A, B, C, algo, n_min, depth, stream):
     torch = _torch()
-    _check_tensor(A, planes, (torch.float64,), "A")
-    _check_tensor(B, planes, (torch.float64,), "B")
-    m, l = A.shape[1], A.shape[2]
-    if B.shape[1] != l:
-        raise ValueError("inner dimensions differ")
-    n = B.shape[2]
+    m, l, n = _operands(A, B, planes, (torch.float64,))
     if C is None:
         C = torch.empty((planes, m, n), dtype=torch.float64, device=A.device)
-    _check_tensor(C, planes, (torch.float64,), "C")
+    _check_tensor(C, planes, (torch.float64,), "C", rows=m, cols=n)
+    require_cuda(A=A, B=B, C=C)
     rc = fn(m, l, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
             _algo(algo), int(n_min), int(depth), _stream_ptr(stream))
     check(rc)
@@ -81,16 +78,11 @@ def gemm_mp(A, B, prec_bits, C=None, algo="block", n_min=0, depth=0, stream=None
     """C := AB in p-bit multi-limb floating point, p = prec_bits (mpgemm_mp)."""
     torch = _torch()
     w = prec_bits // 32
-    dt = (torch.int32, torch.uint32) if hasattr(torch, "uint32") else (torch.int32,)
-    _check_tensor(A, 2 + w, dt, "A")
-    _check_tensor(B, 2 + w, dt, "B")
-    m, l = A.shape[1], A.shape[2]
-    if B.shape[1] != l:
-        raise ValueError("inner dimensions differ")
-    n = B.shape[2]
+    m, l, n = _operands(A, B, 2 + w, int_dtypes())
     if C is None:
         C = torch.empty((2 + w, m, n), dtype=A.dtype, device=A.device)
-    _check_tensor(C, 2 + w, dt, "C")
+    _check_tensor(C, 2 + w, int_dtypes(), "C", rows=m, cols=n)
+    require_cuda(A=A, B=B, C=C)
     rc = lib().mpgemm_mp(m, l, n, int(prec_bits), ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                          ctypes.c_void_p(C.data_ptr()), _algo(algo), int(n_min), int(depth), _stream_ptr(stream))
     check(rc)
@@ -101,9 +93,11 @@ def gemm_via_mp(A, B, prec_bits=0, C=None, algo="block", n_min=0, depth=0, strea
     """C := AB for DD (2 planes) or QD (4 planes) computed on the integer
     pipe in prec_bits-bit multi-limb arithmetic (mpgemm_dd_via_mp /
     mpgemm_qd_via_mp); prec_bits = 0 picks 128 for DD and 256 for QD."""
-    T = A.shape[0]
+    torch = _torch()
+    T = A.shape[0] if isinstance(A, torch.Tensor) and A.dim() == 3 else 0
     if T not in (2, 4):
         raise ValueError("A must hold 2 (DD) or 4 (QD) planes")
+    _operands(A, B, T, (torch.float64,))
     bits = int(prec_bits) or (128 if T == 2 else 256)
     L = lib()
     fn = L.mpgemm_dd_via_mp if T == 2 else L.mpgemm_qd_via_mp
@@ -114,11 +108,15 @@ def to_mp(X, prec_bits, Y=None, stream=None):
     """DD / QD planes X (T, rows, cols) -> multi-limb planes (2 + w, rows,
     cols), c = RN_p(...RN_p(x_0 + x_1)... + x_(T-1)) (mpgemm_terms_to_mp)."""
     torch = _torch()
-    T = X.shape[0]
+    T = X.shape[0] if isinstance(X, torch.Tensor) and X.dim() == 3 else 0
+    if T not in (2, 4):
+        raise ValueError("X must hold 2 (DD) or 4 (QD) planes")
     _check_tensor(X, T, (torch.float64,), "X")
     w = int(prec_bits) // 32
     if Y is None:
         Y = torch.empty((2 + w, X.shape[1], X.shape[2]), dtype=torch.int32, device=X.device)
+    _check_tensor(Y, 2 + w, int_dtypes(), "Y", rows=X.shape[1], cols=X.shape[2])
+    require_cuda(X=X, Y=Y)
     check(lib().mpgemm_terms_to_mp(T, X.shape[1] * X.shape[2], ctypes.c_void_p(X.data_ptr()), int(prec_bits),
                                    ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)))
     return Y
@@ -129,10 +127,13 @@ def from_mp(Y, prec_bits, terms, X=None, stream=None):
     4: QD), x_t = RN_53(r), r -= x_t (mpgemm_mp_to_terms)."""
     torch = _torch()
     w = int(prec_bits) // 32
-    dt = (torch.int32, torch.uint32) if hasattr(torch, "uint32") else (torch.int32,)
-    _check_tensor(Y, 2 + w, dt, "Y")
+    if terms not in (2, 4):
+        raise ValueError("terms must be 2 (DD) or 4 (QD)")
+    _check_tensor(Y, 2 + w, int_dtypes(), "Y")
     if X is None:
         X = torch.empty((terms, Y.shape[1], Y.shape[2]), dtype=torch.float64, device=Y.device)
+    _check_tensor(X, terms, (torch.float64,), "X", rows=Y.shape[1], cols=Y.shape[2])
+    require_cuda(Y=Y, X=X)
     check(lib().mpgemm_mp_to_terms(int(terms), Y.shape[1] * Y.shape[2], int(prec_bits), ctypes.c_void_p(Y.data_ptr()),
                                    ctypes.c_void_p(X.data_ptr()), _stream_ptr(stream)))
     return X
@@ -143,19 +144,15 @@ def gemm_split(A, B, C=None, slices=0, digits="e4m3", stream=None):
     digits) or QD (4 planes; e4m3 digits).  slices = 0 picks the default
     (DD: 16 int8 / 22 e4m3; QD: 44)."""
     torch = _torch()
-    T = A.shape[0]
+    T = A.shape[0] if isinstance(A, torch.Tensor) and A.dim() == 3 else 0
     if T not in (2, 4):
         raise ValueError("A must hold 2 (DD) or 4 (QD) planes")
-    _check_tensor(A, T, (torch.float64,), "A")
-    _check_tensor(B, T, (torch.float64,), "B")
-    m, l = A.shape[1], A.shape[2]
-    if B.shape[1] != l:
-        raise ValueError("inner dimensions differ")
-    n = B.shape[2]
+    m, l, n = _operands(A, B, T, (torch.float64,))
     if C is None:
         C = torch.empty((T, m, n), dtype=torch.float64, device=A.device)
     else:
-        _check_tensor(C, T, (torch.float64,), "C")
+        _check_tensor(C, T, (torch.float64,), "C", rows=m, cols=n)
+    require_cuda(A=A, B=B, C=C)
     p = lambda t: ctypes.c_void_p(t.data_ptr())
     if T == 4:
         if digits != "e4m3":
@@ -221,8 +218,8 @@ def select_precision(log2_target, m, l, n, spread=0, max_out=8):
 def exponent_spread(A, B, stream=None):
     """Binade spread of DD operands (mpgemm_dd_exponent_spread), computed on the GPU."""
     torch = _torch()
-    _check_tensor(A, 2, (torch.float64,), "A")
-    _check_tensor(B, 2, (torch.float64,), "B")
+    _operands(A, B, 2, (torch.float64,))
+    require_cuda(A=A, B=B)
     v = ctypes.c_int()
     check(lib().mpgemm_dd_exponent_spread(A.shape[1], A.shape[2], B.shape[2], ctypes.c_void_p(A.data_ptr()),
                                           ctypes.c_void_p(B.data_ptr()), ctypes.byref(v), _stream_ptr(stream)))

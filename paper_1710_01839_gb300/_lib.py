@@ -109,6 +109,40 @@ def lib():
     return _lib
 
 
+def check_planes(t, planes, dtypes, name, rows=None, cols=None):
+    """Refuse anything but a contiguous tensor of shape (planes, rows, cols)
+    and one of `dtypes` (structure only; require_cuda checks the device once
+    every operand's structure has passed, so that each mistake is reported
+    as what it is)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    if t.dim() != 3 or t.shape[0] != planes:
+        raise ValueError(f"{name} must have shape ({planes}, rows, cols), got {tuple(t.shape)}")
+    if (rows is not None and t.shape[1] != rows) or (cols is not None and t.shape[2] != cols):
+        raise ValueError(f"{name} must have shape ({planes}, {rows}, {cols}), got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def require_cuda(**tensors):
+    """Every tensor on the same CUDA device (the library has no CPU path)."""
+    dev = None
+    for name, t in tensors.items():
+        if not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+        if dev is not None and t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, the other operands on {dev}")
+        dev = t.device
+
+
+def int_dtypes():
+    import torch
+    return (torch.int32, torch.uint32) if hasattr(torch, "uint32") else (torch.int32,)
+
+
 def check(rc: int):
     if rc != 0:
         extra = ""

@@ -5,7 +5,7 @@ from __future__ import annotations
 
 import ctypes
 
-from ._lib import KIND, check, lib
+from ._lib import KIND, check, check_planes, int_dtypes, lib, require_cuda
 
 
 class Desc(ctypes.Structure):
@@ -25,9 +25,15 @@ def make_descs(problems, tiles=None, integer_pipe=False):
     {'dd', 'qd', 'mp256'}.  tiles: optional list of tile edges.
     integer_pipe: run the DD and QD problems on the integer pipe (128 / 256-bit
     limbs; engine = 1)."""
+    import torch
     arr = (Desc * len(problems))()
     for i, (fmt, A, B, C) in enumerate(problems):
         kind = KIND["mp" if fmt.startswith("mp") else fmt]
+        planes, dts = {0: (2, (torch.float64,)), 1: (4, (torch.float64,)), 2: (10, int_dtypes())}[kind]
+        check_planes(A, planes, dts, f"A[{i}]")
+        check_planes(B, planes, dts, f"B[{i}]", rows=A.shape[2])
+        check_planes(C, planes, dts, f"C[{i}]", rows=A.shape[1], cols=B.shape[2])
+        require_cuda(**{f"A[{i}]": A, f"B[{i}]": B, f"C[{i}]": C})
         engine = 1 if integer_pipe and kind != 2 else 0
         arr[i] = Desc(kind, 256 if kind == 2 else 0, A.shape[1], A.shape[2], B.shape[2], A.data_ptr(), B.data_ptr(),
                       C.data_ptr(), 0 if tiles is None else int(tiles[i]), engine)

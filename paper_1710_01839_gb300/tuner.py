@@ -5,7 +5,7 @@ from __future__ import annotations
 import ctypes
 import math
 
-from ._lib import KIND, check, lib
+from ._lib import KIND, check, check_planes, int_dtypes, lib, require_cuda
 
 ALGO_NAME = {0: "simple", 1: "block", 2: "strassen", 3: "auto"}
 VERIFY, REMEMBER, SKIP_SIMPLE, QUICK = 1, 2, 4, 8
@@ -53,8 +53,18 @@ def tune(fmt, A, B, C, flags=REMEMBER, prec_bits=0, stream=None):
     """Run mpgemm_tune on device tensors; returns (choice dict, report dict)."""
     import torch
     kind = KIND["mp" if fmt.startswith("mp") else fmt]
+    if kind == KIND["mp"]:
+        if int(prec_bits) <= 0 or int(prec_bits) % 32:
+            raise ValueError("multi-limb tuning needs prec_bits, a positive multiple of 32")
+        planes, dts = 2 + int(prec_bits) // 32, int_dtypes()
+    else:
+        planes, dts = (2 if kind == KIND["dd"] else 4), (torch.float64,)
+    check_planes(A, planes, dts, "A")
     m, l = A.shape[1], A.shape[2]
+    check_planes(B, planes, dts, "B", rows=l)
     n = B.shape[2]
+    check_planes(C, planes, dts, "C", rows=m, cols=n)
+    require_cuda(A=A, B=B, C=C)
     if stream is None:
         stream = torch.cuda.current_stream()
     rep = TuneReport()

@@ -102,7 +102,7 @@ def test_plan_rejects_bad_descriptors():
     import ctypes
     from paper_1710_01839_gb300 import batched
     import torch
-    A = torch.zeros((6, 4, 4), dtype=torch.int32, device="cuda")
+    A = torch.zeros((10, 4, 4), dtype=torch.int32, device="cuda")
     d = batched.make_descs([("mp256", A, A, A)])
     d[0].prec_bits = 128          # the batched kernel only carries 256-bit multi-limb
     h = ctypes.c_void_p()
