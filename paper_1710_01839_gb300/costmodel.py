@@ -45,15 +45,26 @@ def collect(count, seed=1714, max_dim=1024, stream=None):
     return F, T
 
 
+def _rows_of_features(F, count=None):
+    F = _f32(np.atleast_2d(F))
+    if F.ndim != 2 or F.shape[1] != num_features() or (count is not None and F.shape[0] != count):
+        want = f"({'count' if count is None else count}, {num_features()})"
+        raise ValueError(f"feature rows must have shape {want}, got {F.shape}")
+    return F
+
+
 def train(F, T, epochs=200, seed=1714):
-    F, T = _f32(F), _f32(T)
+    T = _f32(T).reshape(-1)
+    F = _rows_of_features(F, len(T))
+    if int(epochs) <= 0:
+        raise ValueError("epochs must be positive")
     loss = np.zeros(epochs, dtype=np.float32)
     check(lib().mpgemm_cost_train(_ptr(F), _ptr(T), len(T), int(epochs), ctypes.c_ulonglong(seed), _ptr(loss)))
     return loss
 
 
 def predict(F):
-    F = _f32(np.atleast_2d(F))
+    F = _rows_of_features(F)
     out = np.zeros(len(F), dtype=np.float32)
     check(lib().mpgemm_cost_predict(_ptr(F), len(F), _ptr(out)))
     return out

@@ -85,3 +85,16 @@ def test_wrong_dtypes_are_refused():
         mpg.gemm_dd([[0.0]], T(2, 3, 4))
     with pytest.raises(TypeError, match="dtype"):
         batched.make_descs([("mp256", T(10, 4, 4), T(10, 4, 4), T(10, 4, 4))])
+
+
+def test_cost_model_feature_rows_are_checked():
+    import numpy as np
+    from paper_1710_01839_gb300 import costmodel as cm
+    nf = cm.num_features()
+    for call in (lambda: cm.train(np.zeros((4, nf - 1)), np.ones(4)),      # columns
+                 lambda: cm.train(np.zeros((4, nf)), np.ones(5)),          # rows against the times
+                 lambda: cm.train(np.zeros((4, nf)), np.ones(4), epochs=0),
+                 lambda: cm.predict(np.zeros((2, nf + 1))),
+                 lambda: cm.predict(np.zeros(nf - 2))):
+        with pytest.raises(ValueError):
+            call()
