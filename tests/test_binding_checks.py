@@ -98,3 +98,17 @@ def test_cost_model_feature_rows_are_checked():
                  lambda: cm.predict(np.zeros(nf - 2))):
         with pytest.raises(ValueError):
             call()
+
+
+def test_device_check_accepts_one_device_and_refuses_two():
+    from paper_1710_01839_gb300._lib import require_cuda
+
+    class OnDevice:                      # stands in for a CUDA tensor (is_cuda, device)
+        def __init__(self, d):
+            self.is_cuda, self.device = True, torch.device(d)
+
+    require_cuda(A=OnDevice("cuda:0"), B=OnDevice("cuda:0"), C=OnDevice("cuda:0"))
+    with pytest.raises(ValueError, match="cuda:1"):
+        require_cuda(A=OnDevice("cuda:0"), B=OnDevice("cuda:1"))
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        require_cuda(A=OnDevice("cuda:0"), B=torch.zeros(1))
