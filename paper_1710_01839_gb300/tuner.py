@@ -39,7 +39,7 @@ def report_dict(r: TuneReport):
     # Section 3's claim: tuning costs 1.6-2.3x more without the prediction.
     # Device time of the procedure with the sampled runs vs. with full runs
     # of the block algorithm for every n_min (the final timings are common).
-    if all(c["full_ms"] is not None for c in cands):
+    if cands and all(c["full_ms"] is not None for c in cands):
         common = sum(v for v in [out["simple_ms"], out["block_ms"]] + list(out["strassen_ms"].values())
                      if v is not None)
         with_pred = sum(c["sample_ms"] for c in cands) + common
