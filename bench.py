@@ -569,15 +569,27 @@ def cpu_baseline(fmt, A, B, algo, n_min, budget_s):
             "sample": f"{rows} of {m} rows of C ({fmt.upper()} {oalgo} algorithm, k ascending), {dt:.1f} s"}
 
 
+def workload_name(fmt, n, prec=256):
+    """The benchmark workload, as both arms report it in `config`."""
+    if fmt == "mp":
+        return (f"{prec}-bit multi-limb square GEMM m=l=n={n}, uniform mantissa bits with the top bit set, "
+                f"exponents U{{-64..64}}")
+    lead = "hi~U[-1,1], lo=hi*2^-53*u" if fmt == "dd" else "x0~U[-1,1], x(i+1)=x(i)*2^-53*u(i)"
+    return f"{fmt.upper()} square GEMM m=l=n={n}, {lead}, exponent spread 2^[-20,20]"
+
+
 # ---------------------------------------------------------------- reference arm (the oracle)
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    A, B = inputs_for(args.fmt, args.n)
+    A, B = inputs_for(args.fmt, args.n, prec=args.prec)
     m, l, n = args.n, args.n, args.n
-    run = oracle.dd_gemm if args.fmt == "dd" else oracle.qd_gemm
+    if args.fmt == "mp":
+        run = lambda A_, B_, **kw: oracle.mp_gemm(A_, B_, prec_bits=args.prec, **kw)
+    else:
+        run = oracle.dd_gemm if args.fmt == "dd" else oracle.qd_gemm
     cores = oracle.threads()
     per_step_rows = max(cores, 1)
     # size each step to about (cpu-seconds / 4) seconds
@@ -586,8 +598,8 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     target = max(1.0, args.cpu_seconds / 4)
     per_step_rows = int(min(m, max(per_step_rows, per_step_rows * target / max(dt, 1e-3))))
-    for _ in range(args.warmup and 1):
-        pass
+    for _ in range(args.warmup):        # untimed steps of the same size
+        run(A, B, algo="block", n_min=args.n_min, rows=(0, per_step_rows))
     times = []
     for s in range(args.steps):
         r0 = (s * per_step_rows) % max(1, m - per_step_rows + 1)
@@ -598,10 +610,10 @@ def run_reference(args, rank, world):
     value = 2.0 * per_step_rows * n * l * len(times) / tot / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": f"{args.fmt.upper()} square GEMM m=l=n={args.n}, exponent spread 2^[-20,20]",
-                       "fmt": args.fmt, "n": args.n, "algo": "block", "n_min": args.n_min},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32" if args.fmt == "mp" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.fmt, args.n, args.prec), "fmt": args.fmt, "n": args.n,
+                       "algo": "block", "n_min": args.n_min},
             "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step_rows} rows of C per step (of {m}), block algorithm"},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -771,9 +783,8 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{fmt.upper()} square GEMM m=l=n={n}, hi~U[-1,1], lo=hi*2^-53*u, "
-                                   f"exponent spread 2^[-20,20]", "fmt": fmt, "n": n, "algo": algo,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32" if fmt == "mp" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(fmt, n, args.prec), "fmt": fmt, "n": n, "algo": algo,
                        "n_min": n_min, "strassen_depth": depth, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}", "tuning_s": round(t_tune, 3)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
