@@ -14,10 +14,11 @@ Printed: one JSON line (rank 0).  `value` is whole-job effective GFLOP/s,
 events on the launching stream with inputs resident in HBM and L2 flushed
 between steps; `e2e` is the same metric with host->device copies of A and B
 and the device->host copy of C inside the timed region.  `roofline` is the
-dominant kernel's FP64-pipe utilisation; `cpu_baseline` is the oracle on
-the host cores over a bounded row sample.
+dominant kernel's FP64-pipe utilisation (for multi-limb formats, its
+integer issue rate); `cpu_baseline` is the oracle on the host cores over a
+bounded row sample.
 
-  python bench.py [--gpus N --steps K --warmup W] [--fmt dd|qd] [--n 2048]
+  python bench.py [--gpus N --steps K --warmup W] [--fmt dd|qd|mp [--prec BITS]] [--n 2048]
   python bench.py --impl reference ...   (the oracle on the host cores)
 """
 
