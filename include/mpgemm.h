@@ -254,7 +254,10 @@ int mpgemm_mp_to_terms(int terms, int64_t count, int prec_bits, const uint32_t* 
  *               format before the persistent kernel and every C in one pass
  *               per format after it (inside the captured graph of
  *               mpgemm_batched_run_graph).
- * mpgemm_batched_plan validates the descriptors, builds the table of work
+ * mpgemm_batched_plan validates the descriptors (MPGEMM_EINVAL for a
+ * negative size, m or n above 65535 * 64, l above 2^31, a NULL matrix of
+ * nonzero size, a bad engine or tile; MPGEMM_EUNSUPPORTED for another
+ * multi-limb width), builds the table of work
  * items (one per C tile, heaviest first) and copies it to the device
  * (cudaMalloc + synchronous copies: plan outside hot loops).  The plan keeps
  * the pointers; the caller keeps the matrices alive.

@@ -199,10 +199,6 @@ static int desc_tile_kind(const mpgemm_desc& d, int tile, int* tk) {
     return MPGEMM_OK;
 }
 
-static size_t desc_elem_bytes(const mpgemm_desc& d) {
-    return d.kind == MPGEMM_KIND_DD ? 16 : d.kind == MPGEMM_KIND_QD ? 32 : 4 * (size_t)(2 + d.prec_bits / 32);
-}
-
 extern "C" {
 
 static void plan_free(mpgemm_plan P) {
@@ -234,7 +230,8 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
     int64_t limb_words = 0;
     for (int i = 0; i < count; i++) {
         const mpgemm_desc& d = descs[i];
-        if (d.m < 0 || d.l < 0 || d.n < 0 || d.m > 65535 * 64 || d.n > 65535 * 64 || d.engine < 0 || d.engine > 1 ||
+        if (d.m < 0 || d.l < 0 || d.n < 0 || d.m > 65535 * 64 || d.n > 65535 * 64 || d.l > (1LL << 31) ||
+            d.engine < 0 || d.engine > 1 ||
             (d.engine == 1 && d.kind == MPGEMM_KIND_MP)) {
             delete P;
             return MPGEMM_EINVAL;
@@ -257,7 +254,7 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
             delete P;
             return rc;
         }
-        if ((d.m * d.l && !d.A) || (d.l * d.n && !d.B) || (d.m * d.n && !d.C)) {
+        if ((d.m > 0 && d.l > 0 && !d.A) || (d.l > 0 && d.n > 0 && !d.B) || (d.m > 0 && d.n > 0 && !d.C)) {
             delete P;
             return MPGEMM_EINVAL;
         }
@@ -298,9 +295,9 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
         dd[i].B = Bm;
         dd[i].C = Cm;
         const int in = is_dd ? 0 : 1, outp = is_dd ? 2 : 3;
-        if (d.m * d.l) jobs[in].push_back(ConvJob{(const double*)d.A, nullptr, Am, d.m * d.l, 0});
-        if (d.l * d.n) jobs[in].push_back(ConvJob{(const double*)d.B, nullptr, Bm, d.l * d.n, 0});
-        if (d.m * d.n) jobs[outp].push_back(ConvJob{nullptr, (double*)d.C, Cm, d.m * d.n, 0});
+        if (d.m > 0 && d.l > 0) jobs[in].push_back(ConvJob{(const double*)d.A, nullptr, Am, d.m * d.l, 0});
+        if (d.l > 0 && d.n > 0) jobs[in].push_back(ConvJob{(const double*)d.B, nullptr, Bm, d.l * d.n, 0});
+        if (d.m > 0 && d.n > 0) jobs[outp].push_back(ConvJob{nullptr, (double*)d.C, Cm, d.m * d.n, 0});
     }
     for (int k = 0; k < 4 && !rc; k++) {
         int64_t first = 0;

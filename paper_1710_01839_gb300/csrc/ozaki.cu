@@ -1035,7 +1035,7 @@ int mpgemm_qd_ozaki(int64_t m, int64_t l, int64_t n, const double* A, const doub
                     void* stream) {
     const int S = num_slices <= 0 ? 44 : num_slices;
     if (m < 0 || l < 0 || n < 0 || S < 1 || S > QD_SMAX) return MPGEMM_EINVAL;
-    if ((m * l && !A) || (l * n && !B) || (m * n && !C)) return MPGEMM_EINVAL;
+    if ((m > 0 && l > 0 && !A) || (l > 0 && n > 0 && !B) || (m > 0 && n > 0 && !C)) return MPGEMM_EINVAL;
     // a slice pair's f32 sum stays below 2^24 (256 l), a level inside int32
     if (l > 65536 || (double)S * 256.0 * (double)l >= 2147483648.0) return MPGEMM_EUNSUPPORTED;
     if (m > 65535 || n > 65535) return MPGEMM_EUNSUPPORTED;
@@ -1080,7 +1080,7 @@ int mpgemm_dd_ozaki_ex(int64_t m, int64_t l, int64_t n, const double* A, const d
     if (digit_kind != 0 && digit_kind != 1) return MPGEMM_EINVAL;
     int S = num_slices <= 0 ? (digit_kind == 1 ? 22 : 16) : num_slices;
     if (m < 0 || l < 0 || n < 0 || S < 1 || S > max_slices(digit_kind)) return MPGEMM_EINVAL;
-    if ((m * l && !A) || (l * n && !B) || (m * n && !C)) return MPGEMM_EINVAL;
+    if ((m > 0 && l > 0 && !A) || (l > 0 && n > 0 && !B) || (m > 0 && n > 0 && !C)) return MPGEMM_EINVAL;
     if (digit_kind == 0) {
         // every level sum must stay inside int32: S pairs * 127^2 * l < 2^31
         if ((double)S * 16129.0 * (double)l >= 2147483648.0) return MPGEMM_EUNSUPPORTED;

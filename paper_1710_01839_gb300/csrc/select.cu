@@ -193,7 +193,7 @@ double mpgemm_precision_log2_bound(int method, int prec_bits, int num_slices, in
 
 int mpgemm_dd_exponent_spread(int64_t m, int64_t l, int64_t n, const double* A, const double* B, int* spread,
                               void* stream) {
-    if (m < 0 || l < 0 || n < 0 || !spread || (m * l && !A) || (l * n && !B)) return MPGEMM_EINVAL;
+    if (m < 0 || l < 0 || n < 0 || !spread || (m > 0 && l > 0 && !A) || (l > 0 && n > 0 && !B)) return MPGEMM_EINVAL;
     if (l > 65535 * 256LL) return MPGEMM_EUNSUPPORTED;   // grid.y of the column pass
     *spread = 0;
     if (m == 0 || l == 0 || n == 0) return MPGEMM_OK;
