@@ -1086,7 +1086,7 @@ static void ozaki_digits_b32(double hi, double lo, int e, int S, int8_t *d, int6
     double xh = ldexp(hi, -(e + 1)), xl = ldexp(lo, -(e + 1));
     int mag[64];
     int neg = (xh < 0) || (xh == 0 && xl < 0);
-    if (S > 64) die("too many slices");
+    if (S < 1 || S > 64) die("slice count out of range");
     for (int s = 0; s < S; s++) {
         double yh = ldexp(xh, 5), yl = ldexp(xl, 5);
         double t = dd_trunc(yh, yl);
@@ -1147,7 +1147,7 @@ static void ozaki_digits_b32_terms(const double *x, int64_t xstride, int T, int 
     wfx_t W;
     int mag[96];
     int neg;
-    if (S > 96) die("too many slices");
+    if (S < 1 || S > 96) die("slice count out of range");
     wfx_zero(&W);
     for (int t = 0; t < T; t++) wfx_add_double(&W, x[(int64_t)t * xstride]);
     neg = wfx_is_neg(&W);
