@@ -10,7 +10,8 @@ The arithmetic lives in ``mpgemm_oracle.c`` (plain C, compiled with
 ``-ffp-contract=off``); this module compiles it (``build()``) and wraps it
 with ctypes.  Parity of every function is pinned by the ``-m "not gpu"``
 tests against exact rational arithmetic, mpmath, closed forms and the
-paper's tables.
+paper's tables; ``tests/test_oracle_mutants.py`` plants mistakes in copies
+of the C source and requires those pins to catch every one.
 """
 
 from __future__ import annotations
