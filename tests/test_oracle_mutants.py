@@ -127,6 +127,15 @@ MUTANTS = {
     "levels start at slice 2": ("for (int s = 1; s <= S; s++)\n        for (int t = 1;", "for (int s = 2; s <= S; s++)\n        for (int t = 1;", 0, 1),
     "int8 recombination: 7 (g - 1)": ("e[i] + f[j] - 7 * g)", "e[i] + f[j] - 7 * (g - 1))", 0, 1),
     "zero has exponent 0 in the row maximum": ("if (x == 0.0) return INT32_MIN;", "if (x == 0.0) return 0;", 0, 1),
+    # third batch: element operations of Eq 3, the final rounding, conversions, the checker
+    "QD difference adds": ("sub ? qd_neg(Y) : Y", "Y", 0, 1),
+    "multi-limb difference adds": ("if (sub) Y = mp_neg(Y);", "(void)sub;", 0, 1),
+    "greedy rounding one term short": ("for (int t = 0; t < nterms; t++) {", "for (int t = 0; t + 1 < nterms; t++) {", 0, 1),
+    "exact rounding: exponent off by one": ("r = ldexp((double)mant, top - 52 - WFX_FRAC);",
+                                           "r = ldexp((double)mant, top - 53 - WFX_FRAC);", 0, 1),
+    "double to multi-limb drops the low word": ("r.m[w - 2] = (uint32_t)top;", "r.m[w - 2] = 0;", 0, 1),
+    "checker reads A's leading term only": ("            for (int p = 0; p < terms; p++)\n                for (int q = 0; q < terms; q++) {",
+                                            "            for (int p = 0; p < 1; p++)\n                for (int q = 0; q < terms; q++) {", 0, 1),
 }
 
 
