@@ -13,7 +13,6 @@ int32/uint32 tensors of shape (2 + w, rows, cols) with p = 32 w bits.
 from __future__ import annotations
 
 import ctypes
-import os
 
 from ._lib import (ALGO, KIND, MpgemmError, check, check_planes, int_dtypes, lib, lib_path,  # noqa: F401
                    require_cuda)

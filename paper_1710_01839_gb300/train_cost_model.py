@@ -16,7 +16,6 @@ and the regret (t_model / t_best - 1) is reported.  Prints one JSON report.
 from __future__ import annotations
 
 import argparse
-import ctypes
 import json
 import os
 import sys

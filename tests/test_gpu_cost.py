@@ -2,12 +2,10 @@
 known function, fits measured timings, round-trips through a file, and
 drives MPGEMM_AUTO to valid configurations."""
 
-import os
-
 import numpy as np
 import pytest
 
-from gpu_util import DD_BOUND, bound_ratio, dev, host, sample_indices
+from gpu_util import DD_BOUND, dev, host, sample_indices
 from paper_1710_01839_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu

@@ -22,7 +22,7 @@ import numpy as np
 import pytest
 
 import oracle
-from exact import F, U, mp_words_to_fraction, value
+from exact import F, mp_words_to_fraction, value
 from paper_1710_01839_gb300 import inputs as I
 
 

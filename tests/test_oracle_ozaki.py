@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import oracle
-from exact import F, greedy, value
+from exact import greedy, value
 from paper_1710_01839_gb300 import inputs as I
 
 

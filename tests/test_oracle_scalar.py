@@ -11,7 +11,6 @@ and mpmath (no GPU).
   carry-out and cancellation constructed explicitly.
 """
 
-import math
 import random
 from fractions import Fraction
 
