@@ -29,7 +29,10 @@ static void* g_na_ptr[64];
 
 // Device address of the scratch array for the current device.  In host code
 // the array's name is only a host-side stand-in, so the address must come
-// from cudaGetSymbolAddress, once per device with that device current.
+// from cudaGetSymbolAddress, once per device with that device current.  It
+// is resolved before a partition's (green) context is pushed, so the cached
+// address is the primary context's array, which every partition of the
+// device can use and which outlives any partition.
 static int noalloc_scratch(void** out) {
     int dev = 0;
     MPG_CUDA(cudaGetDevice(&dev));
@@ -58,6 +61,7 @@ int mpgemm_dd_strassen_noalloc(int64_t m, int64_t l, int64_t n, const double* A,
     cudaStream_t s = (cudaStream_t)stream;
     if (m == 0 || n == 0) return MPGEMM_OK;
     if (l == 0) {   // empty sums: C = 0
+        PartitionScope pscope(s);
         MPG_CUDA(cudaMemsetAsync(C, 0, 2 * sizeof(double) * (size_t)(m * n), s));
         return MPGEMM_OK;
     }
@@ -65,6 +69,7 @@ int mpgemm_dd_strassen_noalloc(int64_t m, int64_t l, int64_t n, const double* A,
     if (bytes > NOALLOC_SCRATCH_BYTES) return MPGEMM_ENOMEM;   // problem too large for the fixed scratch
     void* ws = nullptr;
     if ((rc = noalloc_scratch(&ws))) return rc;
+    PartitionScope pscope(s);   // a partition's stream: its kernels run in its context
     if (n_min <= 0) n_min = default_n_min(MPGEMM_KIND_DD);
     View<const double> a = planes_view(A, m, l), b = planes_view(B, l, n);
     View<double> c = planes_view(C, m, n);

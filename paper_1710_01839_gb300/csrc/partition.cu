@@ -89,6 +89,10 @@ int device_sms() {
 // The runtime issues work into the context current on the calling thread,
 // so a call on a partition's stream makes the partition's context current
 // for its duration.
+// Addresses of the library's __device__ words are resolved (and cached per
+// device) in the context that was current before the push, the device's
+// primary context: a green context's own module copy would go away with the
+// partition, and a cached address of it would then dangle.
 PartitionScope::PartitionScope(cudaStream_t s) {
     CUcontext c = nullptr;
     {
@@ -97,6 +101,7 @@ PartitionScope::PartitionScope(cudaStream_t s) {
         if (it == g_parts.end()) return;
         c = it->second.ctx;
     }
+    (void)device_status_ptr();
     pushed_ = green().push(c) == CUDA_SUCCESS;
 }
 
