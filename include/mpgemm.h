@@ -360,12 +360,36 @@ int mpgemm_set_workspace(void* dev_ptr, size_t bytes);
  * m, l, n, SMs of the stream) and used by MPGEMM_AUTO on streams with as
  * many SMs.  Synchronous; returns MPGEMM_OK or an
  * error status.
+ *
+ * Persistent tuning cache: mpgemm_tune_cache_open(path) opens (creating it
+ * if needed) an append-only file of JSON lines, one record per timing and
+ * one per finished choice, keyed by (device name, library version, SMs,
+ * kind, prec_bits, m, l, n).  While it is open, mpgemm_tune takes every
+ * timing it finds there instead of measuring it and appends (and flushes)
+ * every new timing as soon as it is measured, so a run that was killed
+ * resumes where it stopped; a shape with a finished choice in the file is
+ * answered from it without timing (unless MPGEMM_TUNE_FORCE), and every
+ * choice read from the file is remembered for MPGEMM_AUTO, which consults
+ * remembered choices before the cost model.  Lines that do not parse are
+ * skipped; records of another device name, SM count or version are not
+ * used.  Several processes may append to one file.  path NULL closes the
+ * cache (remembered choices stay).  MPGEMM_EINVAL if the file cannot be
+ * opened or read.  mpgemm_tune_cache_stats: records loaded at open (choices,
+ * timings), lines skipped, records of other devices or versions; returns 1
+ * while a cache is open, else 0.
+ *
+ * mpgemm_tune_set_timer(fn, ctx): while fn is not NULL, mpgemm_tune asks fn
+ * for each timing (milliseconds; a negative value makes mpgemm_tune return
+ * MPGEMM_ECUDA) instead of launching kernels: the procedure can then run on
+ * recorded or simulated timings, without a GPU.  NULL restores timing on
+ * the device.
  * ------------------------------------------------------------------------- */
 enum {
     MPGEMM_TUNE_VERIFY = 1,       /* also time the full block GEMM for every n_min */
     MPGEMM_TUNE_REMEMBER = 2,     /* store the choice for MPGEMM_AUTO               */
     MPGEMM_TUNE_SKIP_SIMPLE = 4,  /* do not time the simple algorithm               */
-    MPGEMM_TUNE_QUICK = 8         /* one timed run per configuration                */
+    MPGEMM_TUNE_QUICK = 8,        /* one timed run per configuration                */
+    MPGEMM_TUNE_FORCE = 16        /* tune again although the cache has a choice     */
 };
 typedef struct {
     int algo, n_min, depth;      /* the choice                                    */
@@ -379,11 +403,18 @@ typedef struct {
     double simple_ms, block_ms;  /* NaN when not run                              */
     double strassen_ms[4];       /* [d], d = 1..3; NaN when not run               */
     double tuning_ms;            /* wall time of this call                        */
+    int measured;                /* timings taken by this call (not from the cache) */
+    int from_cache;              /* 1: the choice came from the tuning cache      */
 } mpgemm_tune_report;
 int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const void* A, const void* B, void* C,
                 int flags, void* stream, mpgemm_tune_report* report);
 /* Forget every remembered choice. */
 int mpgemm_tune_forget(void);
+int mpgemm_tune_cache_open(const char* path);
+int mpgemm_tune_cache_stats(int* choices, int* measurements, int* skipped_lines, int* foreign_records);
+typedef double (*mpgemm_timer_fn)(void* ctx, int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo,
+                                  int n_min, int depth, int64_t rows, int reps);
+int mpgemm_tune_set_timer(mpgemm_timer_fn fn, void* ctx);
 /* The (algo, n_min, depth) MPGEMM_AUTO would use for this problem on the
    whole device. */
 int mpgemm_auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int* algo, int* n_min,
@@ -528,6 +559,28 @@ int mpgemm_profile(int enable);
 int mpgemm_profile_read(double* total_ms, int* launches);
 /* Library version as 10000*major + 100*minor + patch. */
 int mpgemm_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Peak-rate microbenchmarks (measurement; the paper has no counterpart): the
+ * denominators of the rooflines the benchmark reports, measured on the GPU
+ * at hand.  mpgemm_peak_run launches `iters` iterations of one instruction
+ * loop on every SM of the stream's partition (asynchronous on `stream`) and
+ * stores in *ops the operations that launch performs; the caller times the
+ * launch with events on the same stream.
+ *   MPGEMM_PEAK_TC_E4M3: tcgen05.mma kind::f8f6f4, M 128 x N 256 x K 32,
+ *     e4m3 operands resident in shared memory, f32 accumulator in tensor
+ *     memory; iters = rounds of 4 MMAs per SM (1..2^22); ops = 2 M N K per
+ *     MMA (flops).
+ *   MPGEMM_PEAK_MMA_S8: mma.sync m16n8k32 s8 on register operands; ops =
+ *     2 x 16 x 8 x 32 per instruction (integer operations).
+ *   MPGEMM_PEAK_DFMA: FP64 fused multiply-adds; ops = one per DFMA (the
+ *     FP64 operations of the DD / QD rooflines).
+ *   MPGEMM_PEAK_IMAD: 32-bit integer multiply-adds; ops = one per IMAD
+ *     (thread instructions).
+ * iters 1..2^32; MPGEMM_EINVAL for a bad kind, count or NULL ops.  The
+ * tcgen05 loop's only wait is bounded (a timeout sets the status word). */
+enum { MPGEMM_PEAK_TC_E4M3 = 0, MPGEMM_PEAK_MMA_S8 = 1, MPGEMM_PEAK_DFMA = 2, MPGEMM_PEAK_IMAD = 3 };
+int mpgemm_peak_run(int kind, int64_t iters, double* ops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -45,6 +45,7 @@ SIGNATURES = {
     "mpgemm_strerror": (ctypes.c_char_p, [_I]),
     "mpgemm_last_cuda_error": (_I, []),
     "mpgemm_version": (_I, []),
+    "mpgemm_peak_run": (_I, [_I, _I64, _P, _P]),
     "mpgemm_profile": (_I, [_I]),
     "mpgemm_cost_num_features": (_I, []),
     "mpgemm_cost_choice": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _P, _P]),
@@ -75,6 +76,9 @@ SIGNATURES = {
     "mpgemm_ozaki_split_terms": (_I, [_I, _I, _I64, _I64, _P, _I, _P, _P, _P]),
     "mpgemm_tune": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _I, _P, _P]),
     "mpgemm_tune_forget": (_I, []),
+    "mpgemm_tune_cache_open": (_I, [ctypes.c_char_p]),
+    "mpgemm_tune_cache_stats": (_I, [_P, _P, _P, _P]),
+    "mpgemm_tune_set_timer": (_I, [_P, _P]),
     "mpgemm_auto_choice": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P]),
     "mpgemm_predict_time": (ctypes.c_double, [ctypes.c_double, _I64, _I64]),
     "mpgemm_sample_rows": (_I64, [_I, _I64, _I64, _I, _I]),

@@ -411,15 +411,6 @@ __device__ __forceinline__ void mma_s8(int (&c)[4], const unsigned (&a)[4], unsi
         : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-// FP8 e4m3 x e4m3 -> f32: exact on the digit products (integers <= 256) as
-// long as every partial sum stays below 2^24 in magnitude.
-__device__ __forceinline__ void mma_e4m3(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64, OZ_STAGES = 4, OZ_THREADS = 256;
 constexpr int OZ_STAGE_BYTES = (OZ_BM + OZ_BN) * OZ_BK;   // 16 KB
@@ -431,11 +422,9 @@ __device__ __forceinline__ int swz(int r, int c) { return r * OZ_BK + ((c ^ ((r 
 
 // One CTA = one 128 x 128 tile of one level g; levels are issued heaviest
 // first (level g concatenates g - 1 slice pairs along K).  8 warps as 2 x 4,
-// warp tile 64 x 32 = 4 x 4 mma tiles; 4-stage cp.async pipeline.
-// F8 = false: int8 digits, s32 accumulators.  F8 = true: e4m3 digit codes,
-// f32 accumulators emptied into s32 after every slice pair (a pair's sum is
-// at most 256 l < 2^24, so every f32 partial sum is an exact integer).
-template <bool F8>
+// warp tile 64 x 32 = 4 x 4 mma tiles; 4-stage cp.async pipeline; int8
+// digits, s32 accumulators.  (FP8 digits run on the tcgen05 kernel of
+// tc_levels.cu.)
 __global__ void __launch_bounds__(OZ_THREADS) k_ozaki_levels(int64_t m, int64_t n, int64_t lp, int S,
                                                              const unsigned char* DA, const unsigned char* DB,
                                                              int* Lv, unsigned tiles_m, unsigned tiles_n) {
@@ -470,21 +459,12 @@ __global__ void __launch_bounds__(OZ_THREADS) k_ozaki_levels(int64_t m, int64_t 
     };
 
     int acc[4][4][4];
-    float facc[F8 ? 4 : 1][F8 ? 4 : 1][4];
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
         for (int b = 0; b < 4; b++)
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[a][b][c] = 0;
-    if constexpr (F8) {
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int b = 0; b < 4; b++)
-#pragma unroll
-                for (int c = 0; c < 4; c++) facc[a][b][c] = 0.f;
-    }
 
 #pragma unroll
     for (int st = 0; st < OZ_STAGES - 1; st++) {
@@ -516,25 +496,8 @@ __global__ void __launch_bounds__(OZ_THREADS) k_ozaki_levels(int64_t m, int64_t 
 #pragma unroll
             for (int mi = 0; mi < 4; mi++)
 #pragma unroll
-                for (int ni = 0; ni < 4; ni++) {
-                    if constexpr (F8)
-                        mma_e4m3(facc[mi][ni], a[mi], b[ni >> 1][(ni & 1) * 2], b[ni >> 1][(ni & 1) * 2 + 1]);
-                    else
-                        mma_s8(acc[mi][ni], a[mi], b[ni >> 1][(ni & 1) * 2], b[ni >> 1][(ni & 1) * 2 + 1]);
-                }
-        }
-        if constexpr (F8) {
-            if (it % ksteps == ksteps - 1) {   // end of a slice pair: move the exact f32 sums to s32
-#pragma unroll
-                for (int a = 0; a < 4; a++)
-#pragma unroll
-                    for (int b = 0; b < 4; b++)
-#pragma unroll
-                        for (int c = 0; c < 4; c++) {
-                            acc[a][b][c] += __float2int_rn(facc[a][b][c]);
-                            facc[a][b][c] = 0.f;
-                        }
-            }
+                for (int ni = 0; ni < 4; ni++)
+                    mma_s8(acc[mi][ni], a[mi], b[ni >> 1][(ni & 1) * 2], b[ni >> 1][(ni & 1) * 2 + 1]);
         }
     }
     cp_async_wait<0>();
@@ -952,14 +915,13 @@ int ozaki_split(int kind, int by_col, int64_t rows, int64_t cols, const double* 
     return check_launch();
 }
 
-template <bool F8>
 static int levels_launch(int64_t m, int64_t n, int64_t lp, int S, const void* DA, const void* DB, int* Lv,
                          cudaStream_t s) {
     // set on every call: the current context may be an SM partition's (partition.cu)
-    MPG_CUDA(cudaFuncSetAttribute(k_ozaki_levels<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    MPG_CUDA(cudaFuncSetAttribute(k_ozaki_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     unsigned tm = ceil_div(m, OZ_BM), tn = ceil_div(n, OZ_BN);
     ProfScope ps(s);
-    k_ozaki_levels<F8><<<tm * tn * (unsigned)S, OZ_THREADS, OZ_SMEM, s>>>(
+    k_ozaki_levels<<<tm * tn * (unsigned)S, OZ_THREADS, OZ_SMEM, s>>>(
         m, n, lp, S, (const unsigned char*)DA, (const unsigned char*)DB, Lv, tm, tn);
     return check_launch();
 }
@@ -967,7 +929,7 @@ static int levels_launch(int64_t m, int64_t n, int64_t lp, int S, const void* DA
 int ozaki_levels(int kind, int64_t m, int64_t n, int64_t lp, int S, const void* DA, const void* DB, int* Lv,
                  cudaStream_t s) {
     // FP8 digits: tcgen05 (kind::f8f6f4) kernel; int8 digits: mma.sync s8 (no tcgen05 integer MMA on sm_103a)
-    return kind == 1 ? tc_levels(m, n, lp, S, DA, DB, Lv, s) : levels_launch<false>(m, n, lp, S, DA, DB, Lv, s);
+    return kind == 1 ? tc_levels(m, n, lp, S, DA, DB, Lv, s) : levels_launch(m, n, lp, S, DA, DB, Lv, s);
 }
 
 int ozaki_recombine(int kind, int64_t m, int64_t n, int S, const int* Lv, const int* e, const int* f, double* C,

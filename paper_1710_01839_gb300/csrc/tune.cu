@@ -40,6 +40,16 @@ static std::map<Key, Choice> g_table;
 bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out,
                        float* pred_ms = nullptr);
 
+void remember_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice ch) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_table[Key(kind, prec_bits, m, l, n, sms)] = ch;
+}
+
+// Replacement timer (mpgemm_tune_set_timer): simulated or recorded timings.
+static std::mutex g_timer_mu;
+static mpgemm_timer_fn g_timer = nullptr;
+static void* g_timer_ctx = nullptr;
+
 int auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice* out) {
     {
         std::lock_guard<std::mutex> lk(g_tmu);
@@ -141,6 +151,32 @@ int time_it(const Problem& P, int algo, int n_min, int depth, int64_t rows, int 
     return MPGEMM_OK;
 }
 
+// One timing of the procedure: from the open tuning cache when it holds
+// this measurement, else from the replacement timer if one is set, else
+// timed on the device; new timings are appended to the cache at once.
+int measure(const Problem& P, const TuneKey& key, int algo, int n_min, int depth, int64_t rows, int reps, double* ms,
+            int* measured) {
+    if (tune_cache_lookup_meas(key, algo, n_min, depth, rows, reps, ms)) return MPGEMM_OK;
+    mpgemm_timer_fn fn;
+    void* ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_timer_mu);
+        fn = g_timer;
+        ctx = g_timer_ctx;
+    }
+    if (fn) {
+        const double t = fn(ctx, P.kind, P.prec_bits, P.m, P.l, P.n, algo, n_min, depth, rows, reps);
+        if (!(t >= 0.0)) return MPGEMM_ECUDA;
+        *ms = t;
+    } else {
+        int rc = time_it(P, algo, n_min, depth, rows, reps, ms);
+        if (rc) return rc;
+    }
+    (*measured)++;
+    tune_cache_append_meas(key, algo, n_min, depth, rows, reps, *ms);
+    return MPGEMM_OK;
+}
+
 }  // namespace
 
 }  // namespace mpg
@@ -173,6 +209,18 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
     const int sms = stream_sms(P.s);   // the partition's SMs when the stream has one
     const int reps = (flags & MPGEMM_TUNE_QUICK) ? 1 : 3;
     memset(rep, 0, sizeof *rep);
+    const TuneKey key{kind, P.prec_bits, m, l, n, sms};
+    auto wall_ms = [&] {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    };
+    if (!(flags & MPGEMM_TUNE_FORCE) && tune_cache_lookup_choice(key, rep)) {
+        rep->from_cache = 1;
+        rep->measured = 0;
+        remember_choice(kind, P.prec_bits, m, l, n, sms, Choice{rep->algo, rep->n_min, rep->depth});
+        rep->tuning_ms = wall_ms();
+        return MPGEMM_OK;
+    }
+    int measured = 0;
     static const int cands[] = {16, 32, 64, 128, 256, 512};
     constexpr int NC = (int)(sizeof cands / sizeof cands[0]);
     int best = -1;
@@ -181,7 +229,7 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
         int nm = cands[c];
         int64_t r = mpgemm_sample_rows(kind, m, n, nm, sms);
         double ms = 0;
-        int rc = time_it(P, MPGEMM_BLOCK, nm, 0, r, reps, &ms);
+        int rc = measure(P, key, MPGEMM_BLOCK, nm, 0, r, reps, &ms, &measured);
         if (rc) return rc;
         rep->cand_n_min[c] = nm;
         rep->cand_rows[c] = r;
@@ -189,7 +237,7 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
         rep->cand_pred_ms[c] = ms * rounds(kind, m, n, nm, sms) / rounds(kind, r, n, nm, sms);
         rep->cand_full_ms[c] = NAN;
         if (flags & MPGEMM_TUNE_VERIFY) {
-            rc = time_it(P, MPGEMM_BLOCK, nm, 0, m, reps, &rep->cand_full_ms[c]);
+            rc = measure(P, key, MPGEMM_BLOCK, nm, 0, m, reps, &rep->cand_full_ms[c], &measured);
             if (rc) return rc;
         }
         if (best < 0 || rep->cand_pred_ms[c] < best_pred) {
@@ -202,10 +250,10 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
     int rc;
     rep->simple_ms = NAN;
     if (!(flags & MPGEMM_TUNE_SKIP_SIMPLE)) {
-        rc = time_it(P, MPGEMM_SIMPLE, nm, 0, m, reps, &rep->simple_ms);
+        rc = measure(P, key, MPGEMM_SIMPLE, nm, 0, m, reps, &rep->simple_ms, &measured);
         if (rc) return rc;
     }
-    rc = time_it(P, MPGEMM_BLOCK, nm, 0, m, reps, &rep->block_ms);
+    rc = measure(P, key, MPGEMM_BLOCK, nm, 0, m, reps, &rep->block_ms, &measured);
     if (rc) return rc;
     Choice ch{MPGEMM_BLOCK, nm, 0};
     double best_ms = rep->block_ms;
@@ -219,7 +267,7 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
         if (strassen_extended(m, d) >> d < 16 || strassen_extended(l, d) >> d < 16 ||
             strassen_extended(n, d) >> d < 16)
             continue;
-        rc = time_it(P, MPGEMM_STRASSEN, nm, d, m, reps, &rep->strassen_ms[d]);
+        rc = measure(P, key, MPGEMM_STRASSEN, nm, d, m, reps, &rep->strassen_ms[d], &measured);
         if (rc) return rc;
         if (rep->strassen_ms[d] < best_ms) {
             ch = Choice{MPGEMM_STRASSEN, nm, d};
@@ -230,11 +278,18 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
     rep->n_min = ch.n_min;
     rep->depth = ch.depth;
     rep->best_ms = best_ms;
-    if (flags & MPGEMM_TUNE_REMEMBER) {
-        std::lock_guard<std::mutex> lk(g_tmu);
-        g_table[Key(kind, P.prec_bits, m, l, n, sms)] = ch;
-    }
-    rep->tuning_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    rep->measured = measured;
+    rep->from_cache = 0;
+    if (flags & MPGEMM_TUNE_REMEMBER) remember_choice(kind, P.prec_bits, m, l, n, sms, ch);
+    tune_cache_append_choice(key, rep);
+    rep->tuning_ms = wall_ms();
+    return MPGEMM_OK;
+}
+
+int mpgemm_tune_set_timer(mpgemm_timer_fn fn, void* ctx) {
+    std::lock_guard<std::mutex> lk(g_timer_mu);
+    g_timer = fn;
+    g_timer_ctx = fn ? ctx : nullptr;
     return MPGEMM_OK;
 }
 

@@ -4,11 +4,12 @@ from __future__ import annotations
 
 import ctypes
 import math
+import os
 
 from ._lib import KIND, check, check_planes, int_dtypes, lib, require_cuda
 
 ALGO_NAME = {0: "simple", 1: "block", 2: "strassen", 3: "auto"}
-VERIFY, REMEMBER, SKIP_SIMPLE, QUICK = 1, 2, 4, 8
+VERIFY, REMEMBER, SKIP_SIMPLE, QUICK, FORCE = 1, 2, 4, 8, 16
 
 
 class TuneReport(ctypes.Structure):
@@ -18,7 +19,7 @@ class TuneReport(ctypes.Structure):
                 ("cand_sample_ms", ctypes.c_double * 8), ("cand_pred_ms", ctypes.c_double * 8),
                 ("cand_full_ms", ctypes.c_double * 8), ("simple_ms", ctypes.c_double),
                 ("block_ms", ctypes.c_double), ("strassen_ms", ctypes.c_double * 4),
-                ("tuning_ms", ctypes.c_double)]
+                ("tuning_ms", ctypes.c_double), ("measured", ctypes.c_int), ("from_cache", ctypes.c_int)]
 
 
 def _nan(x):
@@ -35,7 +36,8 @@ def report_dict(r: TuneReport):
                       "rel_diff": (abs(pred - full) / full) if full else None})
     out = {"algo": ALGO_NAME[r.algo], "n_min": r.n_min, "depth": r.depth, "best_ms": r.best_ms,
            "candidates": cands, "simple_ms": _nan(r.simple_ms), "block_ms": r.block_ms,
-           "strassen_ms": {d: _nan(r.strassen_ms[d]) for d in (1, 2, 3)}, "tuning_ms": r.tuning_ms}
+           "strassen_ms": {d: _nan(r.strassen_ms[d]) for d in (1, 2, 3)}, "tuning_ms": r.tuning_ms,
+           "measured": r.measured, "from_cache": bool(r.from_cache)}
     # Section 3's claim: tuning costs 1.6-2.3x more without the prediction.
     # Device time of the procedure with the sampled runs vs. with full runs
     # of the block algorithm for every n_min (the final timings are common).
@@ -82,3 +84,50 @@ def predict_time(t_sample, m, rows):
 
 def sample_rows(fmt, m, n, n_min, num_sms=152):
     return int(lib().mpgemm_sample_rows(KIND[fmt], int(m), int(n), int(n_min), int(num_sms)))
+
+
+# ctypes prototype of mpgemm_timer_fn
+TIMER_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                            ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_int64, ctypes.c_int)
+
+
+def cache_open(path):
+    """Open (or with None close) the persistent tuning cache file."""
+    check(lib().mpgemm_tune_cache_open(None if path is None else os.fsencode(path)))
+
+
+def cache_stats():
+    c, mm, s, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    is_open = lib().mpgemm_tune_cache_stats(ctypes.byref(c), ctypes.byref(mm), ctypes.byref(s), ctypes.byref(f))
+    return {"open": bool(is_open), "choices": c.value, "measurements": mm.value, "skipped_lines": s.value,
+            "foreign_records": f.value}
+
+
+_timer_ref = None
+
+
+def set_timer(fn):
+    """Replace device timing by fn(kind, prec_bits, m, l, n, algo, n_min,
+    depth, rows, reps) -> ms (None restores device timing)."""
+    global _timer_ref
+    if fn is None:
+        _timer_ref = None
+        check(lib().mpgemm_tune_set_timer(None, None))
+        return
+    cb = TIMER_FN(lambda ctx, *a: float(fn(*a)))
+    _timer_ref = cb
+    check(lib().mpgemm_tune_set_timer(ctypes.cast(cb, ctypes.c_void_p), None))
+
+
+def tune_shape(fmt, m, l, n, flags=REMEMBER, prec_bits=0):
+    """mpgemm_tune on placeholder operand pointers, for use with set_timer
+    (nothing is launched while a timer is set); returns the report dict."""
+    if _timer_ref is None:
+        raise RuntimeError("tune_shape needs a timer (set_timer): it passes no operands")
+    kind = KIND["mp" if fmt.startswith("mp") else fmt]
+    rep = TuneReport()
+    fake = ctypes.c_void_p(256)
+    check(lib().mpgemm_tune(kind, int(prec_bits), int(m), int(l), int(n), fake, fake, fake, int(flags), None,
+                            ctypes.byref(rep)))
+    return report_dict(rep)

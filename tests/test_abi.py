@@ -65,3 +65,9 @@ def test_host_only_calls(built):
     assert L.mpgemm_selftest_wait_timeout(0, None) == -1
     assert L.mpgemm_selftest_wait_timeout(5000, None) == -1
     assert L.mpgemm_stream_sms is not None
+    import ctypes
+    ops = ctypes.c_double()
+    assert L.mpgemm_peak_run(7, 1, ctypes.byref(ops), None) == -1           # unknown kind
+    assert L.mpgemm_peak_run(0, 0, ctypes.byref(ops), None) == -1           # no iterations
+    assert L.mpgemm_peak_run(0, (1 << 22) + 1, ctypes.byref(ops), None) == -1   # tcgen05 loop too long
+    assert L.mpgemm_peak_run(2, 1, None, None) == -1                        # no ops output
