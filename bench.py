@@ -84,27 +84,106 @@ def parse():
     ap.add_argument("--ozaki-fp8-slices", type=int, default=22)
     ap.add_argument("--qd-split-n", type=int, default=1024)
     ap.add_argument("--qd-split-slices", type=int, default=44)
+    ap.add_argument("--extra-reps", type=int, default=5, help="timed calls (median) of each comparison arm")
+    ap.add_argument("--no-peaks", action="store_true", help="use the fallback roofline peaks")
     return ap.parse_args()
 
 
-# mma.sync m16n8k32 s8 throughput measured on this machine's GB300 by a loop of
-# independent register-operand mma.sync instructions on all SMs (no tcgen05
-# integer MMA exists on sm_103a).
-INT8_MMA_PEAK_TOPS = 151.2
+# Roofline denominators.  Every run measures them itself with the library's
+# peak microbenchmarks (mpgemm_peak_run, paper_1710_01839_gb300/peaks.py):
+# tcgen05 e4m3 MMA, mma.sync s8, FP64 DFMA and 32-bit IMAD, each over about
+# a second on every SM, with the SM clock sampled meanwhile.  The constants
+# below are used only when that measurement is unavailable.
+PEAKS = {}
+PEAK_DESC = {"tc_e4m3": "tcgen05.mma kind::f8f6f4 M128 N256 K32, operands resident in shared memory",
+             "mma_s8": "mma.sync m16n8k32 s8 on register operands",
+             "dfma": "FP64 DFMA, independent chains, every SM full",
+             "imad": "mad.lo.u32, independent chains, every SM full"}
 
 
-def _fp8_tensor_peak():
-    """Dense FP8 tensor peak for tcgen05 kind::f8f6f4: the measured cuBLAS bf16
-    burst figure (MEASURED_PEAKS.json) x the nominal FP8 / BF16 ratio of 2;
-    fallback 1.9 PFLOP/s bf16 x 2."""
+def _bf16x2_tflops():
+    """The measured cuBLAS bf16 burst (MEASURED_PEAKS.json) x the nominal
+    FP8 / BF16 ratio of 2 (fallback 1.9 PFLOP/s bf16)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return 2.0 * float(json.load(f)["bf16_tflops"]), "measured bf16 burst x 2 (nominal FP8/BF16)"
+            return 2.0 * float(json.load(f)["bf16_tflops"])
     except (OSError, KeyError, ValueError):
-        return 2.0 * 1900.0, "fallback 1.9 PFLOP/s bf16 x 2"
+        return 2.0 * 1900.0
 
 
-E4M3_PEAK_TFLOPS, E4M3_PEAK_NOTE = _fp8_tensor_peak()
+FALLBACK = {"tc_e4m3": (_bf16x2_tflops(), "fallback: measured cuBLAS bf16 burst x 2 (nominal FP8/BF16)"),
+            "mma_s8": (151.2, "fallback: an earlier mma.sync s8 loop on this pool's GB300"),
+            "dfma": (FP64_PEAK_GOPS, "fallback: derived 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"),
+            "imad": (19.0, "fallback: an earlier IMAD loop on this pool's GB300")}
+
+
+def peak(kind):
+    """(value, note): this run's measured rate of `kind`, else the fallback."""
+    p = PEAKS.get(kind)
+    if p:
+        return p["value"], (f"measured in this run: {PEAK_DESC[kind]}, {p['value']:.4g} {p['unit']} "
+                            f"at median SM clock {p['sm_mhz_median']} MHz")
+    return FALLBACK[kind]
+
+
+def measure_peaks():
+    try:
+        from paper_1710_01839_gb300 import peaks
+        PEAKS.update(peaks.measure_all(1.0))
+    except Exception as e:   # reported, and the fallbacks are used
+        PEAKS.clear()
+        PEAKS["error"] = repr(e)
+
+
+def timed_calls(fn, stream, reps=5, flush=None):
+    """Median event time per call and median average duration of the
+    dominant kernel's launches (the library's profiling brackets) over
+    `reps` calls, after one untimed call; L2 flushed before every call."""
+    import ctypes
+    import torch
+    import paper_1710_01839_gb300 as mpg
+    L = mpg.lib()
+    fn()
+    torch.cuda.synchronize()
+    ts, ks = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        L.mpgemm_profile(1)
+        L.mpgemm_profile_read(None, None)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, kl = ctypes.c_double(), ctypes.c_int()
+        L.mpgemm_profile_read(ctypes.byref(kms), ctypes.byref(kl))
+        L.mpgemm_profile(0)
+        ts.append(e0.elapsed_time(e1))
+        ks.append(kms.value / max(kl.value, 1))
+    return float(np.median(ts)), float(np.median(ks))
+
+
+def _flush_buffer():
+    import torch
+    return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+
+def mp_roofline(bits, macs, k_ms, kname):
+    """Multi-limb kernel: algorithmic IMAD fraction (2 w^2 32-bit IMADs per
+    multiply-accumulate, the schoolbook limb products, against the measured
+    IMAD rate) and the issue fraction of the instructions it executes."""
+    w = bits // 32
+    imad_peak, imad_note = peak("imad")
+    alg = macs * 2.0 * w * w / (k_ms * 1e-3) / 1e12
+    ipm = MP_INSTR_PER_MAC.get(bits)
+    issue = macs * ipm / 32.0 / (k_ms * 1e-3) / 1e9 if ipm else None
+    return {"bound": "alu", "unit": "T IMAD/s (algorithmic: 2 w^2 per MAC)", "achieved": alg, "peak": imad_peak,
+            "frac": alg / imad_peak, "frac_algorithmic": alg / imad_peak, "peak_note": imad_note,
+            "issue": {"unit": "G warp-instructions/s", "achieved": issue, "peak": ISSUE_PEAK_GWIPS,
+                      "frac": issue / ISSUE_PEAK_GWIPS if issue else None, "instructions_per_mac": ipm,
+                      "peak_note": "derived: 1 warp-instruction/clk per SM sub-partition x 4 x 152 SMs x 2070 MHz"},
+            "kernel": f"{kname}, {macs:.3g} MACs x 2 w^2 = {2 * w * w} IMAD", "kernel_ms": k_ms}
 
 
 def split_precision_extra(args, stream):
@@ -123,42 +202,30 @@ def split_precision_extra(args, stream):
     L = mpg.lib()
     sp = ctypes.c_void_p(int(stream.cuda_stream))
     p = lambda t: ctypes.c_void_p(t.data_ptr())
+    flush = _flush_buffer()
+    reps = args.extra_reps
 
     def oz():
         rc = L.mpgemm_dd_ozaki(n, n, n, p(Ad), p(Bd), p(Cd), S, sp)
         if rc:
             raise RuntimeError(mpg.strerror(rc))
 
-    def timed(fn, steps):
-        fn()
-        torch.cuda.synchronize()
-        L.mpgemm_profile(1)
-        L.mpgemm_profile_read(None, None)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        kms, kl = ctypes.c_double(), ctypes.c_int()
-        L.mpgemm_profile_read(ctypes.byref(kms), ctypes.byref(kl))
-        L.mpgemm_profile(0)
-        return e0.elapsed_time(e1) / steps, kms.value / max(kl.value, 1)
-
     flops = 2.0 * n ** 3
-    oz_ms, oz_kms = timed(oz, 3)
+    oz_ms, oz_kms = timed_calls(oz, stream, reps, flush)
     pairs = S * (S + 1) // 2
     lp = (n + 127) // 128 * 128
     int_ops = 2.0 * n * n * lp * pairs
+    s8_peak, s8_note = peak("mma_s8")
     out = {"workload": f"DD m=l=n={n}, rows/cols scaled 2^U{{-16..16}}, S={S} int8 slices",
+           "timing": f"median of {reps} calls, L2 flushed (256 MB write) before each",
            "ozaki_gflops": flops / (oz_ms * 1e-3) / 1e9, "ozaki_ms": oz_ms,
            "roofline": {"bound": "tensor", "unit": "TOPS (int8 mma.sync)",
-                        "achieved": int_ops / (oz_kms * 1e-3) / 1e12, "peak": INT8_MMA_PEAK_TOPS,
-                        "frac": int_ops / (oz_kms * 1e-3) / 1e12 / INT8_MMA_PEAK_TOPS,
+                        "achieved": int_ops / (oz_kms * 1e-3) / 1e12, "peak": s8_peak, "peak_note": s8_note,
+                        "frac": int_ops / (oz_kms * 1e-3) / 1e12 / s8_peak,
                         "kernel": f"k_ozaki_levels, {pairs} slice pairs x 2 n^2 l int8 ops", "kernel_ms": oz_kms,
                         "kernel_share": oz_kms / oz_ms}}
     for name, algo, nm, d in (("plain_dd_block", "block", 64, 0), ("plain_dd_strassen3", "strassen", 32, 3)):
-        ms, _ = timed(lambda: mpg.gemm_dd(Ad, Bd, Cd, algo=algo, n_min=nm, depth=d), 1)
+        ms, _ = timed_calls(lambda: mpg.gemm_dd(Ad, Bd, Cd, algo=algo, n_min=nm, depth=d), stream, reps, flush)
         out[name + "_gflops"] = flops / (ms * 1e-3) / 1e9
         out[name + "_ms"] = ms
     out["speedup_vs_best_plain_dd"] = min(out["plain_dd_block_ms"], out["plain_dd_strassen3_ms"]) / oz_ms
@@ -170,18 +237,23 @@ def split_precision_extra(args, stream):
         if rc:
             raise RuntimeError(mpg.strerror(rc))
 
-    f8_ms, f8_kms = timed(oz8, 3)
+    f8_ms, f8_kms = timed_calls(oz8, stream, reps, flush)
     pairs8 = S8 * (S8 + 1) // 2
     f8_flops = 2.0 * n * n * lp * pairs8
     out["fp8"] = {"slices": S8, "gflops": flops / (f8_ms * 1e-3) / 1e9, "ms": f8_ms,
                   "speedup_vs_int8": oz_ms / f8_ms,
                   "speedup_vs_best_plain_dd": min(out["plain_dd_block_ms"], out["plain_dd_strassen3_ms"]) / f8_ms,
-                  "roofline": {"bound": "tensor", "unit": "TFLOP/s (e4m3)",
-                               "achieved": f8_flops / (f8_kms * 1e-3) / 1e12, "peak": E4M3_PEAK_TFLOPS, "peak_note": E4M3_PEAK_NOTE,
-                               "frac": f8_flops / (f8_kms * 1e-3) / 1e12 / E4M3_PEAK_TFLOPS,
-                               "kernel": f"k_levels_tc (tcgen05 kind::f8f6f4), {pairs8} slice pairs x 2 n^2 l",
-                               "kernel_ms": f8_kms, "kernel_share": f8_kms / f8_ms}}
+                  "roofline": tc_roofline(f8_flops, f8_kms, f"k_levels_tc (tcgen05 kind::f8f6f4), {pairs8} slice "
+                                                            "pairs x 2 n^2 l", f8_ms)}
     return out
+
+
+def tc_roofline(flops, k_ms, kname, call_ms):
+    tc_peak, tc_note = peak("tc_e4m3")
+    ach = flops / (k_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "unit": "TFLOP/s (e4m3)", "achieved": ach, "peak": tc_peak, "peak_note": tc_note,
+            "frac": ach / tc_peak, "frac_vs_bf16_burst_x2": ach / _bf16x2_tflops(), "kernel": kname,
+            "kernel_ms": k_ms, "kernel_share": k_ms / call_ms}
 
 
 def mlp_arm(fmt, Ad, Bd, Cd, gemm, tuned_ms, prec_bits):
@@ -221,44 +293,27 @@ def qd_split_extra(args, stream):
     against the plain FP64-pipe QD kernels on the same QD inputs (the large
     QD workload: m = l = n = qd_split_n, per-element exponents 2^U{-20..20}).
     Accuracy (<= 4 l 2^-208 |A||B|) is asserted by the parity tests."""
-    import ctypes
     import torch
     import paper_1710_01839_gb300 as mpg
     n, S = args.qd_split_n, args.qd_split_slices
     A, B = inputs_for("qd", n)
     Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     Cd = torch.empty_like(Ad)
-    L = mpg.lib()
-
-    def timed(fn, steps):
-        fn()
-        torch.cuda.synchronize()
-        L.mpgemm_profile(1)
-        L.mpgemm_profile_read(None, None)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        kms, kl = ctypes.c_double(), ctypes.c_int()
-        L.mpgemm_profile_read(ctypes.byref(kms), ctypes.byref(kl))
-        L.mpgemm_profile(0)
-        return e0.elapsed_time(e1) / steps, kms.value / max(kl.value, 1)
+    flush = _flush_buffer()
+    reps = max(args.extra_reps, 10)
 
     flops = 2.0 * n ** 3
-    sp_ms, sp_kms = timed(lambda: mpg.gemm_split(Ad, Bd, Cd, slices=S), 10)
+    sp_ms, sp_kms = timed_calls(lambda: mpg.gemm_split(Ad, Bd, Cd, slices=S), stream, reps, flush)
     lp = (n + 127) // 128 * 128
     tc_flops = 2.0 * n * n * lp * S * (S + 1) / 2
     out = {"workload": f"QD m=l=n={n}, per-element exponents 2^U{{-20..20}}, S={S} e4m3 slices",
+           "timing": f"median of {reps} calls, L2 flushed (256 MB write) before each",
            "qd_split_gflops": flops / (sp_ms * 1e-3) / 1e9, "qd_split_ms": sp_ms,
-           "roofline": {"bound": "tensor", "unit": "TFLOP/s (e4m3)",
-                        "achieved": tc_flops / (sp_kms * 1e-3) / 1e12, "peak": E4M3_PEAK_TFLOPS,
-                        "peak_note": E4M3_PEAK_NOTE, "frac": tc_flops / (sp_kms * 1e-3) / 1e12 / E4M3_PEAK_TFLOPS,
-                        "kernel": f"k_levels_tc (tcgen05 kind::f8f6f4), {S * (S + 1) // 2} slice pairs x 2 n^2 l",
-                        "kernel_ms": sp_kms, "kernel_share": sp_kms / sp_ms}}
+           "roofline": tc_roofline(tc_flops, sp_kms, f"k_levels_tc (tcgen05 kind::f8f6f4), {S * (S + 1) // 2} "
+                                                     "slice pairs x 2 n^2 l", sp_ms)}
     for name, algo, nm, d in (("plain_qd_block", "block", 32, 0), ("plain_qd_strassen3", "strassen", 16, 3)):
-        ms, _ = timed(lambda: mpg.gemm_qd(Ad, Bd, Cd, algo=algo, n_min=nm, depth=d), 1)
+        ms, _ = timed_calls(lambda: mpg.gemm_qd(Ad, Bd, Cd, algo=algo, n_min=nm, depth=d), stream, args.extra_reps,
+                            flush)
         out[name + "_gflops"] = flops / (ms * 1e-3) / 1e9
         out[name + "_ms"] = ms
     out["speedup_vs_best_plain_qd"] = min(out["plain_qd_block_ms"], out["plain_qd_strassen3_ms"]) / sp_ms
@@ -272,12 +327,11 @@ def via_mp_extra(args, stream, fp64_dd_gflops):
     come from the Section 3 tuner run on the converted operands, and each
     timed call includes both conversions.  Accuracy (far inside the DD / QD
     bounds; bit-identical to the oracle) is asserted by the parity tests."""
-    import ctypes
     import torch
     import paper_1710_01839_gb300 as mpg
     from paper_1710_01839_gb300 import tuner
-    L = mpg.lib()
     out = {}
+    flush = _flush_buffer()
     for fmt, n, bits, ref in (("dd", args.n, 128, fp64_dd_gflops), ("qd", args.qd_split_n, 256, None)):
         A, B = inputs_for(fmt, n)
         Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
@@ -291,39 +345,20 @@ def via_mp_extra(args, stream, fp64_dd_gflops):
         del Am, Bm, Cm
         algo, n_min, depth = choice["algo"], choice["n_min"], choice["depth"]
         call = lambda: mpg.gemm_via_mp(Ad, Bd, bits, Cd, algo=algo, n_min=n_min, depth=depth, stream=stream)
-        call()
-        torch.cuda.synchronize()
-        reps = 3
-        L.mpgemm_profile(1)
-        L.mpgemm_profile_read(None, None)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            call()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        kms, kl = ctypes.c_double(), ctypes.c_int()
-        L.mpgemm_profile_read(ctypes.byref(kms), ctypes.byref(kl))
-        L.mpgemm_profile(0)
-        ms = e0.elapsed_time(e1) / reps
+        ms, k_ms = timed_calls(call, stream, args.extra_reps, flush)
         status = mpg.stream_status()
         if status != 0:
             raise RuntimeError(f"device status {status}: {mpg.strerror(status)}")
         flops = 2.0 * n ** 3
         leaf = (n + (1 << depth) - 1) >> depth if algo == "strassen" else n
         macs = (7 ** depth if algo == "strassen" else 1) * float(leaf) ** 3
-        k_ms = kms.value / max(kl.value, 1)
-        ipm = MP_INSTR_PER_MAC[bits]
-        achieved = macs * ipm / 32.0 / (k_ms * 1e-3) / 1e9
+        roof = mp_roofline(bits, macs, k_ms, f"{bits}-bit {'leaf ' if algo == 'strassen' else ''}GEMM")
+        roof["kernel_share"] = k_ms / ms
         out[fmt] = {"workload": f"{fmt.upper()} m=l=n={n} (inputs of the FP64-pipe {fmt.upper()} GEMM), "
                                 f"{bits}-bit limbs", "prec_bits": bits,
+                    "timing": f"median of {args.extra_reps} calls, L2 flushed before each",
                     "choice": {"algo": algo, "n_min": n_min, "depth": depth}, "tuning_s": round(t_tune, 3),
-                    "gflops": flops / (ms * 1e-3) / 1e9, "ms": ms,
-                    "roofline": {"bound": "alu", "unit": "G warp-instructions/s (issue)", "achieved": achieved,
-                                 "peak": ISSUE_PEAK_GWIPS, "frac": achieved / ISSUE_PEAK_GWIPS,
-                                 "kernel": f"{bits}-bit {'leaf ' if algo == 'strassen' else ''}GEMM, {macs:.3g} MACs "
-                                           f"x {ipm} thread-instructions", "kernel_ms": k_ms,
-                                 "kernel_share": k_ms / ms}}
+                    "gflops": flops / (ms * 1e-3) / 1e9, "ms": ms, "roofline": roof}
         if ref is not None:
             out[fmt]["speedup_vs_fp64_pipe"] = out[fmt]["gflops"] / ref
     return out
@@ -541,17 +576,54 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(fmt, A, B, algo, n_min, budget_s):
-    """The oracle (as it stands) on the host cores over a row sample of the
-    same workload: rate = 2 * rows * n * l / t."""
+# The oracle's time for one whole Strassen product must stay a bounded
+# sample of CPU work; above this estimate the CPU legs fall back to a row
+# sample of the block algorithm (Strassen cannot be row-sampled).
+STRASSEN_ORACLE_MAX_S = 20.0
+
+
+def _oracle_run(fmt, A):
     import oracle
-    m, l, n = A.shape[1], A.shape[2], B.shape[2]
     if fmt == "mp":
         pb = 32 * (A.shape[0] - 2)
-        run = lambda A_, B_, **kw: oracle.mp_gemm(A_, B_, prec_bits=pb, **kw)
-    else:
-        run = oracle.dd_gemm if fmt == "dd" else oracle.qd_gemm
+        return lambda A_, B_, **kw: oracle.mp_gemm(A_, B_, prec_bits=pb, **kw)
+    return oracle.dd_gemm if fmt == "dd" else oracle.qd_gemm
+
+
+def _oracle_strassen_fits(run, A, B, n_min, depth):
+    """Estimate the oracle's whole Strassen product as 8x its time for the
+    same algorithm on the leading half-size problem (the work scales as
+    m l n)."""
+    m, l, n = A.shape[1], A.shape[2], B.shape[2]
+    h = lambda x: max(2 ** depth, x // 2)
+    Ah = np.ascontiguousarray(A[:, :h(m), :h(l)])
+    Bh = np.ascontiguousarray(B[:, :h(l), :h(n)])
+    t0 = time.perf_counter()
+    run(Ah, Bh, algo="strassen", n_min=n_min, depth=depth)
+    dt = time.perf_counter() - t0
+    est = dt * (m * l * n) / (h(m) * h(l) * h(n))
+    return est <= STRASSEN_ORACLE_MAX_S, est
+
+
+def cpu_baseline(fmt, A, B, algo, n_min, depth, budget_s):
+    """The oracle (as it stands) on the host cores, on the configuration the
+    GPU step runs: for Strassen the whole product at the same depth (when it
+    fits the CPU budget), else a row sample of the block algorithm:
+    rate = 2 * rows * n * l / t."""
+    import oracle
+    m, l, n = A.shape[1], A.shape[2], B.shape[2]
+    run = _oracle_run(fmt, A)
     cores = oracle.threads()
+    if algo == "strassen" and depth > 0:
+        fits, est = _oracle_strassen_fits(run, A, B, n_min, depth)
+        if fits:
+            t0 = time.perf_counter()
+            run(A, B, algo="strassen", n_min=n_min, depth=depth)
+            dt = time.perf_counter() - t0
+            return {"value": 2.0 * m * n * l / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                    "same_config": True,
+                    "sample": f"the whole product ({fmt.upper()} Strassen depth {depth}, leaves block n_min {n_min}, "
+                              f"the GPU step's configuration), {dt:.1f} s"}
     oalgo = "block" if algo in ("block", "strassen", "tuned") else "simple"
     rows = max(1, cores)
     t0 = time.perf_counter()
@@ -566,7 +638,7 @@ def cpu_baseline(fmt, A, B, algo, n_min, budget_s):
         dt = time.perf_counter() - t0
         rows = more
     gflops = 2.0 * rows * n * l / dt / 1e9
-    return {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+    return {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "same_config": oalgo == algo,
             "sample": f"{rows} of {m} rows of C ({fmt.upper()} {oalgo} algorithm, k ascending), {dt:.1f} s"}
 
 
@@ -581,44 +653,75 @@ def workload_name(fmt, n, prec=256):
 
 # ---------------------------------------------------------------- reference arm (the oracle)
 
+# The configuration the reference arm times: what the Section 3 tuner picks
+# on GB300 at the benchmark's sizes (Strassen depth 3 in every measured
+# format; the oracle's n_min only blocks its CPU loops, the arithmetic of
+# every c_ij is the same at any n_min).
+REF_ALGO, REF_N_MIN, REF_DEPTH = "strassen", 32, 3
+REF_ARM_MAX_S = 300.0   # whole products for every step only while the run stays within this estimate
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
     A, B = inputs_for(args.fmt, args.n, prec=args.prec)
     m, l, n = args.n, args.n, args.n
-    if args.fmt == "mp":
-        run = lambda A_, B_, **kw: oracle.mp_gemm(A_, B_, prec_bits=args.prec, **kw)
-    else:
-        run = oracle.dd_gemm if args.fmt == "dd" else oracle.qd_gemm
+    run = _oracle_run(args.fmt, A)
     cores = oracle.threads()
+    if args.algo == "tuned":
+        algo, n_min, depth = REF_ALGO, REF_N_MIN, REF_DEPTH
+    else:
+        algo, n_min, depth = args.algo, args.n_min, args.depth if args.algo == "strassen" else 0
+    if algo == "strassen" and depth > 0:
+        fits, est = _oracle_strassen_fits(run, A, B, n_min, depth)
+        if fits and est * (args.steps + args.warmup) <= REF_ARM_MAX_S:
+            for _ in range(args.warmup):
+                run(A, B, algo="strassen", n_min=n_min, depth=depth)
+            times = []
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                run(A, B, algo="strassen", n_min=n_min, depth=depth)
+                times.append(time.perf_counter() - t0)
+            tot = sum(times)
+            value = 2.0 * m * n * l * len(times) / tot / 1e9
+            sample = (f"the whole product per step ({args.fmt.upper()} Strassen depth {depth}, leaves block "
+                      f"n_min {n_min})")
+            print(json.dumps(_reference_line(args, world, value, tot, len(times), cores, sample,
+                                             {"algo": algo, "n_min": n_min, "strassen_depth": depth})), flush=True)
+            return
+    algo, depth = "block", 0
     per_step_rows = max(cores, 1)
     # size each step to about (cpu-seconds / 4) seconds
     t0 = time.perf_counter()
-    run(A, B, algo="block", n_min=args.n_min, rows=(0, per_step_rows))
+    run(A, B, algo="block", n_min=n_min, rows=(0, per_step_rows))
     dt = time.perf_counter() - t0
     target = max(1.0, args.cpu_seconds / 4)
     per_step_rows = int(min(m, max(per_step_rows, per_step_rows * target / max(dt, 1e-3))))
     for _ in range(args.warmup):        # untimed steps of the same size
-        run(A, B, algo="block", n_min=args.n_min, rows=(0, per_step_rows))
+        run(A, B, algo="block", n_min=n_min, rows=(0, per_step_rows))
     times = []
     for s in range(args.steps):
         r0 = (s * per_step_rows) % max(1, m - per_step_rows + 1)
         t0 = time.perf_counter()
-        run(A, B, algo="block", n_min=args.n_min, rows=(r0, r0 + per_step_rows))
+        run(A, B, algo="block", n_min=n_min, rows=(r0, r0 + per_step_rows))
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = 2.0 * per_step_rows * n * l * len(times) / tot / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+    sample = f"{per_step_rows} rows of C per step (of {m}), block algorithm"
+    print(json.dumps(_reference_line(args, world, value, tot, len(times), cores, sample,
+                                     {"algo": "block", "n_min": n_min, "strassen_depth": 0})), flush=True)
+
+
+def _reference_line(args, world, value, tot_s, steps, cores, sample, cfg):
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32" if args.fmt == "mp" else "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.fmt, args.n, args.prec), "fmt": args.fmt, "n": args.n,
-                       "algo": "block", "n_min": args.n_min},
-            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step_rows} rows of C per step (of {m}), block algorithm"},
+            "config": dict({"workload": workload_name(args.fmt, args.n, args.prec), "fmt": args.fmt, "n": args.n},
+                           **cfg),
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- our arm
@@ -708,30 +811,6 @@ def main():
     flops_step = 2.0 * m * n * l
     value = whole_job_rate(world, flops_step, args.steps, t_max)
 
-    # -------- dominant kernel roofline (FP64 pipe)
-    leaf = n >> depth if algo == "strassen" else n
-    leaf_count = 7 ** depth if algo == "strassen" else 1
-    macs_per_launch = leaf_count * float(leaf) ** 3
-    k_avg_ms = kms.value / max(kl.value, 1)
-    kname = (f"{fmt} {'leaf ' if algo == 'strassen' else ''}{'simple' if algo == 'simple' else 'block'} GEMM")
-    if is_mp:
-        # integer pipe: issue-bound; instructions per MAC come from ncu (see profiles/)
-        ipm = MP_INSTR_PER_MAC.get(args.prec)
-        achieved = macs_per_launch * ipm / 32.0 / (k_avg_ms * 1e-3) / 1e9 if ipm else None
-        roofline = {"bound": "alu", "unit": "G warp-instructions/s (issue)", "achieved": achieved,
-                    "peak": ISSUE_PEAK_GWIPS, "frac": achieved / ISSUE_PEAK_GWIPS if achieved else None,
-                    "traffic": None, "kernel": f"{kname}, {macs_per_launch:.3g} MACs x {ipm} thread-instructions",
-                    "kernel_ms": k_avg_ms, "kernel_share_of_step": kms.value / tot_ms if tot_ms else None,
-                    "peak_note": "derived: 1 warp-instruction/clk per SM sub-partition x 4 x 152 SMs x 2070 MHz"}
-    else:
-        achieved = macs_per_launch * FP64_OPS_PER_MAC[fmt] / (k_avg_ms * 1e-3) / 1e9
-        traffic = TRAFFIC_BYTES.get((fmt, n, algo, n_min, depth))
-        roofline = {"bound": "alu", "unit": "Gop/s (FP64 pipe)", "achieved": achieved, "peak": FP64_PEAK_GOPS,
-                    "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic,
-                    "kernel": f"{kname}, {macs_per_launch:.3g} MACs x {FP64_OPS_PER_MAC[fmt]} FP64 ops per launch",
-                    "kernel_ms": k_avg_ms, "kernel_share_of_step": kms.value / tot_ms if tot_ms else None,
-                    "peak_note": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"}
-
     # -------- end to end through host buffers
     e2e = None
     if not args.no_e2e:
@@ -760,6 +839,31 @@ def main():
                "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(Ch.numel() * Ch.element_size()),
                "ms_per_step": e_ms / args.steps}
 
+    # -------- roofline denominators, measured on this GPU (after the timed region)
+    if not args.no_peaks:
+        measure_peaks()
+
+    # -------- dominant kernel roofline
+    leaf = (n + (1 << depth) - 1) >> depth if algo == "strassen" else n
+    leaf_count = 7 ** depth if algo == "strassen" else 1
+    macs_per_launch = leaf_count * float(leaf) ** 3
+    k_avg_ms = kms.value / max(kl.value, 1)
+    kname = (f"{fmt} {'leaf ' if algo == 'strassen' else ''}{'simple' if algo == 'simple' else 'block'} GEMM")
+    if is_mp:
+        roofline = mp_roofline(args.prec, macs_per_launch, k_avg_ms, kname)
+        roofline["traffic"] = None
+    else:
+        fp64_peak, fp64_note = peak("dfma")
+        achieved = macs_per_launch * FP64_OPS_PER_MAC[fmt] / (k_avg_ms * 1e-3) / 1e9
+        traffic = TRAFFIC_BYTES.get((fmt, n, algo, n_min, depth))
+        roofline = {"bound": "alu", "unit": "Gop/s (FP64 pipe)", "achieved": achieved, "peak": fp64_peak,
+                    "frac": achieved / fp64_peak, "traffic": traffic,
+                    "kernel": f"{kname}, {macs_per_launch:.3g} MACs x {FP64_OPS_PER_MAC[fmt]} FP64 ops per launch",
+                    "kernel_ms": k_avg_ms, "peak_note": fp64_note,
+                    "frac_vs_derived_peak": achieved / FP64_PEAK_GOPS,
+                    "derived_peak_note": "2 FP64 ops/clk/SM x 152 SMs x 2070 MHz = 629 G op/s"}
+    roofline["kernel_share_of_step"] = kms.value / tot_ms if tot_ms else None
+
     extras = bextra = qextra = vextra = pextra = None
     if not args.no_extras and fmt == "dd":
         extras = split_precision_extra(args, stream)
@@ -780,7 +884,7 @@ def main():
 
     cpu = None
     if not args.no_cpu and world == 1:
-        cpu = cpu_baseline(fmt, A, B, algo, n_min if n_min > 0 else 64, args.cpu_seconds)
+        cpu = cpu_baseline(fmt, A, B, algo, n_min if n_min > 0 else 64, depth, args.cpu_seconds)
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -790,6 +894,29 @@ def main():
                        "parallelism": f"replicas x{world}", "tuning_s": round(t_tune, 3)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
+    summary = {}
+    if extras is not None:
+        f8 = extras["fp8"]
+        summary["dd_split_4096"] = {
+            "int8_gflops": extras["ozaki_gflops"], "fp8_gflops": f8["gflops"],
+            "plain_dd_block_gflops": extras["plain_dd_block_gflops"],
+            "plain_dd_strassen3_gflops": extras["plain_dd_strassen3_gflops"],
+            "fp8_speedup_vs_best_plain_dd": f8["speedup_vs_best_plain_dd"],
+            "int8_speedup_vs_best_plain_dd": extras["speedup_vs_best_plain_dd"],
+            "fp8_level_kernel_frac": f8["roofline"]["frac"], "int8_level_kernel_frac": extras["roofline"]["frac"]}
+    if qextra is not None:
+        summary["qd_split_1024"] = {"fp8_gflops": qextra["qd_split_gflops"],
+                                    "speedup_vs_best_plain_qd": qextra["speedup_vs_best_plain_qd"],
+                                    "level_kernel_frac": qextra["roofline"]["frac"]}
+    if vextra is not None:
+        summary["integer_pipe"] = {k: {"gflops": v["gflops"], "frac_algorithmic": v["roofline"]["frac_algorithmic"]}
+                                   for k, v in vextra.items()}
+    if PEAKS:
+        summary["peaks"] = {k: (round(v["value"], 4) if isinstance(v, dict) else v) for k, v in PEAKS.items()}
+    if summary:
+        line["summary"] = summary
+    if PEAKS:
+        line["peaks"] = PEAKS
     if tune_info is not None:
         line["tuning"] = tune_info
     if extras is not None:
