@@ -48,12 +48,14 @@ __device__ __forceinline__ int clamp_exp(long long e, unsigned& status) {
 
 // Shift the N-limb value v right by d >= 0 bits; OR of the dropped bits goes
 // into sticky.  Limbs move by powers of two (selects, no dynamic register
-// indexing), then a funnel shift.
-template <int N>
+// indexing), then a funnel shift.  QMAX: the caller guarantees that at most
+// QMAX whole limbs move (d < 32 (QMAX + 1)), which drops the barrel stages
+// above it.
+template <int N, int QMAX = N>
 __device__ __forceinline__ void shr_sticky(uint32_t (&v)[N], int d, uint32_t& sticky) {
     int q = d >> 5;
 #pragma unroll
-    for (int st = 1; st < N; st <<= 1) {
+    for (int st = 1; st < N && st <= QMAX; st <<= 1) {
         bool on = (q & st) != 0;
         uint32_t drop = 0;
 #pragma unroll
@@ -65,7 +67,7 @@ __device__ __forceinline__ void shr_sticky(uint32_t (&v)[N], int d, uint32_t& st
             v[i] = on ? nv : v[i];
         }
     }
-    if (q >= N) {   // everything shifted out
+    if (QMAX >= N && q >= N) {   // everything shifted out
         uint32_t all = 0;
 #pragma unroll
         for (int i = 0; i < N; i++) all |= v[i];
@@ -319,30 +321,31 @@ __device__ __forceinline__ void mp_mul(const MPV<W>& x, const MPV<W>& y, MPV<W>&
 }
 
 // r = RN_p(a + b).
+//
+// One code path for every exponent difference d and both signs, so that the
+// threads of a warp (whose operands differ in d and sign at random in a
+// GEMM) do not diverge: d is clamped to p + 2 (from there on |y| is below a
+// quarter of x's ulp and the frame below rounds to x, which is RN(x + y) for
+// every larger d as well), y is aligned by the barrel shifter, and the sum
+// and the difference are one carry chain X + (Y xor mask) + carry-in.
 template <int W>
 __device__ __forceinline__ void mp_add(const MPV<W>& a, const MPV<W>& b, MPV<W>& r, unsigned& status) {
     constexpr int p = 32 * W;
     constexpr int N = W + 2;   // [guard, M (W limbs), carry]
-    if (a.f & 2u) {
-        if (b.f & 2u) {
-            mp_set_zero(r, a.f & b.f & 1u);
+    if ((a.f | b.f) & 2u) {    // a zero operand (rare)
+        if (a.f & 2u) {
+            if (b.f & 2u) mp_set_zero(r, a.f & b.f & 1u);
+            else r = b;
         } else {
-            r = b;
+            r = a;
         }
-        return;
-    }
-    if (b.f & 2u) {
-        r = a;
         return;
     }
     const bool sw = b.e > a.e;
     const int ex = sw ? b.e : a.e;
     const unsigned sx = (sw ? b.f : a.f) & 1u, sy = (sw ? a.f : b.f) & 1u;
-    const long long d = (long long)ex - (sw ? a.e : b.e);
-    if (d >= p + 2) {          // |y| below half an ulp of every neighbour of x
-        r = sw ? b : a;
-        return;
-    }
+    const long long dl = (long long)ex - (sw ? a.e : b.e);
+    const int d = dl < p + 2 ? (int)dl : p + 2;
     uint32_t X[N], Y[N];
     X[0] = 0u;
     Y[0] = 0u;
@@ -354,35 +357,27 @@ MP_UNROLL
     X[N - 1] = 0u;
     Y[N - 1] = 0u;
     uint32_t sticky = 0u;
-    if (d < 32) {
-        // the common GEMM case: no limb moves, and the guard limb keeps
-        // every shifted-out bit (no sticky)
-        const int r = (int)d;
-MP_UNROLL
-        for (int i = 0; i < N - 1; i++) Y[i] = __funnelshift_r(Y[i], Y[i + 1], r);
-        Y[N - 1] >>= r;
-    } else {
-        shr_sticky<N>(Y, (int)d, sticky);
-    }
+    shr_sticky<N, W>(Y, d, sticky);   // d <= p + 2: at most W limbs move
     const bool stk = sticky != 0u;
-    uint32_t S[N];
+    // sum, or X - Y - stk (the dropped part of y then leaves a positive
+    // remainder below S's last bit, kept as sticky) as X + ~Y + 1 - stk
+    const bool sub = sx != sy;
+    const uint32_t mask = sub ? 0xFFFFFFFFu : 0u;
+    uint32_t S[N], dummy, cout;
+    asm volatile("add.cc.u32 %0, %1, 0xFFFFFFFF;" : "=r"(dummy) : "r"((sub && !stk) ? 1u : 0u));
+#pragma unroll
+    for (int i = 0; i < N; i++) asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(S[i]) : "r"(X[i]), "r"(Y[i] ^ mask));
+    asm volatile("addc.u32 %0, 0, 0;" : "=r"(cout));
     unsigned sign = sx;
-    if (sx == sy) {
-        add_limbs<N>(X, Y, S);
-    } else {
-        // S = X - Y - stk; the dropped part of y then leaves a positive
-        // remainder below S's last bit, kept as sticky.
-        const uint32_t br = sub_limbs<N>(X, Y, stk ? 1u : 0u, S);
-        if (br) {   // only when d == 0 and My > Mx (exact): negate
-            uint32_t c = 1u;
+    if (sub && !cout) {   // a borrow: only when d == 0 and My > Mx (exact): negate
+        uint32_t c = 1u;
 MP_UNROLL
-            for (int i = 0; i < N; i++) {
-                uint32_t v = ~S[i] + c;
-                c = (c && v == 0u) ? 1u : 0u;
-                S[i] = v;
-            }
-            sign = sy;
+        for (int i = 0; i < N; i++) {
+            uint32_t v = ~S[i] + c;
+            c = (c && v == 0u) ? 1u : 0u;
+            S[i] = v;
         }
+        sign = sy;
     }
     uint32_t nz = 0u;
 MP_UNROLL

@@ -187,11 +187,12 @@ __device__ __forceinline__ void mp_mac(MPV<W>& c, const MPV<W>& a, const MPV<W>&
 constexpr int MP_STREAM_LIMBS = 16;
 
 // Shared memory (words) of one mp_block_tile: two KT-deep panels of 16
-// elements, each [exponent, flags, (pad, pad,) W limbs]; streamed operands
-// put their limbs at a 16-byte boundary.
+// elements, each [exponent, flags, (pad, pad,) W limbs]; from 4 limbs up the
+// limbs start at a 16-byte boundary, so an element is read with 128-bit
+// loads (register operands) or streamed four limbs per load.
 template <int W>
 __host__ __device__ constexpr int mp_tile_limb_offset() {
-    return W >= MP_STREAM_LIMBS ? 4 : 2;
+    return W >= 4 ? 4 : 2;
 }
 template <int W, int KT>
 __host__ __device__ constexpr int mp_tile_words() {
@@ -236,6 +237,27 @@ __device__ __forceinline__ void mp_block_tile(int64_t m, int64_t l, int64_t n, c
             MPV<W> t;
             if constexpr (W >= MP_STREAM_LIMBS) {
                 mp_mul_acc<W>((int)ar[0], ar[1], SmemLimbs{ar + OFF}, (int)br[0], br[1], SmemLimbs{br + OFF}, t, st);
+            } else if constexpr (W % 4 == 0) {
+                MPV<W> a, b;
+                const uint2 ha = *reinterpret_cast<const uint2*>(ar), hb = *reinterpret_cast<const uint2*>(br);
+                a.e = (int)ha.x;
+                a.f = ha.y;
+                b.e = (int)hb.x;
+                b.f = hb.y;
+MP_UNROLL
+                for (int w = 0; w < W; w += 4) {
+                    const uint4 va = *reinterpret_cast<const uint4*>(ar + OFF + w);
+                    const uint4 vb = *reinterpret_cast<const uint4*>(br + OFF + w);
+                    a.m[w] = va.x;
+                    a.m[w + 1] = va.y;
+                    a.m[w + 2] = va.z;
+                    a.m[w + 3] = va.w;
+                    b.m[w] = vb.x;
+                    b.m[w + 1] = vb.y;
+                    b.m[w + 2] = vb.z;
+                    b.m[w + 3] = vb.w;
+                }
+                mp_mul<W>(a, b, t, st);
             } else {
                 MPV<W> a, b;
                 a.e = (int)ar[0];
