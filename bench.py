@@ -97,7 +97,7 @@ def parse():
 PEAKS = {}
 PEAK_DESC = {"tc_e4m3": "tcgen05.mma kind::f8f6f4 M128 N256 K32, operands resident in shared memory",
              "mma_s8": "mma.sync m16n8k32 s8 on register operands",
-             "dfma": "FP64 DFMA, independent chains, every SM full",
+             "fp64": "the fastest of FP64 DFMA, DADD and DMUL loops (independent chains, every SM full)",
              "imad": "mad.lo.u32, independent chains, every SM full"}
 
 
@@ -113,7 +113,7 @@ def _bf16x2_tflops():
 
 FALLBACK = {"tc_e4m3": (_bf16x2_tflops(), "fallback: measured cuBLAS bf16 burst x 2 (nominal FP8/BF16)"),
             "mma_s8": (151.2, "fallback: an earlier mma.sync s8 loop on this pool's GB300"),
-            "dfma": (FP64_PEAK_GOPS, "fallback: derived 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"),
+            "fp64": (FP64_PEAK_GOPS, "fallback: derived 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"),
             "imad": (19.0, "fallback: an earlier IMAD loop on this pool's GB300")}
 
 
@@ -121,7 +121,8 @@ def peak(kind):
     """(value, note): this run's measured rate of `kind`, else the fallback."""
     p = PEAKS.get(kind)
     if p:
-        return p["value"], (f"measured in this run: {PEAK_DESC[kind]}, {p['value']:.4g} {p['unit']} "
+        src = f" ({p['source']})" if "source" in p else ""
+        return p["value"], (f"measured in this run: {PEAK_DESC[kind]}{src}, {p['value']:.4g} {p['unit']} "
                             f"at median SM clock {p['sm_mhz_median']} MHz")
     return FALLBACK[kind]
 
@@ -591,17 +592,26 @@ def _oracle_run(fmt, A):
 
 
 def _oracle_strassen_fits(run, A, B, n_min, depth):
-    """Estimate the oracle's whole Strassen product as 8x its time for the
-    same algorithm on the leading half-size problem (the work scales as
-    m l n)."""
+    """Estimate the oracle's time for the whole Strassen product: first from
+    a few rows of its block algorithm (cheap, pessimistic up to about 3x:
+    leaf work 7^d (n / 2^d)^3 of n^3); if that is within 4x of the limit,
+    from the same Strassen call on the leading half-size problem (x 8)."""
+    import oracle
     m, l, n = A.shape[1], A.shape[2], B.shape[2]
+    rows = max(1, oracle.threads())
+    t0 = time.perf_counter()
+    run(A, B, algo="block", n_min=n_min, rows=(0, min(rows, m)))
+    est = (time.perf_counter() - t0) * m / min(rows, m) * (7.0 / 8.0) ** depth
+    if est <= STRASSEN_ORACLE_MAX_S:
+        return True, est
+    if est > 4 * STRASSEN_ORACLE_MAX_S:
+        return False, est
     h = lambda x: max(2 ** depth, x // 2)
     Ah = np.ascontiguousarray(A[:, :h(m), :h(l)])
     Bh = np.ascontiguousarray(B[:, :h(l), :h(n)])
     t0 = time.perf_counter()
     run(Ah, Bh, algo="strassen", n_min=n_min, depth=depth)
-    dt = time.perf_counter() - t0
-    est = dt * (m * l * n) / (h(m) * h(l) * h(n))
+    est = (time.perf_counter() - t0) * (m * l * n) / (h(m) * h(l) * h(n))
     return est <= STRASSEN_ORACLE_MAX_S, est
 
 
@@ -853,7 +863,7 @@ def main():
         roofline = mp_roofline(args.prec, macs_per_launch, k_avg_ms, kname)
         roofline["traffic"] = None
     else:
-        fp64_peak, fp64_note = peak("dfma")
+        fp64_peak, fp64_note = peak("fp64")
         achieved = macs_per_launch * FP64_OPS_PER_MAC[fmt] / (k_avg_ms * 1e-3) / 1e9
         traffic = TRAFFIC_BYTES.get((fmt, n, algo, n_min, depth))
         roofline = {"bound": "alu", "unit": "Gop/s (FP64 pipe)", "achieved": achieved, "peak": fp64_peak,
@@ -912,7 +922,8 @@ def main():
         summary["integer_pipe"] = {k: {"gflops": v["gflops"], "frac_algorithmic": v["roofline"]["frac_algorithmic"]}
                                    for k, v in vextra.items()}
     if PEAKS:
-        summary["peaks"] = {k: (round(v["value"], 4) if isinstance(v, dict) else v) for k, v in PEAKS.items()}
+        summary["peaks"] = {k: (round(v["value"], 4) if isinstance(v, dict) else v) for k, v in PEAKS.items()
+                            if k not in ("dfma", "dadd", "dmul")}
     if summary:
         line["summary"] = summary
     if PEAKS:

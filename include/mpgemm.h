@@ -299,8 +299,16 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
  * two hidden layers of 64 ReLU units, trained with Adam by hand-written
  * kernels on timings the library measures itself.  Once trained (or loaded)
  * it is installed for the process: MPGEMM_AUTO then picks, for shapes it has
- * not tuned, the candidate (simple, block tile 16/32/64, Strassen depth 1..3
- * with those tiles) of least predicted time, and batched plans use it for
+ * not tuned, among the candidates (simple, block tile 16/32/64, Strassen
+ * depth 1..3 with those tiles): when only one is predicted within 30 % of
+ * the best (about twice the model's 90th-percentile error), that one; else
+ * the (at most 4) candidates within that margin are timed once on the
+ * call's own operands and the fastest is remembered for the shape (and
+ * appended to the tuning cache when one is open), so the first such call
+ * is synchronous and writes C more than once.  While the stream captures a
+ * graph, or in model-only mode (mpgemm_auto_mode(0); 1 restores timing),
+ * nothing is timed: among the configurations predicted within 10 % of the
+ * best, the one with the fewest launches.  Batched plans use the model for
  * tile = 0.  mpgemm_tune (measured) remains available and wins when it has
  * a remembered choice.
  *   mpgemm_cost_features   feature vector (mpgemm_cost_num_features floats)
@@ -415,6 +423,7 @@ int mpgemm_tune_cache_stats(int* choices, int* measurements, int* skipped_lines,
 typedef double (*mpgemm_timer_fn)(void* ctx, int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int algo,
                                   int n_min, int depth, int64_t rows, int reps);
 int mpgemm_tune_set_timer(mpgemm_timer_fn fn, void* ctx);
+int mpgemm_auto_mode(int mode);
 /* The (algo, n_min, depth) MPGEMM_AUTO would use for this problem on the
    whole device. */
 int mpgemm_auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int* algo, int* n_min,
@@ -438,6 +447,23 @@ int mpgemm_stream_status(void* stream);
    MPGEMM_ETIMEOUT is the expected result (the status word is cleared and
    the context stays usable).  MPGEMM_EINVAL for a limit out of range. */
 int mpgemm_selftest_wait_timeout(int limit_ms, void* stream);
+/* Host-side fault injection, for testing callers' error handling (the paper
+   has no counterpart).  Arms one fault: the (after + 1)-th device allocation
+   (what = MPGEMM_FAULT_ALLOC: Strassen / split-precision / integer-pipe
+   workspace, batched plans, precision selection, cost model buffers) or
+   launch check (MPGEMM_FAULT_LAUNCH) the library makes from now on fails,
+   then the fault disarms; what = MPGEMM_FAULT_NONE disarms.  An injected
+   allocation failure allocates nothing and makes the call return
+   MPGEMM_ENOMEM (workspace) or the failing API's error; an injected launch
+   failure is reported after a launch that did run (MPGEMM_ECUDA,
+   mpgemm_last_cuda_error() = 719, a launch failure), so the error paths run
+   as for real failures: owned workspace is released on the stream, plans
+   are torn down.  Nothing is done to the GPU.  The environment variable
+   MPGEMM_FAULT=alloc:N or launch:N arms the same fault at the first call
+   that checks it.  mpgemm_fault_fired: faults injected so far. */
+enum { MPGEMM_FAULT_NONE = 0, MPGEMM_FAULT_ALLOC = 1, MPGEMM_FAULT_LAUNCH = 2 };
+int mpgemm_fault_inject(int what, long long after);
+int mpgemm_fault_fired(void);
 /* Self-test of the DD / QD kernels' TwoSum: for i < count, out[i] =
    RN(a[i] + b[i]), out[count + i] = its rounding error as the kernels
    compute it (the integer-pipe form) and out[2 count + i] = the same error
@@ -577,9 +603,18 @@ int mpgemm_version(void);
  *     FP64 operations of the DD / QD rooflines).
  *   MPGEMM_PEAK_IMAD: 32-bit integer multiply-adds; ops = one per IMAD
  *     (thread instructions).
+ *   MPGEMM_PEAK_DADD / MPGEMM_PEAK_DMUL: FP64 adds / multiplies; ops = one
+ *     per instruction.
  * iters 1..2^32; MPGEMM_EINVAL for a bad kind, count or NULL ops.  The
  * tcgen05 loop's only wait is bounded (a timeout sets the status word). */
-enum { MPGEMM_PEAK_TC_E4M3 = 0, MPGEMM_PEAK_MMA_S8 = 1, MPGEMM_PEAK_DFMA = 2, MPGEMM_PEAK_IMAD = 3 };
+enum {
+    MPGEMM_PEAK_TC_E4M3 = 0,
+    MPGEMM_PEAK_MMA_S8 = 1,
+    MPGEMM_PEAK_DFMA = 2,
+    MPGEMM_PEAK_IMAD = 3,
+    MPGEMM_PEAK_DADD = 4,
+    MPGEMM_PEAK_DMUL = 5
+};
 int mpgemm_peak_run(int kind, int64_t iters, double* ops, void* stream);
 
 #ifdef __cplusplus

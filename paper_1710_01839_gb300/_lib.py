@@ -36,6 +36,8 @@ SIGNATURES = {
     "mpgemm_set_workspace": (_I, [_P, _SZ]),
     "mpgemm_stream_status": (_I, [_P]),
     "mpgemm_selftest_wait_timeout": (_I, [_I, _P]),
+    "mpgemm_fault_inject": (_I, [_I, ctypes.c_longlong]),
+    "mpgemm_fault_fired": (_I, []),
     "mpgemm_partition_create": (_I, [_I, _P, _P]),
     "mpgemm_precision_log2_bound": (ctypes.c_double, [_I, _I, _I, _I64, _I]),
     "mpgemm_select_precision": (_I, [ctypes.c_double, _I64, _I64, _I64, _I, _P, _I]),
@@ -76,6 +78,7 @@ SIGNATURES = {
     "mpgemm_ozaki_split_terms": (_I, [_I, _I, _I64, _I64, _P, _I, _P, _P, _P]),
     "mpgemm_tune": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _I, _P, _P]),
     "mpgemm_tune_forget": (_I, []),
+    "mpgemm_auto_mode": (_I, [_I]),
     "mpgemm_tune_cache_open": (_I, [ctypes.c_char_p]),
     "mpgemm_tune_cache_stats": (_I, [_P, _P, _P, _P]),
     "mpgemm_tune_set_timer": (_I, [_P, _P]),

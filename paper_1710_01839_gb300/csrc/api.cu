@@ -1,6 +1,8 @@
 // C-ABI entry points of libmpgemm (declared in include/mpgemm.h): argument
 // checks, dispatch to the kernels, device status word, workspace.
+#include <atomic>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -18,7 +20,64 @@ static thread_local int t_last_cuda_error = 0;
 
 void set_last_cuda_error(cudaError_t e) { t_last_cuda_error = (int)e; }
 
+// ---------------------------------------------------------------- host fault injection
+//
+// One armed fault: the (after + 1)-th device allocation (FAULT_ALLOC) or
+// launch check (FAULT_LAUNCH) the library makes from now on reports a
+// failure, then the fault disarms.  Nothing is done to the GPU: an injected
+// allocation failure allocates nothing, an injected launch failure is
+// reported after a launch that did run, so the error paths that follow
+// (workspace released, plan torn down) run as they would for a real one.
+static std::atomic<int> g_fault_kind{0};
+static std::atomic<long long> g_fault_left{0};
+static std::atomic<int> g_fault_fired{0};
+
+static void fault_from_env() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char* v = getenv("MPGEMM_FAULT");
+        if (!v) return;
+        int kind = !strncmp(v, "alloc:", 6) ? FAULT_ALLOC : !strncmp(v, "launch:", 7) ? FAULT_LAUNCH : 0;
+        if (!kind) return;
+        const char* num = strchr(v, ':') + 1;
+        char* end = nullptr;
+        long long after = strtoll(num, &end, 10);
+        if (end == num || *end || after < 0) return;
+        g_fault_left.store(after);
+        g_fault_kind.store(kind);
+    });
+}
+
+bool fault_fire(int kind) {
+    fault_from_env();
+    if (g_fault_kind.load() != kind) return false;
+    if (g_fault_left.fetch_sub(1) != 0) return false;
+    g_fault_kind.store(0);
+    g_fault_fired.fetch_add(1);
+    return true;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    if (fault_fire(FAULT_ALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    if (fault_fire(FAULT_ALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
+
 int check_launch() {
+    if (fault_fire(FAULT_LAUNCH)) {
+        set_last_cuda_error(cudaErrorLaunchFailure);
+        return MPGEMM_ECUDA;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
@@ -55,6 +114,10 @@ int workspace_get(size_t bytes, cudaStream_t s, void** out, bool* owned) {
     *out = nullptr;
     *owned = false;
     if (bytes == 0) return MPGEMM_OK;
+    if (fault_fire(FAULT_ALLOC)) {   // an injected failure of the allocation below
+        set_last_cuda_error(cudaErrorMemoryAllocation);
+        return MPGEMM_ENOMEM;
+    }
     int dev = 0;
     MPG_CUDA(cudaGetDevice(&dev));
     {
@@ -131,7 +194,7 @@ static int ddqd_entry(int kind, int64_t m, int64_t l, int64_t n, const double* A
     if (l == 0) return zero_result<double>(kind, m, n, P, C, s);
     if (algo == MPGEMM_AUTO) {
         Choice ch;
-        rc = auto_choice(kind, 0, m, l, n, stream_sms(s), &ch);
+        rc = auto_choice_measured(kind, 0, m, l, n, A, B, C, s, &ch);
         if (rc) return rc;
         algo = ch.algo;
         n_min = ch.n_min;
@@ -157,7 +220,7 @@ static int mp_entry(int64_t m, int64_t l, int64_t n, int prec_bits, const uint32
     if (l == 0) return zero_result<uint32_t>(MPGEMM_KIND_MP, m, n, 2 + w, C, s);
     if (algo == MPGEMM_AUTO) {
         Choice ch;
-        rc = auto_choice(MPGEMM_KIND_MP, prec_bits, m, l, n, stream_sms(s), &ch);
+        rc = auto_choice_measured(MPGEMM_KIND_MP, prec_bits, m, l, n, A, B, C, s, &ch);
         if (rc) return rc;
         algo = ch.algo;
         n_min = ch.n_min;
@@ -244,6 +307,17 @@ const char* mpgemm_strerror(int status) {
 }
 
 int mpgemm_last_cuda_error(void) { return t_last_cuda_error; }
+
+int mpgemm_fault_inject(int what, long long after) {
+    fault_from_env();   // an environment setting read later would override this call
+    if (what < 0 || what > FAULT_LAUNCH || after < 0) return MPGEMM_EINVAL;
+    g_fault_kind.store(0);
+    g_fault_left.store(after);
+    g_fault_kind.store(what);
+    return MPGEMM_OK;
+}
+
+int mpgemm_fault_fired(void) { return g_fault_fired.load(); }
 
 int mpgemm_selftest_wait_timeout(int limit_ms, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;

@@ -280,7 +280,7 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
         rc = e == cudaErrorMemoryAllocation ? MPGEMM_ENOMEM : MPGEMM_ECUDA;
     };
     cudaError_t e;
-    if (limb_words && (e = cudaMalloc(&P->d_limbs, sizeof(uint32_t) * (size_t)limb_words)) != cudaSuccess) fail(e);
+    if (limb_words && (e = dev_malloc((void**)&P->d_limbs, sizeof(uint32_t) * (size_t)limb_words)) != cudaSuccess) fail(e);
     // point the integer-pipe descriptors at their copies; conversion jobs
     std::vector<ConvJob> jobs[4];
     for (int i = 0; i < count && !rc; i++) {
@@ -308,7 +308,7 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
         P->conv[k].njobs = (int)jobs[k].size();
         P->conv[k].total = first;
         if (jobs[k].empty()) continue;
-        if ((e = cudaMalloc(&P->conv[k].d_jobs, sizeof(ConvJob) * jobs[k].size())) != cudaSuccess) fail(e);
+        if ((e = dev_malloc((void**)&P->conv[k].d_jobs, sizeof(ConvJob) * jobs[k].size())) != cudaSuccess) fail(e);
         else if ((e = cudaMemcpy(P->conv[k].d_jobs, jobs[k].data(), sizeof(ConvJob) * jobs[k].size(),
                                  cudaMemcpyHostToDevice)) != cudaSuccess)
             fail(e);
@@ -323,9 +323,9 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
                    cudaSuccess)
         fail(e);
     P->grid = std::max(1, sms * std::max(occ, 1));
-    if (!rc && count && (e = cudaMalloc(&P->d_descs, sizeof(DevDesc) * count)) != cudaSuccess) fail(e);
-    if (!rc && P->nwork && (e = cudaMalloc(&P->d_work, sizeof(Work) * P->nwork)) != cudaSuccess) fail(e);
-    if (!rc && (e = cudaMalloc(&P->d_counter, sizeof(unsigned))) != cudaSuccess) fail(e);
+    if (!rc && count && (e = dev_malloc((void**)&P->d_descs, sizeof(DevDesc) * count)) != cudaSuccess) fail(e);
+    if (!rc && P->nwork && (e = dev_malloc((void**)&P->d_work, sizeof(Work) * P->nwork)) != cudaSuccess) fail(e);
+    if (!rc && (e = dev_malloc((void**)&P->d_counter, sizeof(unsigned))) != cudaSuccess) fail(e);
     if (!rc && count && (e = cudaMemcpy(P->d_descs, dd.data(), sizeof(DevDesc) * count, cudaMemcpyHostToDevice)))
         fail(e);
     if (!rc && P->nwork && (e = cudaMemcpy(P->d_work, work.data(), sizeof(Work) * P->nwork, cudaMemcpyHostToDevice)))

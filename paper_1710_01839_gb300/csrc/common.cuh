@@ -71,7 +71,15 @@ __host__ __device__ inline unsigned ceil_div(int64_t a, int64_t b) { return (uns
     } while (0)
 
 void set_last_cuda_error(cudaError_t e);
-int check_launch();   // cudaGetLastError -> status
+int check_launch();   // cudaGetLastError -> status (or an injected launch failure)
+
+// Host fault injection (mpgemm_fault_inject, MPGEMM_FAULT): true when the
+// armed fault of this kind fires now.  Device allocations of the library go
+// through dev_malloc / dev_malloc_async (or workspace_get), which honour it.
+enum { FAULT_ALLOC = 1, FAULT_LAUNCH = 2 };
+bool fault_fire(int kind);
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s);
 
 // CTA raster order: with group size G (in tiles), consecutive CTA ids cover a
 // G x G super-tile of C before moving on (G = 1 is plain row-major order).

@@ -235,8 +235,8 @@ static std::mutex g_mmu;
 static Model g_model;
 
 static int upload_model(Model& M) {
-    if (!M.d_params) MPG_CUDA(cudaMalloc(&M.d_params, sizeof(float) * NPARAM));
-    if (!M.d_norm) MPG_CUDA(cudaMalloc(&M.d_norm, sizeof(float) * (2 * NF + 2)));
+    if (!M.d_params) MPG_CUDA(dev_malloc((void**)&M.d_params, sizeof(float) * NPARAM));
+    if (!M.d_norm) MPG_CUDA(dev_malloc((void**)&M.d_norm, sizeof(float) * (2 * NF + 2)));
     MPG_CUDA(cudaMemcpy(M.d_params, M.params.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
     MPG_CUDA(cudaMemcpy(M.d_norm, M.norm.data(), sizeof(float) * (2 * NF + 2), cudaMemcpyHostToDevice));
     M.ready = true;
@@ -248,8 +248,8 @@ static int predict(const float* feats, int count, float* out) {
     std::lock_guard<std::mutex> lk(g_mmu);
     if (!g_model.ready) return MPGEMM_EUNSUPPORTED;
     float *dX = nullptr, *dO = nullptr;
-    MPG_CUDA(cudaMalloc(&dX, sizeof(float) * NF * (size_t)count));
-    cudaError_t e = cudaMalloc(&dO, sizeof(float) * (size_t)count);
+    MPG_CUDA(dev_malloc((void**)&dX, sizeof(float) * NF * (size_t)count));
+    cudaError_t e = dev_malloc((void**)&dO, sizeof(float) * (size_t)count);
     if (e == cudaSuccess) e = cudaMemcpy(dX, feats, sizeof(float) * NF * (size_t)count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_mlp_predict<<<ceil_div(count, 128), 128>>>(dX, count, g_model.d_params, g_model.d_norm, dO);
@@ -309,6 +309,33 @@ bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n,
     out->n_min = cs[pick].tile;
     out->depth = cs[pick].depth;
     if (pred_ms) *pred_ms = T[pick];
+    return true;
+}
+
+// The configurations predicted within (1 + margin) of the best, fastest
+// first, at most kmax; false without a model.
+bool cost_model_shortlist(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, double margin,
+                          int kmax, std::vector<Choice>* out, std::vector<float>* pred_ms) {
+    {
+        std::lock_guard<std::mutex> lk(g_mmu);
+        if (!g_model.ready) return false;
+    }
+    std::vector<Cand> cs = candidates(kind, m, l, n);
+    std::vector<float> F(cs.size() * NF), T(cs.size());
+    for (size_t i = 0; i < cs.size(); i++)
+        encode_features(kind, prec_bits, m, l, n, cs[i].algo, cs[i].tile, cs[i].depth, sms, &F[i * NF]);
+    if (predict(F.data(), (int)cs.size(), T.data()) != MPGEMM_OK) return false;
+    std::vector<size_t> order(cs.size());
+    for (size_t i = 0; i < cs.size(); i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return T[a] < T[b]; });
+    out->clear();
+    if (pred_ms) pred_ms->clear();
+    for (size_t k = 0; k < order.size() && (int)out->size() < kmax; k++) {
+        const size_t i = order[k];
+        if (k > 0 && T[i] > (1.0 + margin) * T[order[0]]) break;
+        out->push_back(Choice{cs[i].algo, cs[i].tile, cs[i].depth});
+        if (pred_ms) pred_ms->push_back(T[i]);
+    }
     return true;
 }
 
@@ -422,9 +449,9 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
             rc = MPGEMM_ECUDA;
         }
     };
-    ck(cudaMalloc(&A, bytes));
-    ck(cudaMalloc(&B, bytes));
-    ck(cudaMalloc(&C, bytes));
+    ck(dev_malloc((void**)&A, bytes));
+    ck(dev_malloc((void**)&B, bytes));
+    ck(dev_malloc((void**)&C, bytes));
     ck(cudaEventCreate(&e0));
     ck(cudaEventCreate(&e1));
     std::mt19937_64 rng(seed);
@@ -544,11 +571,11 @@ int mpgemm_cost_train(const float* features, const float* times_ms, int count, i
             rc = MPGEMM_ECUDA;
         }
     };
-    ck(cudaMalloc(&dX, sizeof(float) * X.size()));
-    ck(cudaMalloc(&dY, sizeof(float) * Y.size()));
-    ck(cudaMalloc(&dP, sizeof(float) * NPARAM));
-    ck(cudaMalloc(&dL, sizeof(float) * epochs));
-    ck(cudaMalloc(&dPerm, sizeof(int) * perm.size()));
+    ck(dev_malloc((void**)&dX, sizeof(float) * X.size()));
+    ck(dev_malloc((void**)&dY, sizeof(float) * Y.size()));
+    ck(dev_malloc((void**)&dP, sizeof(float) * NPARAM));
+    ck(dev_malloc((void**)&dL, sizeof(float) * epochs));
+    ck(dev_malloc((void**)&dPerm, sizeof(int) * perm.size()));
     if (rc == MPGEMM_OK) {
         ck(cudaMemcpy(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice));
         ck(cudaMemcpy(dY, Y.data(), sizeof(float) * Y.size(), cudaMemcpyHostToDevice));

@@ -9,11 +9,14 @@
 //   MPGEMM_PEAK_MMA_S8   mma.sync.m16n8k32 s8 x s8 -> s32 on register
 //                        operands, 8 independent accumulators per warp (the
 //                        int8 split-precision level kernel's instruction);
-//   MPGEMM_PEAK_DFMA     FP64 fused multiply-add, 8 independent chains per
-//                        thread (the DD / QD kernels' pipe);
+//   MPGEMM_PEAK_DFMA     FP64 fused multiply-add, 16 independent operations
+//                        per iteration on loop-invariant operands (the DD /
+//                        QD kernels' pipe);
 //   MPGEMM_PEAK_IMAD     32-bit integer multiply-add (mad.lo.u32), 8
 //                        independent chains per thread (the multi-limb
-//                        kernels' limb products).
+//                        kernels' limb products);
+//   MPGEMM_PEAK_DADD / _DMUL  the same with FP64 adds / multiplies: the FP64
+//                        pipe's rate is the fastest of the three loops.
 //
 // Each launch covers every SM of the stream's partition.  The caller times
 // it (events on the same stream) and divides the operation count that
@@ -115,17 +118,26 @@ __global__ void __launch_bounds__(256) k_peak_mma_s8(int64_t iters) {
     if (s == 0x7F3A5C11) g_peak_sink[0] = (unsigned)s;
 }
 
-__global__ void __launch_bounds__(256) k_peak_dfma(int64_t iters, double b, double c) {
-    double x[8];
+// FP64 loops: 16 independent operations per iteration, each on loop-invariant
+// operands (no dependent chains, so only the pipe's throughput limits them);
+// asm volatile keeps every instruction.  OP 0: DFMA, 1: DADD, 2: DMUL.
+template <int OP>
+__global__ void __launch_bounds__(256) k_peak_fp64(int64_t iters, double b, double c) {
+    const double x = 1.0 + 1e-3 * threadIdx.x;
+    double r[16];
 #pragma unroll
-    for (int j = 0; j < 8; j++) x[j] = 1.0 + 1e-3 * (threadIdx.x + 37 * j);
+    for (int j = 0; j < 16; j++) r[j] = 0.0;
     for (int64_t it = 0; it < iters; it++) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) x[j] = fma(x[j], b, c);
+        for (int j = 0; j < 16; j++) {
+            if constexpr (OP == 0) asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r[j]) : "d"(x), "d"(b), "d"(c));
+            else if constexpr (OP == 1) asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r[j]) : "d"(x), "d"(c));
+            else asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r[j]) : "d"(x), "d"(b));
+        }
     }
     double s = 0;
 #pragma unroll
-    for (int j = 0; j < 8; j++) s += x[j];
+    for (int j = 0; j < 16; j++) s += r[j];
     if (s == 1234.5) g_peak_sink[1] = __double_as_longlong(s);
 }
 
@@ -149,7 +161,7 @@ using namespace mpg;
 
 extern "C" int mpgemm_peak_run(int kind, int64_t iters, double* ops, void* stream) {
     if (iters < 1 || iters > (int64_t(1) << 32) || !ops) return MPGEMM_EINVAL;
-    if (kind < MPGEMM_PEAK_TC_E4M3 || kind > MPGEMM_PEAK_IMAD) return MPGEMM_EINVAL;
+    if (kind < MPGEMM_PEAK_TC_E4M3 || kind > MPGEMM_PEAK_DMUL) return MPGEMM_EINVAL;
     // keeps one tcgen05 launch well inside its bounded wait
     if (kind == MPGEMM_PEAK_TC_E4M3 && iters > (int64_t(1) << 22)) return MPGEMM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -174,12 +186,16 @@ extern "C" int mpgemm_peak_run(int kind, int64_t iters, double* ops, void* strea
             *ops = 2.0 * 16 * 8 * 32 * 8 * (double)iters * ((double)occ * sms * 256 / 32);
             break;
         }
-        case MPGEMM_PEAK_DFMA: {
+        case MPGEMM_PEAK_DFMA:
+        case MPGEMM_PEAK_DADD:
+        case MPGEMM_PEAK_DMUL: {
             int occ = 0;
-            MPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peak_dfma, 256, 0));
+            auto kern = kind == MPGEMM_PEAK_DFMA ? k_peak_fp64<0> : kind == MPGEMM_PEAK_DADD ? k_peak_fp64<1>
+                                                                                            : k_peak_fp64<2>;
+            MPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0));
             if (occ < 1) return MPGEMM_ECUDA;
-            k_peak_dfma<<<occ * sms, 256, 0, s>>>(iters, 0.999999, 1e-7);
-            *ops = 8.0 * (double)iters * (double)occ * sms * 256;
+            kern<<<occ * sms, 256, 0, s>>>(iters, 0.999999, 1e-7);
+            *ops = 16.0 * (double)iters * (double)occ * sms * 256;
             break;
         }
         case MPGEMM_PEAK_IMAD: {

@@ -200,7 +200,7 @@ int mpgemm_dd_exponent_spread(int64_t m, int64_t l, int64_t n, const double* A, 
     cudaStream_t s = (cudaStream_t)stream;
     PartitionScope pscope(s);
     int* buf = nullptr;   // [result | column max (n) | column min (n)]
-    cudaError_t e = cudaMallocAsync((void**)&buf, sizeof(int) * (size_t)(1 + 2 * n), s);
+    cudaError_t e = dev_malloc_async((void**)&buf, sizeof(int) * (size_t)(1 + 2 * n), s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
         return MPGEMM_ENOMEM;

@@ -45,6 +45,16 @@ void remember_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, i
     g_table[Key(kind, prec_bits, m, l, n, sms)] = ch;
 }
 
+// MPGEMM_AUTO's selection mode (mpgemm_auto_mode): 1 = the cost model's
+// short list timed on the operands when it holds more than one
+// configuration, 0 = the cost model's pick alone (never times).
+static int g_auto_mode = 1;
+// The short list: configurations predicted within this fraction of the best
+// (about twice the model's 90th-percentile error on held-out timings), at
+// most this many.
+constexpr double AUTO_MARGIN = 0.30;
+constexpr int AUTO_MAX_TIMED = 4;
+
 // Replacement timer (mpgemm_tune_set_timer): simulated or recorded timings.
 static std::mutex g_timer_mu;
 static mpgemm_timer_fn g_timer = nullptr;
@@ -179,6 +189,63 @@ int measure(const Problem& P, const TuneKey& key, int algo, int n_min, int depth
 
 }  // namespace
 
+int auto_choice_measured(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const void* A, const void* B,
+                         void* C, cudaStream_t s, Choice* out) {
+    const int sms = stream_sms(s);
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        auto it = g_table.find(Key(kind, prec_bits, m, l, n, sms));
+        if (it != g_table.end()) {
+            *out = it->second;
+            return MPGEMM_OK;
+        }
+    }
+    std::vector<Choice> list;
+    std::vector<float> pred;
+    if (!cost_model_shortlist(kind, prec_bits, m, l, n, sms, AUTO_MARGIN, AUTO_MAX_TIMED, &list, &pred) ||
+        list.empty())
+        return auto_choice(kind, prec_bits, m, l, n, sms, out);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    }
+    int mode;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        mode = g_auto_mode;
+    }
+    if (list.size() == 1 || mode == 0 || cap != cudaStreamCaptureStatusNone)
+        return auto_choice(kind, prec_bits, m, l, n, sms, out);   // the model's rule, nothing timed
+    Problem P{kind, kind == MPGEMM_KIND_MP ? prec_bits : 0, m, l, n, A, B, C, s};
+    const TuneKey key{kind, P.prec_bits, m, l, n, sms};
+    int measured = 0, best = -1;
+    double best_ms = 0.0;
+    for (size_t i = 0; i < list.size(); i++) {
+        const float p = pred[i];
+        const int reps = p < 1.0f ? 5 : p < 20.0f ? 3 : 1;
+        double ms = 0.0;
+        int rc = measure(P, key, list[i].algo, list[i].n_min, list[i].depth, m, reps, &ms, &measured);
+        if (rc) return rc;
+        if (best < 0 || ms < best_ms) {
+            best = (int)i;
+            best_ms = ms;
+        }
+    }
+    *out = list[best];
+    remember_choice(kind, P.prec_bits, m, l, n, sms, *out);
+    mpgemm_tune_report rep;
+    memset(&rep, 0, sizeof rep);
+    rep.algo = out->algo;
+    rep.n_min = out->n_min;
+    rep.depth = out->depth;
+    rep.best_ms = best_ms;
+    rep.simple_ms = rep.block_ms = NAN;
+    for (int d = 0; d < 4; d++) rep.strassen_ms[d] = NAN;
+    tune_cache_append_choice(key, &rep);
+    return MPGEMM_OK;
+}
+
 }  // namespace mpg
 
 using namespace mpg;
@@ -283,6 +350,13 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
     if (flags & MPGEMM_TUNE_REMEMBER) remember_choice(kind, P.prec_bits, m, l, n, sms, ch);
     tune_cache_append_choice(key, rep);
     rep->tuning_ms = wall_ms();
+    return MPGEMM_OK;
+}
+
+int mpgemm_auto_mode(int mode) {
+    if (mode != 0 && mode != 1) return MPGEMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_auto_mode = mode;
     return MPGEMM_OK;
 }
 

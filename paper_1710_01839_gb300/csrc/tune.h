@@ -2,6 +2,9 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
 
 #include "../../include/mpgemm.h"
 
@@ -21,6 +24,15 @@ int auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sm
 
 int default_n_min(int kind);
 
+// MPGEMM_AUTO for a call with operands (device pointers in the format of
+// `kind`; C may be overwritten): the remembered choice; else the cost
+// model's short list of configurations predicted within its own error of
+// the best, where a list of more than one is timed once on the operands
+// (not while the stream captures a graph, and not in model-only mode) and
+// its fastest member remembered; without a model, the default.
+int auto_choice_measured(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const void* A, const void* B,
+                         void* C, cudaStream_t s, Choice* out);
+
 // Stores a choice for MPGEMM_AUTO (as MPGEMM_TUNE_REMEMBER does).
 void remember_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, Choice ch);
 
@@ -31,6 +43,11 @@ struct TuneKey {
     int64_t m, l, n;
     int sms;
 };
+// Cost model (mlp.cu): the configurations predicted within (1 + margin) of
+// the best, fastest first, at most kmax; false without a model.
+bool cost_model_shortlist(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, double margin,
+                          int kmax, std::vector<Choice>* out, std::vector<float>* pred_ms);
+
 bool tune_cache_lookup_meas(const TuneKey& k, int algo, int n_min, int depth, int64_t rows, int reps, double* ms);
 void tune_cache_append_meas(const TuneKey& k, int algo, int n_min, int depth, int64_t rows, int reps, double ms);
 bool tune_cache_lookup_choice(const TuneKey& k, mpgemm_tune_report* rep);

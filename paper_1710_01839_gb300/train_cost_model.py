@@ -43,6 +43,102 @@ def _time(fn, reps=3):
     return float(np.median(ts))
 
 
+def _time_interleaved(fns, reps=5):
+    """Median ms of each function, timed round-robin (rep r of every
+    function before rep r + 1 of any), after one untimed call each."""
+    import torch
+    for f in fns:
+        f()
+    torch.cuda.synchronize()
+    ts = [[] for _ in fns]
+    for _ in range(reps):
+        for i, f in enumerate(fns):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            ts[i].append(a.elapsed_time(b))
+    return [float(np.median(t)) for t in ts]
+
+
+def batched_like_shapes(count, seed=2024, min_dim=16, max_dim=1024):
+    """(fmt, bits, m, l, n): m, l, n log-uniform in [min_dim, max_dim] (the
+    batched workload's recipe), formats cycling DD, QD, 256-bit, 128-bit."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        fmt, bits = [("dd", 0), ("qd", 0), ("mp", 256), ("mp", 128)][i % 4]
+        m, l, n = (int(round(x)) for x in np.exp(rng.uniform(np.log(min_dim), np.log(max_dim), 3)))
+        out.append((fmt, bits, m, l, n))
+    return out
+
+
+def auto_regret_study(shapes, reps=5):
+    """MPGEMM_AUTO's pick (the cost model, with its short list timed on the
+    operands when the model is not sure) against every candidate timed
+    exhaustively, one GEMM at a time; also the model's pick alone."""
+    import ctypes
+    import torch
+    import paper_1710_01839_gb300 as mpg
+    from paper_1710_01839_gb300 import costmodel as cm, inputs as I
+    L = mpg.lib()
+    rows = []
+    for i, (fmt, bits, m, l, n) in enumerate(shapes):
+        if fmt == "dd":
+            A, B = I.dd_random(m, l, 500 + i), I.dd_random(l, n, 600 + i)
+        elif fmt == "qd":
+            A, B = I.qd_random(m, l, 500 + i), I.qd_random(l, n, 600 + i)
+        else:
+            A, B = I.mp_random(m, l, bits // 32, 500 + i), I.mp_random(l, n, bits // 32, 600 + i)
+        Ad = torch.from_numpy(A.view(np.int32) if fmt == "mp" else A).cuda()
+        Bd = torch.from_numpy(B.view(np.int32) if fmt == "mp" else B).cuda()
+
+        def run(algo, tile, depth):
+            if fmt == "dd":
+                return lambda: mpg.gemm_dd(Ad, Bd, algo=algo, n_min=tile, depth=depth)
+            if fmt == "qd":
+                return lambda: mpg.gemm_qd(Ad, Bd, algo=algo, n_min=tile, depth=depth)
+            return lambda: mpg.gemm_mp(Ad, Bd, bits, algo=algo, n_min=tile, depth=depth)
+
+        tmax = {"dd": 64, "qd": 32, "mp": 16}[fmt]
+        ext = lambda x, d: (x + (1 << d) - 1) >> d << d
+        cands = [("simple", 16, 0)] + [("block", t, 0) for t in (16, 32, 64) if t <= tmax]
+        for d in (1, 2, 3):
+            if all((ext(x, d) >> d) >= 16 for x in (m, l, n)):
+                cands += [("strassen", t, d) for t in (16, 32, 64) if t <= tmax]
+        kind = {"dd": 0, "qd": 1, "mp": 2}[fmt]
+        L.mpgemm_tune_forget()
+        run("auto", 0, 0)()                                 # AUTO decides (and remembers)
+        torch.cuda.synchronize()
+        a, nm, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check = L.mpgemm_auto_choice(kind, bits, m, l, n, ctypes.byref(a), ctypes.byref(nm), ctypes.byref(d))
+        assert check == 0
+        auto = ({0: "simple", 1: "block", 2: "strassen"}[a.value], nm.value, d.value)
+        ch = cm.choice(fmt, m, l, n, prec_bits=bits)        # the model's rule alone (nothing timed)
+        rule = (ch["algo"], ch["n_min"], ch["depth"])
+        for c in (auto, rule):
+            if c not in cands:
+                cands.append(c)
+        meas = _time_interleaved([run(*c) for c in cands], reps)
+        best = int(np.argmin(meas))
+        t_auto, t_rule = meas[cands.index(auto)], meas[cands.index(rule)]
+        rows.append({"fmt": fmt if fmt != "mp" else f"mp{bits}", "m": m, "l": l, "n": n, "auto_pick": auto,
+                     "model_rule_pick": rule, "best": cands[best], "t_auto_ms": t_auto, "t_rule_ms": t_rule,
+                     "t_best_ms": meas[best], "regret_auto": t_auto / meas[best] - 1,
+                     "regret_model_rule": t_rule / meas[best] - 1})
+        del Ad, Bd
+    L.mpgemm_tune_forget()
+    ra = [r["regret_auto"] for r in rows]
+    rr = [r["regret_model_rule"] for r in rows]
+    return {"shapes": rows, "count": len(rows),
+            "auto": {"mean": float(np.mean(ra)), "median": float(np.median(ra)), "max": float(np.max(ra)),
+                     "over_10pct": int(np.sum(np.array(ra) > 0.10)),
+                     "time_weighted": float(sum(r["t_auto_ms"] for r in rows) / sum(r["t_best_ms"] for r in rows) - 1)},
+            "model_rule": {"mean": float(np.mean(rr)), "median": float(np.median(rr)), "max": float(np.max(rr)),
+                           "over_10pct": int(np.sum(np.array(rr) > 0.10))}}
+
+
 def regret_study(shapes_seed=99, count=12, max_dim=1024):
     """Model's pick vs exhaustive timing of all candidates, single GEMMs."""
     import torch
@@ -100,9 +196,16 @@ def main():
     ap.add_argument("--regret-shapes", type=int, default=12)
     ap.add_argument("--evaluate", default=None, metavar="MODEL",
                     help="only load MODEL and run the regret study (no collection or training)")
+    ap.add_argument("--auto-regret", type=int, default=0, metavar="SHAPES",
+                    help="with --evaluate: MPGEMM_AUTO's regret on SHAPES shapes drawn like the batched workload")
     args = ap.parse_args()
     import torch  # noqa: F401  (CUDA context, current stream)
     from paper_1710_01839_gb300 import costmodel as cm
+    if args.evaluate and args.auto_regret:
+        cm.load(args.evaluate)
+        print(json.dumps({"model": args.evaluate,
+                          "auto_regret": auto_regret_study(batched_like_shapes(args.auto_regret))}), flush=True)
+        return
     if args.evaluate:
         cm.load(args.evaluate)
         print(json.dumps({"model": args.evaluate,
