@@ -86,6 +86,9 @@ def parse():
     ap.add_argument("--qd-split-slices", type=int, default=44)
     ap.add_argument("--extra-reps", type=int, default=5, help="timed calls (median) of each comparison arm")
     ap.add_argument("--no-peaks", action="store_true", help="use the fallback roofline peaks")
+    ap.add_argument("--tuning-table", action="store_true",
+                    help="run the Section 3 tuning-time experiment (paper_1710_01839_gb300.tuning_experiment) "
+                         "over DD, QD and 128/256/1024-bit at n = 128..1024 +- 1 and print its JSON instead")
     return ap.parse_args()
 
 
@@ -743,6 +746,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.tuning_table:
+        from paper_1710_01839_gb300 import tuning_experiment
+        print(json.dumps(tuning_experiment.run()), flush=True)
+        return
 
     import torch
     import paper_1710_01839_gb300 as mpg
