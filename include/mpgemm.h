@@ -166,6 +166,14 @@ int mpgemm_ozaki_levels_ex(int digit_kind, int64_t m, int64_t l, int64_t n, int 
 int mpgemm_qd_ozaki(int64_t m, int64_t l, int64_t n, const double* A, const double* B, double* C, int num_slices,
                     void* stream);
 int mpgemm_qd_ozaki_slices_default(void);
+/* The order in which the tcgen05 level kernel (e4m3 digits) runs its jobs,
+   one job per 128 x 256 tile of C and level g: tiles grouped into
+   super-tiles whose digit planes fit in L2, super-tiles in row-major order,
+   within a super-tile the levels from g = S + 1 down to 2.  Host arithmetic
+   only: writes (g, first row, first column) of job j to jobs[3j .. 3j + 2]
+   for j < max_jobs and returns the number of jobs (tiles x S), or
+   MPGEMM_EINVAL for bad sizes (m, n <= 65535). */
+int mpgemm_split_job_order(int64_t m, int64_t n, int64_t l, int num_slices, int* jobs, int max_jobs);
 int mpgemm_ozaki_split_terms(int terms, int by_col, int64_t rows, int64_t cols, const double* X, int num_slices,
                              int* expo, void* digits, void* stream);
 

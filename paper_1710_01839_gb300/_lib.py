@@ -75,6 +75,7 @@ SIGNATURES = {
     "mpgemm_ozaki_levels": (_I, [_I64, _I64, _I64, _I, _P, _P, _P, _P]),
     "mpgemm_qd_ozaki": (_I, [_I64, _I64, _I64, _P, _P, _P, _I, _P]),
     "mpgemm_qd_ozaki_slices_default": (_I, []),
+    "mpgemm_split_job_order": (_I, [_I64, _I64, _I64, _I, _P, _I]),
     "mpgemm_ozaki_split_terms": (_I, [_I, _I, _I64, _I64, _P, _I, _P, _P, _P]),
     "mpgemm_tune": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _I, _P, _P]),
     "mpgemm_tune_forget": (_I, []),

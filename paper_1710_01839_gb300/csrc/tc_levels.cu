@@ -33,6 +33,7 @@
 // asynchronous write is in flight when tensor memory is freed.
 #include <cuda.h>
 
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -69,10 +70,28 @@ struct TcJob {
     int g, row0, col0;
 };
 
-// Job j: levels from g = S + 1 (S pairs) down to g = 2, tiles row-major within a level.
-__device__ __forceinline__ TcJob tc_job(int j, int S, int tiles, int tiles_n) {
-    const int tile = j % tiles;
-    return TcJob{S + 1 - j / tiles, (tile / tiles_n) * TC_M, (tile % tiles_n) * TC_N};
+// Job order: the tiles are grouped into super-tiles of SR x SC tiles (bands
+// of SR tile rows, each cut into SC tile columns; the last band and the last
+// super-tile of a band may be smaller), super-tiles in row-major order, and
+// within a super-tile the levels from g = S + 1 (S pairs) down to g = 2, the
+// tiles of a level row-major.  All levels of a super-tile read the same S
+// digit planes of its SR row blocks of A and SC column blocks of B, which the
+// host sizes to stay in L2 while the super-tile's jobs run.
+struct TcOrder {
+    int S, tiles_m, tiles_n, SR, SC;
+};
+
+__host__ __device__ inline TcJob tc_job(int j, const TcOrder& o) {
+    const int band_jobs = o.SR * o.tiles_n * o.S;   // every band but the last is full
+    const int b = j / band_jobs;
+    const int r = j - b * band_jobs;
+    const int h = o.tiles_m - b * o.SR < o.SR ? o.tiles_m - b * o.SR : o.SR;
+    const int st_jobs = h * o.SC * o.S;             // every super-tile of a band but the last is full
+    const int c = r / st_jobs;
+    const int q = r - c * st_jobs;
+    const int w = o.tiles_n - c * o.SC < o.SC ? o.tiles_n - c * o.SC : o.SC;
+    const int lvl = q / (h * w), t = q - lvl * (h * w);
+    return TcJob{o.S + 1 - lvl, (b * o.SR + t / w) * TC_M, (c * o.SC + t % w) * TC_N};
 }
 
 // Index of this CTA's job in round k (snake order).
@@ -80,7 +99,7 @@ __device__ __forceinline__ int tc_job_index(int k, int G, int c) { return k * G 
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_levels_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n,
-                int ksteps, int S, int Q, int tiles_n, int tiles, int vec, int* __restrict__ Lv, unsigned* status) {
+                int ksteps, int S, int Q, TcOrder order, int tiles, int vec, int* __restrict__ Lv, unsigned* status) {
     extern __shared__ unsigned char dsm[];
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tmem_full[2], tmem_empty[2], drain;
     __shared__ uint32_t tmem_base;
@@ -123,7 +142,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int k = 0; k < rounds && ok; k++) {
                 const int j = tc_job_index(k, G, cta);
                 if (j >= J) continue;
-                const TcJob jb = tc_job(j, S, tiles, tiles_n);
+                const TcJob jb = tc_job(j, order);
                 for (int s = 1; s < jb.g && ok; s++) {
                     for (int kb = 0; kb < ksteps; kb++, it++) {
                         const int st = (int)(it % TC_STAGES);
@@ -155,7 +174,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int k = 0; k < rounds && ok; k++) {
                 const int j = tc_job_index(k, G, cta);
                 if (j >= J) continue;
-                const int pairs = S - j / tiles;   // g - 1
+                const int pairs = tc_job(j, order).g - 1;
                 for (int s0 = 1; s0 <= pairs && ok; s0 += Q, cc++) {
                     const int np = (pairs - s0 + 1) < Q ? (pairs - s0 + 1) : Q;
                     const uint32_t acc = cc & 1;
@@ -215,7 +234,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int k = 0; k < rounds && ok; k++) {
             const int j = tc_job_index(k, G, cta);
             if (j >= J) continue;
-            const TcJob jb = tc_job(j, S, tiles, tiles_n);
+            const TcJob jb = tc_job(j, order);
             const int pairs = jb.g - 1;
             const int64_t r = (int64_t)jb.row0 + quarter * 32 + lane;
             int* out = Lv + (int64_t)(jb.g - 2) * m * n + r * n;
@@ -342,6 +361,24 @@ static int digit_map(CUtensorMap* map, const void* D, int64_t rows, int64_t lp, 
     return r == CUDA_SUCCESS ? MPGEMM_OK : MPGEMM_EINVAL;
 }
 
+// Super-tile shape for the job order: SC column blocks (256 x lp x S digit
+// bytes each) and SR row blocks (128 x lp x S) whose planes together take at
+// most about three quarters of the 129 MB L2.
+constexpr double TC_L2_BUDGET = 96.0 * 1024 * 1024;
+
+static TcOrder tc_order(int64_t m, int64_t n, int64_t lp, int S) {
+    TcOrder o;
+    o.S = S;
+    o.tiles_m = (int)ceil_div(m, TC_M);
+    o.tiles_n = (int)ceil_div(n, TC_N);
+    const double a_blk = (double)TC_M * (double)lp * S, b_blk = (double)TC_N * (double)lp * S;
+    double sc = std::floor(TC_L2_BUDGET / 2 / b_blk);
+    o.SC = (int)(sc < 1 ? 1 : sc > o.tiles_n ? o.tiles_n : sc);
+    double sr = std::floor((TC_L2_BUDGET - o.SC * b_blk) / a_blk);
+    o.SR = (int)(sr < 1 ? 1 : sr > o.tiles_m ? o.tiles_m : sr);
+    return o;
+}
+
 int tc_levels(int64_t m, int64_t n, int64_t lp, int S, const void* DA, const void* DB, int* Lv, cudaStream_t s) {
     if (lp <= 0 || lp % TC_BK || S < 1) return MPGEMM_EINVAL;
     if (((uintptr_t)DA | (uintptr_t)DB) & 15) return MPGEMM_EINVAL;   // tensor-map base alignment
@@ -357,17 +394,35 @@ int tc_levels(int64_t m, int64_t n, int64_t lp, int S, const void* DA, const voi
     // set on every call: the current context may be an SM partition's (partition.cu)
     MPG_CUDA(cudaFuncSetAttribute(k_levels_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     const int sms = stream_sms(s);   // one persistent CTA per SM of the stream's partition
-    const int tiles_m = (int)ceil_div(m, TC_M), tiles_n = (int)ceil_div(n, TC_N);
-    const int tiles = tiles_m * tiles_n;
+    const TcOrder order = tc_order(m, n, lp, S);
+    const int tiles = order.tiles_m * order.tiles_n;
     const int64_t jobs = (int64_t)tiles * S;
     const int grid = (int)(jobs < sms ? jobs : sms);
     const int vec = ((uintptr_t)Lv % 16 == 0) && (n % 4 == 0);
     {
         ProfScope ps(s);
-        k_levels_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(mA, mB, (int)m, (int)n, (int)(lp / TC_BK), S, Q, tiles_n,
+        k_levels_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(mA, mB, (int)m, (int)n, (int)(lp / TC_BK), S, Q, order,
                                                       tiles, vec, Lv, status);
     }
     return check_launch();
 }
 
 }  // namespace mpg
+
+using namespace mpg;
+
+extern "C" int mpgemm_split_job_order(int64_t m, int64_t n, int64_t l, int num_slices, int* jobs, int max_jobs) {
+    if (m < 1 || n < 1 || l < 1 || num_slices < 1 || m > 65535 || n > 65535 || max_jobs < 0 || (max_jobs && !jobs))
+        return MPGEMM_EINVAL;
+    const int64_t lp = (l + TC_BK - 1) / TC_BK * TC_BK;
+    const TcOrder o = tc_order(m, n, lp, num_slices);
+    const int64_t J = (int64_t)o.tiles_m * o.tiles_n * num_slices;
+    if (J > 0x7FFFFFFF) return MPGEMM_EUNSUPPORTED;
+    for (int64_t j = 0; j < J && j < max_jobs; j++) {
+        const TcJob jb = tc_job((int)j, o);
+        jobs[3 * j] = jb.g;
+        jobs[3 * j + 1] = jb.row0;
+        jobs[3 * j + 2] = jb.col0;
+    }
+    return (int)J;
+}
