@@ -309,9 +309,11 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
  * it is installed for the process: MPGEMM_AUTO then picks, for shapes it has
  * not tuned, among the candidates (simple, block tile 16/32/64, Strassen
  * depth 1..3 with those tiles): when only one is predicted within 30 % of
- * the best (about twice the model's 90th-percentile error), that one; else
- * the (at most 4) candidates within that margin are timed once on the
- * call's own operands and the fastest is remembered for the shape (and
+ * the best (about twice the model's 90th-percentile error) and no other
+ * algorithm within 60 %, that one; else those candidates (the ones within
+ * 30 % and the best of each algorithm within 60 %, at most 5) are timed
+ * once on the call's own operands and the fastest is remembered for the
+ * shape (and
  * appended to the tuning cache when one is open), so the first such call
  * is synchronous and writes C more than once.  While the stream captures a
  * graph, or in model-only mode (mpgemm_auto_mode(0); 1 restores timing),
@@ -322,7 +324,7 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
  *   mpgemm_cost_features   feature vector (mpgemm_cost_num_features floats)
  *   mpgemm_cost_collect    time `count` random configurations (shapes
  *                          log-uniform in [16, max_dim], formats DD / QD /
- *                          128- or 256-bit multi-limb, valid algorithms);
+ *                          128- to 1024-bit multi-limb, valid algorithms);
  *                          host output arrays; synchronous; allocates its
  *                          own operand buffers and releases them on every
  *                          path; a failed CUDA call gives MPGEMM_ECUDA, a

@@ -313,7 +313,8 @@ bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n,
 }
 
 // The configurations predicted within (1 + margin) of the best, fastest
-// first, at most kmax; false without a model.
+// first, and the fastest of each algorithm family (simple, block, Strassen)
+// predicted within (1 + 2 margin), at most kmax; false without a model.
 bool cost_model_shortlist(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, double margin,
                           int kmax, std::vector<Choice>* out, std::vector<float>* pred_ms) {
     {
@@ -330,9 +331,13 @@ bool cost_model_shortlist(int kind, int prec_bits, int64_t m, int64_t l, int64_t
     std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return T[a] < T[b]; });
     out->clear();
     if (pred_ms) pred_ms->clear();
+    bool family[3] = {false, false, false};
     for (size_t k = 0; k < order.size() && (int)out->size() < kmax; k++) {
         const size_t i = order[k];
-        if (k > 0 && T[i] > (1.0 + margin) * T[order[0]]) break;
+        const bool near = k == 0 || T[i] <= (1.0 + margin) * T[order[0]];
+        const bool family_best = !family[cs[i].algo] && T[i] <= (1.0 + 2.0 * margin) * T[order[0]];
+        if (!near && !family_best) continue;
+        family[cs[i].algo] = true;
         out->push_back(Choice{cs[i].algo, cs[i].tile, cs[i].depth});
         if (pred_ms) pred_ms->push_back(T[i]);
     }
@@ -439,7 +444,7 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
         g_model.sms = sms;
     }
     const size_t maxe = (size_t)max_dim * max_dim;
-    const size_t bytes = maxe * 40;   // largest element: 256-bit multi-limb, 10 words
+    const size_t bytes = maxe * 4 * 34;   // largest element: 1024-bit multi-limb, 34 words
     void *A = nullptr, *B = nullptr, *C = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = MPGEMM_OK;
@@ -460,9 +465,10 @@ int mpgemm_cost_collect(int count, unsigned long long seed, int max_dim, float* 
         int64_t m = (int64_t)std::lround(std::exp(U(rng))), l = (int64_t)std::lround(std::exp(U(rng))),
                 n = (int64_t)std::lround(std::exp(U(rng)));
         int kind = (int)(rng() % 3);
-        // multi-limb: 256 bits (the batched workload's width) or 128 bits
-        // (the width of the integer-pipe DD GEMM)
-        int prec = kind == MPGEMM_KIND_MP ? (rng() % 2 ? 256 : 128) : 0;
+        // multi-limb: 256 bits (the batched workload's width), 128 bits (the
+        // width of the integer-pipe DD GEMM), 512 and 1024 bits
+        static const int precs[10] = {128, 128, 128, 256, 256, 256, 256, 512, 512, 1024};
+        int prec = kind == MPGEMM_KIND_MP ? precs[rng() % 10] : 0;
         if (rng() % 3 == 0) {   // a third of the shapes even enough for Strassen
             m &= ~7LL;
             l &= ~7LL;

@@ -9,9 +9,8 @@
 //   MPGEMM_PEAK_MMA_S8   mma.sync.m16n8k32 s8 x s8 -> s32 on register
 //                        operands, 8 independent accumulators per warp (the
 //                        int8 split-precision level kernel's instruction);
-//   MPGEMM_PEAK_DFMA     FP64 fused multiply-add, 16 independent operations
-//                        per iteration on loop-invariant operands (the DD /
-//                        QD kernels' pipe);
+//   MPGEMM_PEAK_DFMA     FP64 fused multiply-add, 16 independent chains per
+//                        thread (the DD / QD kernels' pipe);
 //   MPGEMM_PEAK_IMAD     32-bit integer multiply-add (mad.lo.u32), 8
 //                        independent chains per thread (the multi-limb
 //                        kernels' limb products);
@@ -118,26 +117,25 @@ __global__ void __launch_bounds__(256) k_peak_mma_s8(int64_t iters) {
     if (s == 0x7F3A5C11) g_peak_sink[0] = (unsigned)s;
 }
 
-// FP64 loops: 16 independent operations per iteration, each on loop-invariant
-// operands (no dependent chains, so only the pipe's throughput limits them);
-// asm volatile keeps every instruction.  OP 0: DFMA, 1: DADD, 2: DMUL.
+// FP64 loops: 16 independent dependent chains per thread (a chain cannot be
+// hoisted out of the loop; 16 of them per thread and every SM full keep the
+// pipe fed).  OP 0: DFMA, 1: DADD, 2: DMUL.
 template <int OP>
 __global__ void __launch_bounds__(256) k_peak_fp64(int64_t iters, double b, double c) {
-    const double x = 1.0 + 1e-3 * threadIdx.x;
-    double r[16];
+    double x[16];
 #pragma unroll
-    for (int j = 0; j < 16; j++) r[j] = 0.0;
+    for (int j = 0; j < 16; j++) x[j] = 1.0 + 1e-3 * (threadIdx.x + 37 * j);
     for (int64_t it = 0; it < iters; it++) {
 #pragma unroll
         for (int j = 0; j < 16; j++) {
-            if constexpr (OP == 0) asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r[j]) : "d"(x), "d"(b), "d"(c));
-            else if constexpr (OP == 1) asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r[j]) : "d"(x), "d"(c));
-            else asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r[j]) : "d"(x), "d"(b));
+            if constexpr (OP == 0) x[j] = fma(x[j], b, c);
+            else if constexpr (OP == 1) x[j] = __dadd_rn(x[j], c);
+            else x[j] = __dmul_rn(x[j], b);
         }
     }
     double s = 0;
 #pragma unroll
-    for (int j = 0; j < 16; j++) s += r[j];
+    for (int j = 0; j < 16; j++) s += x[j];
     if (s == 1234.5) g_peak_sink[1] = __double_as_longlong(s);
 }
 

@@ -50,10 +50,10 @@ void remember_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, i
 // configuration, 0 = the cost model's pick alone (never times).
 static int g_auto_mode = 1;
 // The short list: configurations predicted within this fraction of the best
-// (about twice the model's 90th-percentile error on held-out timings), at
-// most this many.
+// (about twice the model's 90th-percentile error on held-out timings) and
+// the best of each algorithm family within twice it, at most this many.
 constexpr double AUTO_MARGIN = 0.30;
-constexpr int AUTO_MAX_TIMED = 4;
+constexpr int AUTO_MAX_TIMED = 5;
 
 // Replacement timer (mpgemm_tune_set_timer): simulated or recorded timings.
 static std::mutex g_timer_mu;

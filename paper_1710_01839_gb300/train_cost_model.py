@@ -4,7 +4,7 @@ to paper_1710_01839_gb300/data/cost_model_gb300.bin (or --out).
     python -m paper_1710_01839_gb300.train_cost_model [--count 5000] [--epochs 200]
 
 Steps: mpgemm_cost_collect times `count` random configurations (shapes
-log-uniform in [16, max_dim], DD / QD / 128- and 256-bit multi-limb, every valid
+log-uniform in [16, max_dim], DD / QD / 128- to 1024-bit multi-limb, every valid
 algorithm / tile / Strassen depth); 90 % train the model (mpgemm_cost_train),
 10 % measure its held-out error.  Then, for a set of random shapes, the
 configuration the library's choice rule picks with the model
