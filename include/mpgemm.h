@@ -310,11 +310,11 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
  * not tuned, among the candidates (simple, block tile 16/32/64, Strassen
  * depth 1..3 with those tiles): when only one is predicted within 30 % of
  * the best (about twice the model's 90th-percentile error) and no other
- * algorithm within 60 %, that one; else those candidates (the ones within
- * 30 % and the best of each algorithm within 60 %, at most 5) are timed
- * once on the call's own operands and the fastest is remembered for the
- * shape (and
- * appended to the tuning cache when one is open), so the first such call
+ * algorithm's best within 60 % or predicted below 2 ms, that one; else
+ * those candidates (the ones within 30 % and the best of each algorithm
+ * within 60 % or below 2 ms, at most 6) are timed once on the call's own
+ * operands and the fastest is remembered for the shape (and appended to
+ * the tuning cache when one is open), so the first such call
  * is synchronous and writes C more than once.  While the stream captures a
  * graph, or in model-only mode (mpgemm_auto_mode(0); 1 restores timing),
  * nothing is timed: among the configurations predicted within 10 % of the
@@ -481,6 +481,12 @@ int mpgemm_fault_fired(void);
    bit for every pair of doubles.  Device pointers (out: 3 count doubles);
    asynchronous on stream; MPGEMM_EINVAL for bad arguments. */
 int mpgemm_selftest_two_sum(int64_t count, const double* a, const double* b, double* out, void* stream);
+/* Self-test of the DD MAC's sum of its two error terms: for i < count,
+   out[i] = RN(a[i] + b[i]) as the kernels compute it on the integer pipe and
+   out[count + i] = the FP64 add; equal bit for bit for every pair of
+   doubles.  Device pointers (out: 2 count doubles); asynchronous on stream;
+   MPGEMM_EINVAL for bad arguments. */
+int mpgemm_selftest_dadd(int64_t count, const double* a, const double* b, double* out, void* stream);
 /* Self-test of the DD kernel's product error term: out[i] = RN(a[i] b[i]),
    out[count + i] = its rounding error as the kernel computes it (the
    integer-pipe form) and out[2 count + i] = fma(a[i], b[i], -out[i]).  The

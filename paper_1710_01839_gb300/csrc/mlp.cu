@@ -314,9 +314,10 @@ bool cost_model_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n,
 
 // The configurations predicted within (1 + margin) of the best, fastest
 // first, and the fastest of each algorithm family (simple, block, Strassen)
-// predicted within (1 + 2 margin), at most kmax; false without a model.
+// predicted within (1 + 2 margin) or below cheap_ms (cheap to time), at most
+// kmax; false without a model.
 bool cost_model_shortlist(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, double margin,
-                          int kmax, std::vector<Choice>* out, std::vector<float>* pred_ms) {
+                          double cheap_ms, int kmax, std::vector<Choice>* out, std::vector<float>* pred_ms) {
     {
         std::lock_guard<std::mutex> lk(g_mmu);
         if (!g_model.ready) return false;
@@ -335,7 +336,8 @@ bool cost_model_shortlist(int kind, int prec_bits, int64_t m, int64_t l, int64_t
     for (size_t k = 0; k < order.size() && (int)out->size() < kmax; k++) {
         const size_t i = order[k];
         const bool near = k == 0 || T[i] <= (1.0 + margin) * T[order[0]];
-        const bool family_best = !family[cs[i].algo] && T[i] <= (1.0 + 2.0 * margin) * T[order[0]];
+        const bool family_best =
+            !family[cs[i].algo] && (T[i] <= (1.0 + 2.0 * margin) * T[order[0]] || T[i] <= cheap_ms);
         if (!near && !family_best) continue;
         family[cs[i].algo] = true;
         out->push_back(Choice{cs[i].algo, cs[i].tile, cs[i].depth});

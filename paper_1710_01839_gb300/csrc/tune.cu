@@ -51,9 +51,11 @@ void remember_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, i
 static int g_auto_mode = 1;
 // The short list: configurations predicted within this fraction of the best
 // (about twice the model's 90th-percentile error on held-out timings) and
-// the best of each algorithm family within twice it, at most this many.
+// the best of each algorithm family within twice it or predicted cheap to
+// time, at most this many.
 constexpr double AUTO_MARGIN = 0.30;
-constexpr int AUTO_MAX_TIMED = 5;
+constexpr double AUTO_CHEAP_MS = 2.0;   // a family's best predicted below this is timed anyway
+constexpr int AUTO_MAX_TIMED = 6;
 
 // Replacement timer (mpgemm_tune_set_timer): simulated or recorded timings.
 static std::mutex g_timer_mu;
@@ -202,7 +204,8 @@ int auto_choice_measured(int kind, int prec_bits, int64_t m, int64_t l, int64_t 
     }
     std::vector<Choice> list;
     std::vector<float> pred;
-    if (!cost_model_shortlist(kind, prec_bits, m, l, n, sms, AUTO_MARGIN, AUTO_MAX_TIMED, &list, &pred) ||
+    if (!cost_model_shortlist(kind, prec_bits, m, l, n, sms, AUTO_MARGIN, AUTO_CHEAP_MS, AUTO_MAX_TIMED, &list,
+                              &pred) ||
         list.empty())
         return auto_choice(kind, prec_bits, m, l, n, sms, out);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

@@ -44,9 +44,11 @@ struct TuneKey {
     int sms;
 };
 // Cost model (mlp.cu): the configurations predicted within (1 + margin) of
-// the best, fastest first, at most kmax; false without a model.
+// the best, fastest first, and the best of each algorithm family predicted
+// within (1 + 2 margin) or below cheap_ms, at most kmax; false without a
+// model.
 bool cost_model_shortlist(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int sms, double margin,
-                          int kmax, std::vector<Choice>* out, std::vector<float>* pred_ms);
+                          double cheap_ms, int kmax, std::vector<Choice>* out, std::vector<float>* pred_ms);
 
 bool tune_cache_lookup_meas(const TuneKey& k, int algo, int n_min, int depth, int64_t rows, int reps, double* ms);
 void tune_cache_append_meas(const TuneKey& k, int algo, int n_min, int depth, int64_t rows, int reps, double ms);
