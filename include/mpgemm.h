@@ -481,12 +481,6 @@ int mpgemm_fault_fired(void);
    bit for every pair of doubles.  Device pointers (out: 3 count doubles);
    asynchronous on stream; MPGEMM_EINVAL for bad arguments. */
 int mpgemm_selftest_two_sum(int64_t count, const double* a, const double* b, double* out, void* stream);
-/* Self-test of the DD MAC's sum of its two error terms: for i < count,
-   out[i] = RN(a[i] + b[i]) as the kernels compute it on the integer pipe and
-   out[count + i] = the FP64 add; equal bit for bit for every pair of
-   doubles.  Device pointers (out: 2 count doubles); asynchronous on stream;
-   MPGEMM_EINVAL for bad arguments. */
-int mpgemm_selftest_dadd(int64_t count, const double* a, const double* b, double* out, void* stream);
 /* Self-test of the DD kernel's product error term: out[i] = RN(a[i] b[i]),
    out[count + i] = its rounding error as the kernel computes it (the
    integer-pipe form) and out[2 count + i] = fma(a[i], b[i], -out[i]).  The

@@ -38,7 +38,6 @@ SIGNATURES = {
     "mpgemm_selftest_wait_timeout": (_I, [_I, _P]),
     "mpgemm_fault_inject": (_I, [_I, ctypes.c_longlong]),
     "mpgemm_fault_fired": (_I, []),
-    "mpgemm_selftest_dadd": (_I, [_I64, _P, _P, _P, _P]),
     "mpgemm_partition_create": (_I, [_I, _P, _P]),
     "mpgemm_precision_log2_bound": (ctypes.c_double, [_I, _I, _I, _I64, _I]),
     "mpgemm_select_precision": (_I, [ctypes.c_double, _I64, _I64, _I64, _I, _P, _I]),

@@ -7,11 +7,9 @@
 //   DD:  state (s, t).  p = RN(ah bh) and its exact error e from one FMA,
 //        the two cross products accumulated into t with two more FMAs, then
 //        (s, r) = TwoSum(s, p) and t <- t + (e + r).  Every DD_RENORM steps
-//        (s, t) = TwoSum(s, t).  5 FP64 operations per step: the error
-//        terms of the product and of the exponent-ordered TwoSum below,
-//        and their sum (a correctly rounded add, bit-identical to the FP64
-//        one), run on the integer pipe (the library DD add + multiply pair
-//        costs 27).
+//        (s, t) = TwoSum(s, t).  6 FP64 operations per step: the error
+//        terms of the product and of the exponent-ordered TwoSum below run
+//        on the integer pipe (the library DD add + multiply pair costs 27).
 //        Worst-case error after l steps: about (DD_RENORM + 3) l u^2 sum|a||b|
 //        plus O(u^2) per product, inside the required 16 l u^2 |A||B|
 //        (= 4 l 2^-104 |A||B|) for DD_RENORM = 8.
@@ -104,55 +102,6 @@ __device__ __forceinline__ double two_prod_err(double a, double b, double p) {
     return __longlong_as_double((long long)((sgn << 63) | ((unsigned long long)F << 52) | ((m << (lz - 11)) & MM)));
 }
 
-// RN(x + y), bit-identical to __dadd_rn(x, y), on the integer pipe: the
-// textbook correctly rounded addition with three extra low bits (guard,
-// round, sticky).  The operands are ordered by magnitude (the bit patterns
-// of non-negative doubles order as their values), the smaller mantissa is
-// aligned with the bits shifted out ORed into the sticky bit, added or
-// subtracted, normalised (one bit right after a carry, left after a
-// cancellation, which loses more than one bit only when the exponents
-// differ by at most one and the difference is exact), and rounded to
-// nearest, ties to even.  The sum of two normal doubles with exponent fields
-// below 0x7fe cannot overflow.  A zero operand is handled here (x + 0 = x;
-// the sum of two zeros is -0 only for two -0); a subnormal, infinite or NaN
-// operand, an exponent field of 0x7fe or a subnormal result take the FP64
-// add.
-__device__ __forceinline__ double dadd_int(double x, double y) {
-    constexpr unsigned long long SGN = 1ull << 63, MM = (1ull << 52) - 1ull, H = 1ull << 52;
-    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long by = (unsigned long long)__double_as_longlong(y);
-    const unsigned long long ax = bx & ~SGN, ay = by & ~SGN;
-    const bool sw = ay > ax;
-    const unsigned long long bl = sw ? by : bx, bs = sw ? bx : by;   // larger and smaller magnitude
-    const unsigned long long al = sw ? ay : ax, as = sw ? ax : ay;
-    const int El = (int)(al >> 52), Es = (int)(as >> 52);
-    if (Es == 0) {
-        if (as == 0 && El != 0x7ff) return __longlong_as_double((long long)(al == 0 ? (bx & by & SGN) : bl));
-        return __dadd_rn(x, y);
-    }
-    if (El >= 0x7fe) return __dadd_rn(x, y);
-    const int d = El - Es < 63 ? El - Es : 63;
-    const unsigned long long X = ((al & MM) | H) << 3;             // 56 bits
-    const unsigned long long Y = ((as & MM) | H) << 3;
-    const unsigned long long lost = d == 0 ? 0ull : (Y << ((64 - d) & 63));
-    const unsigned long long Ya = (Y >> d) | (lost != 0ull ? 1ull : 0ull);
-    const bool sub = ((bl ^ bs) >> 63) != 0ull;
-    unsigned long long S = sub ? X - Ya : X + Ya;                   // < 2^57
-    if (S == 0ull) return 0.0;                                     // exact cancellation: +0
-    const int sh = __clzll((long long)S) - 8;                       // leading bit to bit 55
-    int E = El - sh;
-    S = sh < 0 ? ((S >> 1) | (S & 1ull)) : (S << sh);
-    if (E <= 0) return __dadd_rn(x, y);
-    const unsigned low = (unsigned)(S & 7ull);
-    S >>= 3;
-    S += (low > 4u || (low == 4u && (S & 1ull))) ? 1ull : 0ull;
-    if (S >> 53) {   // rounded up into the next binade
-        S >>= 1;
-        E += 1;
-    }
-    return __longlong_as_double((long long)((bl & SGN) | ((unsigned long long)E << 52) | (S & MM)));
-}
-
 // TwoSum: s = RN(a + b), e = a + b - s exactly, for any a, b.  Computed as
 // Dekker's Fast2Sum after ordering the operands by their exponent fields,
 // compared on the integer pipe, with the error term on the integer pipe as
@@ -206,7 +155,7 @@ __device__ __forceinline__ void dd_mac(DDAcc& c, double ah, double al, double bh
     double s, r;
     two_sum(c.s, p, s, r);
     c.s = s;
-    c.t = __dadd_rn(t, dadd_int(e, r));   // the two error terms summed on the integer pipe
+    c.t = __dadd_rn(t, __dadd_rn(e, r));
 }
 
 __device__ __forceinline__ void dd_renorm(DDAcc& c) {

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_simple(int64_t m, int64_t l, int64_t n,
 // One CTA computes a BM x BM block of C (ddqd_block_tile); CTA order follows
 // the super-tile raster with group G (n_min / BM when n_min > BM).
 template <class Fmt, int BM, int RM, int KT>
-__global__ void __launch_bounds__((BM / RM) * (BM / RM), BM == 64 ? 1 : 0) k_block(int64_t m, int64_t l, int64_t n,
+__global__ void __launch_bounds__((BM / RM) * (BM / RM)) k_block(int64_t m, int64_t l, int64_t n,
                                                                  View<const double> A, View<const double> B,
                                                                  View<double> C, unsigned G) {
     __shared__ __align__(16) double sm[ddqd_tile_doubles<Fmt, BM, KT>()];
@@ -99,15 +99,6 @@ int ddqd_gemm(int kind, int algo, int64_t m, int64_t l, int64_t n, int64_t batch
     return launch_block_cfg<QDFmt, 32, 2, 8>(m, l, n, batch, A, B, C, n_min, s);
 }
 
-// The integer-pipe RN(x + y) against the FP64 add, element by element
-// (mpgemm_selftest_dadd).
-__global__ void k_selftest_dadd(int64_t count, const double* a, const double* b, double* out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    out[i] = dadd_int(a[i], b[i]);
-    out[count + i] = __dadd_rn(a[i], b[i]);
-}
-
 // TwoSum with the integer-pipe error term against the FP64 formula, element
 // by element (mpgemm_selftest_two_sum).
 __global__ void k_selftest_two_sum(int64_t count, const double* a, const double* b, double* out) {
@@ -141,15 +132,6 @@ extern "C" int mpgemm_selftest_two_prod(int64_t count, const double* a, const do
     cudaStream_t s = (cudaStream_t)stream;
     mpg::PartitionScope pscope(s);
     mpg::k_selftest_two_prod<<<mpg::ceil_div(count, 256), 256, 0, s>>>(count, a, b, out);
-    return mpg::check_launch();
-}
-
-extern "C" int mpgemm_selftest_dadd(int64_t count, const double* a, const double* b, double* out, void* stream) {
-    if (count < 0 || (count && (!a || !b || !out))) return MPGEMM_EINVAL;
-    if (count == 0) return MPGEMM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    mpg::PartitionScope pscope(s);
-    mpg::k_selftest_dadd<<<mpg::ceil_div(count, 256), 256, 0, s>>>(count, a, b, out);
     return mpg::check_launch();
 }
 

@@ -164,84 +164,3 @@ def test_two_prod_rule_is_the_exact_error():
     # underflowing or overflowing products are routed to the FMA
     assert two_prod_err_int(2.0 ** -600, 2.0 ** -600, 2.0 ** -600 * 2.0 ** -600) is None
     assert two_prod_err_int(2.0 ** 600, 2.0 ** 600, math.inf) is None
-
-
-# ------------------------------------------------------------------ the integer-pipe RN(x + y)
-
-SGN, MM52, H52, M64 = 1 << 63, (1 << 52) - 1, 1 << 52, (1 << 64) - 1
-
-
-def dadd_int(x, y):
-    """The DD MAC's sum of its two error terms as the kernel computes it
-    (guard, round and sticky bits, round to nearest even), restated in
-    Python integers; None where the kernel takes the FP64 add."""
-    bx, by = bits(x), bits(y)
-    ax, ay = bx & ~SGN & M64, by & ~SGN & M64
-    sw = ay > ax
-    bl, bs = (by, bx) if sw else (bx, by)
-    al, as_ = (ay, ax) if sw else (ax, ay)
-    El, Es = al >> 52, as_ >> 52
-    if Es == 0:
-        if as_ == 0 and El != 0x7ff:
-            return from_bits(bx & by & SGN) if al == 0 else from_bits(bl)
-        return None
-    if El >= 0x7fe:
-        return None
-    d = min(El - Es, 63)
-    X, Y = ((al & MM52) | H52) << 3, ((as_ & MM52) | H52) << 3
-    lost = 0 if d == 0 else (Y << (64 - d)) & M64
-    Ya = (Y >> d) | (1 if lost else 0)
-    S = X - Ya if (bl ^ bs) >> 63 else X + Ya
-    if S == 0:
-        return 0.0
-    sh = (64 - S.bit_length()) - 8
-    E = El - sh
-    S = (S >> 1) | (S & 1) if sh < 0 else (S << sh) & M64
-    if E <= 0:
-        return None
-    low, S = S & 7, S >> 3
-    if low > 4 or (low == 4 and S & 1):
-        S += 1
-    if S >> 53:
-        S, E = S >> 1, E + 1
-    return from_bits((bl & SGN) | (E << 52) | (S & MM52))
-
-
-def _rn_of_exact_sum(x, y):
-    """RN(x + y) from the exact rational sum (Python's float() of a Fraction
-    rounds correctly, ties to even)."""
-    s = Fraction(x) + Fraction(y)
-    if s == 0:
-        return 0.0 if not (math.copysign(1, x) < 0 and math.copysign(1, y) < 0) else -0.0
-    return float(s)
-
-
-@pytest.mark.parametrize("spread", [0, 1, 2, 3, 30, 54, 55, 56, 60, 200])
-def test_integer_add_rule_is_correct_rounding(spread):
-    rng = np.random.default_rng(500 + spread)
-    fallback = 0
-    for _ in range(4000):
-        x = float(rng.uniform(1, 2) * 2.0 ** int(rng.integers(-300, 300))) * float(rng.choice([-1.0, 1.0]))
-        y = x * float(rng.uniform(0.5, 2)) * 2.0 ** -int(rng.integers(0, spread + 1)) * float(rng.choice([-1.0, 1.0]))
-        for a, b in ((x, y), (y, x)):
-            r = dadd_int(a, b)
-            if r is None:
-                fallback += 1
-                continue
-            assert bits(r) == bits(_rn_of_exact_sum(a, b)), (a, b)
-    assert fallback == 0
-
-
-def test_integer_add_rule_edge_cases():
-    ulp1 = 2.0 ** -52
-    cases = [(1.0, ulp1 / 2), (1.0, ulp1 / 2 * 3), (1.0 + ulp1, ulp1 / 2), (1.0, -ulp1 / 4), (1.0, -ulp1 / 2),
-             (2.0 - ulp1, ulp1 / 2), (2.0 - ulp1, ulp1), (1.0, -1.0), (0.0, -0.0), (-0.0, -0.0), (-0.0, 3.5),
-             (1.5, -1.5 + ulp1), (2.0 ** 1000, -2.0 ** 1000 * (1 - ulp1)), (1.0, 2.0 ** -60), (1.0, -2.0 ** -60),
-             (3.0, -1.5000000000000002), (1e300, 1e300)]
-    for a, b in cases:
-        for x, y in ((a, b), (b, a)):
-            r = dadd_int(x, y)
-            assert r is not None and bits(r) == bits(_rn_of_exact_sum(x, y)), (x, y)
-    # the FP64 add is taken for subnormal, infinite, NaN and near-overflow operands
-    for x, y in ((5e-324, 1.0), (math.inf, 1.0), (math.nan, 1.0), (1.7976931348623157e308, 1.0)):
-        assert dadd_int(x, y) is None and dadd_int(y, x) is None

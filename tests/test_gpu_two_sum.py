@@ -126,73 +126,3 @@ def test_product_error_crafted_pairs():
     a, b = np.meshgrid(vals, vals, indexing="ij")
     p, e_int, e_fma = _run_prod(a.ravel(), b.ravel())
     assert np.array_equal(_bits(e_int), _bits(e_fma))
-
-
-# ---------------------------------------------------------------- the DD MAC's integer-pipe add
-
-def _run_dadd(a, b):
-    import ctypes
-    import torch
-    a = np.ascontiguousarray(a, dtype=np.float64)
-    b = np.ascontiguousarray(b, dtype=np.float64)
-    out = torch.empty(2 * len(a), dtype=torch.float64, device="cuda")
-    ad, bd = dev(a), dev(b)
-    rc = mpg.lib().mpgemm_selftest_dadd(len(a), ctypes.c_void_p(ad.data_ptr()), ctypes.c_void_p(bd.data_ptr()),
-                                        ctypes.c_void_p(out.data_ptr()), None)
-    assert rc == 0
-    o = out.cpu().numpy().reshape(2, -1)
-    return o[0], o[1]
-
-
-def _same(x, y):
-    """Bit-identical, with every NaN counted as equal to every NaN."""
-    nx, ny = np.isnan(x), np.isnan(y)
-    return np.array_equal(nx, ny) and np.array_equal(_bits(x[~nx]), _bits(y[~ny]))
-
-
-def test_integer_add_random_pairs_over_the_exponent_range():
-    rng = np.random.default_rng(2025)
-    n = 1 << 20
-    bits = rng.integers(0, 2**63, size=(2, n), dtype=np.uint64) | (rng.integers(0, 2, size=(2, n), dtype=np.uint64) << np.uint64(63))
-    r_int, r_fp = _run_dadd(bits[0].view(np.float64), bits[1].view(np.float64))
-    assert _same(r_int, r_fp)
-
-
-@pytest.mark.parametrize("spread", [0, 1, 2, 3, 20, 53, 54, 55, 56, 60, 120])
-def test_integer_add_close_exponents_and_cancellation(spread):
-    rng = np.random.default_rng(300 + spread)
-    n = 1 << 18
-    a = rng.uniform(1, 2, n) * np.ldexp(1.0, rng.integers(-1000, 1000, n)) * rng.choice([-1.0, 1.0], n)
-    b = rng.uniform(0.5, 2, n) * np.ldexp(a, -rng.integers(0, spread + 1, n)) * rng.choice([-1.0, 1.0], n)
-    # near-cancellations: b = -a perturbed in its last bits
-    c = -(a.view(np.uint64) ^ rng.integers(0, 8, n, dtype=np.uint64)).view(np.float64)
-    r_int, r_fp = _run_dadd(np.concatenate([a, b, a]), np.concatenate([b, a, c]))
-    assert _same(r_int, r_fp)
-
-
-def test_integer_add_crafted_pairs():
-    tiny, big = np.ldexp(1.0, -1074), np.finfo(np.float64).max
-    u = 2.0 ** -52
-    vals = [0.0, -0.0, 1.0, -1.0, 1.0 + u, 2.0 - u, u / 2, 3 * u / 2, -u / 4, tiny, -tiny, 2.0 ** -1022,
-            2.0 ** -1022 * (1 + u), big, -big, big / 2, np.inf, -np.inf, np.nan, 2.0 ** 1023, 1.5, -1.5 + u]
-    a = np.array([x for x in vals for _ in vals])
-    b = np.array([y for _ in vals for y in vals])
-    r_int, r_fp = _run_dadd(a, b)
-    assert _same(r_int, r_fp)
-
-
-def test_integer_add_dd_mac_operands():
-    """Pairs (e, r) as the DD multiply-accumulate forms them: the exact
-    product error and the TwoSum error of random DD operands."""
-    from fractions import Fraction
-    rng = np.random.default_rng(77)
-    n = 1 << 15
-    ah = rng.uniform(-1, 1, n) * np.ldexp(1.0, rng.integers(-20, 21, n))
-    bh = rng.uniform(-1, 1, n) * np.ldexp(1.0, rng.integers(-20, 21, n))
-    s = rng.uniform(-1, 1, n) * np.ldexp(1.0, rng.integers(-10, 30, n))
-    p = ah * bh
-    e = np.array([float(Fraction(x) * Fraction(y) - Fraction(q)) for x, y, q in zip(ah, bh, p)])   # exact
-    sp = s + p
-    r = (s - (sp - p)) + (p - (sp - (sp - p)))   # Knuth's TwoSum error
-    r_int, r_fp = _run_dadd(e, r)
-    assert _same(r_int, r_fp)
