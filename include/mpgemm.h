@@ -312,8 +312,9 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
  * the best (about twice the model's 90th-percentile error) and no other
  * algorithm's best within 60 % or predicted below 2 ms, that one; else
  * those candidates (the ones within 30 % and the best of each algorithm
- * within 60 % or below 2 ms, at most 6) are timed once on the call's own
- * operands and the fastest is remembered for the shape (and appended to
+ * within 60 % or below 2 ms, at most 6) are timed on the call's own
+ * operands (10 / 3 / 1 back-to-back runs for predictions below 1 / 20 ms /
+ * above) and the fastest is remembered for the shape (and appended to
  * the tuning cache when one is open), so the first such call
  * is synchronous and writes C more than once.  While the stream captures a
  * graph, or in model-only mode (mpgemm_auto_mode(0); 1 restores timing),
@@ -373,7 +374,8 @@ int mpgemm_set_workspace(void* dev_ptr, size_t bytes);
  *   2. keep the n_min with the smallest prediction;
  *   3. time simple, block(n_min) and Strassen depths 1..3 (leaves at n_min)
  *      and report the fastest.
- * Timings are medians of 3 event-timed runs (1 with MPGEMM_TUNE_QUICK).
+ * Each timing is the time per run of 3 runs issued back to back after a
+ * warm-up run (1 with MPGEMM_TUNE_QUICK): the steady-state cost of a call.
  * With MPGEMM_TUNE_REMEMBER the choice is stored for this (kind, prec_bits,
  * m, l, n, SMs of the stream) and used by MPGEMM_AUTO on streams with as
  * many SMs.  Synchronous; returns MPGEMM_OK or an

@@ -139,27 +139,28 @@ int run_once(const Problem& P, int algo, int n_min, int depth, int64_t rows) {
     return ddqd_gemm(P.kind, algo, rows, P.l, P.n, 1, a, b, c, n_min, P.s);
 }
 
-// Median of `reps` event-timed runs after one warm-up, in ms.
+// Time per run, in ms, of `reps` runs issued back to back between two
+// events (after one warm-up run): the steady-state cost of a repeated call,
+// with the host's launch overhead overlapped by the device's work as it is
+// in a loop of calls.
 int time_it(const Problem& P, int algo, int n_min, int depth, int64_t rows, int reps, double* ms) {
     cudaEvent_t e0, e1;
     MPG_CUDA(cudaEventCreate(&e0));
     MPG_CUDA(cudaEventCreate(&e1));
     int rc = run_once(P, algo, n_min, depth, rows);
-    std::vector<double> t;
-    for (int i = 0; i < reps && rc == MPGEMM_OK; i++) {
+    if (rc == MPGEMM_OK && cudaStreamSynchronize(P.s) != cudaSuccess) rc = MPGEMM_ECUDA;
+    float f = 0.f;
+    if (rc == MPGEMM_OK) {
         cudaEventRecord(e0, P.s);
-        rc = run_once(P, algo, n_min, depth, rows);
+        for (int i = 0; i < reps && rc == MPGEMM_OK; i++) rc = run_once(P, algo, n_min, depth, rows);
         cudaEventRecord(e1, P.s);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = MPGEMM_ECUDA;
-        float f = 0.f;
         cudaEventElapsedTime(&f, e0, e1);
-        t.push_back(f);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    std::sort(t.begin(), t.end());
-    *ms = t.empty() ? 0.0 : t[t.size() / 2];
+    *ms = reps > 0 ? (double)f / reps : 0.0;
     return MPGEMM_OK;
 }
 
@@ -226,7 +227,7 @@ int auto_choice_measured(int kind, int prec_bits, int64_t m, int64_t l, int64_t 
     double best_ms = 0.0;
     for (size_t i = 0; i < list.size(); i++) {
         const float p = pred[i];
-        const int reps = p < 1.0f ? 5 : p < 20.0f ? 3 : 1;
+        const int reps = p < 1.0f ? 10 : p < 20.0f ? 3 : 1;
         double ms = 0.0;
         int rc = measure(P, key, list[i].algo, list[i].n_min, list[i].depth, m, reps, &ms, &measured);
         if (rc) return rc;

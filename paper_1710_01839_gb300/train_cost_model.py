@@ -43,22 +43,33 @@ def _time(fn, reps=3):
     return float(np.median(ts))
 
 
-def _time_interleaved(fns, reps=5):
-    """Median ms of each function, timed round-robin (rep r of every
-    function before rep r + 1 of any), after one untimed call each."""
+def _time_interleaved(fns, reps=5, window_ms=1.0):
+    """Steady-state ms per call of each function: calls issued back to back
+    between two events, enough of them to fill about `window_ms` (at most
+    20), the windows of all functions timed round-robin `reps` times (round
+    r of every function before round r + 1 of any); median over rounds."""
     import torch
+    counts = []
     for f in fns:
         f()
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        f()
+        b.record()
+        torch.cuda.synchronize()
+        counts.append(max(1, min(20, int(window_ms / max(a.elapsed_time(b), 1e-3)))))
     ts = [[] for _ in fns]
     for _ in range(reps):
         for i, f in enumerate(fns):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
             a.record()
-            f()
+            for _ in range(counts[i]):
+                f()
             b.record()
             torch.cuda.synchronize()
-            ts[i].append(a.elapsed_time(b))
+            ts[i].append(a.elapsed_time(b) / counts[i])
     return [float(np.median(t)) for t in ts]
 
 
