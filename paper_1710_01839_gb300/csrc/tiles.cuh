@@ -216,7 +216,49 @@ __device__ __forceinline__ void mp_block_tile(int64_t m, int64_t l, int64_t n, c
     const int tid = threadIdx.x, ty = tid / BM, tx = tid % BM;
     MPV<W> c;
     mp_set_zero(c, 0u);
+    // 128 / 256 bits (KT = 8): a panel holds 128 elements of A and 128 of B,
+    // one per thread, staged whole: threads 0..127 take A's (row r, k offset
+    // cc), rows fastest (consecutive threads write consecutive 16-byte
+    // aligned elements: at most 2-way bank conflicts), threads 128..255 take
+    // B's (k offset rb, column cb), columns fastest (coalesced reads).  The
+    // element's address is formed once; per panel only k moves.
+    constexpr bool kWhole = (W % 4 == 0) && (W < MP_STREAM_LIMBS) && (KT == 8) && (OFF == 4);
+    const bool sA = tid < 128;
+    const int el = tid & 127;
+    const int er = sA ? (el & 15) : (el >> 4), ec = sA ? (el >> 4) : (el & 15);   // A: (r, cc); B: (rb, cb)
+    const uint32_t* gbase = nullptr;
+    bool fixed_ok = false;
+    int64_t ps = 0;
+    uint32_t* sdst = nullptr;
+    if constexpr (kWhole) {
+        if (sA) {
+            fixed_ok = i0 + er < m;
+            gbase = A.p + z * A.bs + (fixed_ok ? (i0 + er) * A.ld : 0);
+            ps = A.ps;
+            sdst = &As[ec][er][0];
+        } else {
+            fixed_ok = j0 + ec < n;
+            gbase = B.p + z * B.bs + (fixed_ok ? j0 + ec : 0);
+            ps = B.ps;
+            sdst = &Bs[er][ec][0];
+        }
+    }
     for (int64_t k0 = 0; k0 < l; k0 += KT) {
+        if constexpr (kWhole) {
+            const int64_t k = k0 + (sA ? ec : er);
+            const bool ok = fixed_ok && k < l;
+            const uint32_t* src = gbase + (sA ? k : k * B.ld);
+            uint32_t w[OFF + W];
+            w[0] = ok ? __ldg(src) : 0u;
+            w[1] = ok ? __ldg(src + ps) : 2u;   // flags: zero
+            w[2] = 0u;
+            w[3] = 0u;
+MP_UNROLL
+            for (int q = 0; q < W; q++) w[OFF + q] = ok ? __ldg(src + (2 + q) * ps) : 0u;
+MP_UNROLL
+            for (int q = 0; q < OFF + W; q += 4)
+                *reinterpret_cast<uint4*>(sdst + q) = make_uint4(w[q], w[q + 1], w[q + 2], w[q + 3]);
+        } else
         for (int idx = tid; idx < WORDS; idx += 256) {
             int q = idx / (BM * KT), rem = idx % (BM * KT);
             int slot = q < 2 ? q : q - 2 + OFF;
