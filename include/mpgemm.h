@@ -314,7 +314,8 @@ int mpgemm_batched_sequential(const mpgemm_desc* descs, int count, void* stream)
  * those candidates (the ones within 30 % and the best of each algorithm
  * within 60 % or below 2 ms, at most 6) are timed on the call's own
  * operands (10 / 3 / 1 back-to-back runs for predictions below 1 / 20 ms /
- * above) and the fastest is remembered for the shape (and appended to
+ * above; among those within 3 % of the fastest, the fewest launches) and
+ * that one is remembered for the shape (and appended to
  * the tuning cache when one is open), so the first such call
  * is synchronous and writes C more than once.  While the stream captures a
  * graph, or in model-only mode (mpgemm_auto_mode(0); 1 restores timing),
@@ -436,6 +437,13 @@ typedef double (*mpgemm_timer_fn)(void* ctx, int kind, int prec_bits, int64_t m,
                                   int n_min, int depth, int64_t rows, int reps);
 int mpgemm_tune_set_timer(mpgemm_timer_fn fn, void* ctx);
 int mpgemm_auto_mode(int mode);
+/* The tuner's timer for one configuration: *ms = the time per call of
+   `reps` calls (1..1000) of (algo, n_min, depth) on the operands, issued
+   back to back between two events on `stream` after one warm-up call (C is
+   overwritten).  Synchronous.  The timer mpgemm_tune and MPGEMM_AUTO use,
+   for comparisons on the same footing. */
+int mpgemm_time_config(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const void* A, const void* B,
+                       void* C, int algo, int n_min, int depth, int reps, void* stream, double* ms);
 /* The (algo, n_min, depth) MPGEMM_AUTO would use for this problem on the
    whole device. */
 int mpgemm_auto_choice(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, int* algo, int* n_min,

@@ -223,19 +223,26 @@ int auto_choice_measured(int kind, int prec_bits, int64_t m, int64_t l, int64_t 
         return auto_choice(kind, prec_bits, m, l, n, sms, out);   // the model's rule, nothing timed
     Problem P{kind, kind == MPGEMM_KIND_MP ? prec_bits : 0, m, l, n, A, B, C, s};
     const TuneKey key{kind, P.prec_bits, m, l, n, sms};
-    int measured = 0, best = -1;
-    double best_ms = 0.0;
+    int measured = 0;
+    std::vector<double> t(list.size());
     for (size_t i = 0; i < list.size(); i++) {
         const float p = pred[i];
         const int reps = p < 1.0f ? 10 : p < 20.0f ? 3 : 1;
-        double ms = 0.0;
-        int rc = measure(P, key, list[i].algo, list[i].n_min, list[i].depth, m, reps, &ms, &measured);
+        int rc = measure(P, key, list[i].algo, list[i].n_min, list[i].depth, m, reps, &t[i], &measured);
         if (rc) return rc;
-        if (best < 0 || ms < best_ms) {
-            best = (int)i;
-            best_ms = ms;
-        }
     }
+    // the fastest; among those within 3 % of it (timing noise), the fewest
+    // launches (a caller with more launch overhead than this timer pays less)
+    const double tmin = *std::min_element(t.begin(), t.end());
+    auto launches = [](const Choice& c) { return c.algo == MPGEMM_STRASSEN ? 3 * c.depth + 1 : 1; };
+    int best = -1;
+    for (size_t i = 0; i < list.size(); i++) {
+        if (t[i] > 1.03 * tmin) continue;
+        if (best < 0 || launches(list[i]) < launches(list[best]) ||
+            (launches(list[i]) == launches(list[best]) && t[i] < t[best]))
+            best = (int)i;
+    }
+    const double best_ms = t[best];
     *out = list[best];
     remember_choice(kind, P.prec_bits, m, l, n, sms, *out);
     mpgemm_tune_report rep;
@@ -355,6 +362,17 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
     tune_cache_append_choice(key, rep);
     rep->tuning_ms = wall_ms();
     return MPGEMM_OK;
+}
+
+int mpgemm_time_config(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const void* A, const void* B,
+                       void* C, int algo, int n_min, int depth, int reps, void* stream, double* ms) {
+    if (!ms || m <= 0 || l <= 0 || n <= 0 || !A || !B || !C || reps < 1 || reps > 1000) return MPGEMM_EINVAL;
+    if (kind < MPGEMM_KIND_DD || kind > MPGEMM_KIND_MP) return MPGEMM_EINVAL;
+    if (kind == MPGEMM_KIND_MP && (prec_bits <= 0 || prec_bits % 32)) return MPGEMM_EINVAL;
+    if (algo < MPGEMM_SIMPLE || algo > MPGEMM_STRASSEN || n_min < 1 || depth < 0 || depth > 4) return MPGEMM_EINVAL;
+    Problem P{kind, kind == MPGEMM_KIND_MP ? prec_bits : 0, m, l, n, A, B, C, (cudaStream_t)stream};
+    PartitionScope pscope(P.s);
+    return time_it(P, algo, n_min, algo == MPGEMM_STRASSEN ? depth : 0, m, reps, ms);
 }
 
 int mpgemm_auto_mode(int mode) {

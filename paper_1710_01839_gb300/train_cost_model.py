@@ -73,6 +73,37 @@ def _time_interleaved(fns, reps=5, window_ms=1.0):
     return [float(np.median(t)) for t in ts]
 
 
+def _time_library(kind, bits, m, l, n, Ad, Bd, Cd, cands, reps=5):
+    """Each candidate (algo, n_min, depth) timed with the library's own timer
+    (mpgemm_time_config: calls back to back between two events, from C, as
+    MPGEMM_AUTO times its short list), 10 / 3 / 1 calls per window for
+    candidates below 1 / 20 ms / above, windows round-robin over the
+    candidates `reps` times; median over rounds."""
+    import ctypes
+    import paper_1710_01839_gb300 as mpg
+    L = mpg.lib()
+    codes = {"simple": 0, "block": 1, "strassen": 2}
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    def one(c, r):
+        ms = ctypes.c_double()
+        rc = L.mpgemm_time_config(kind, bits, m, l, n, p(Ad), p(Bd), p(Cd), codes[c[0]], c[1], c[2], r, None,
+                                  ctypes.byref(ms))
+        if rc:
+            raise RuntimeError(f"mpgemm_time_config: {mpg.strerror(rc)}")
+        return ms.value
+
+    calls = []
+    for c in cands:
+        t = one(c, 1)
+        calls.append(10 if t < 1.0 else 3 if t < 20.0 else 1)
+    ts = [[] for _ in cands]
+    for _ in range(reps):
+        for i, c in enumerate(cands):
+            ts[i].append(one(c, calls[i]))
+    return [float(np.median(t)) for t in ts]
+
+
 def batched_like_shapes(count, seed=2024, min_dim=16, max_dim=1024):
     """(fmt, bits, m, l, n): m, l, n log-uniform in [min_dim, max_dim] (the
     batched workload's recipe), formats cycling DD, QD, 256-bit, 128-bit."""
@@ -88,7 +119,8 @@ def batched_like_shapes(count, seed=2024, min_dim=16, max_dim=1024):
 def auto_regret_study(shapes, reps=5):
     """MPGEMM_AUTO's pick (the cost model, with its short list timed on the
     operands when the model is not sure) against every candidate timed
-    exhaustively, one GEMM at a time; also the model's pick alone."""
+    exhaustively with the library's timer (_time_library), one GEMM at a
+    time; also the model's pick alone."""
     import ctypes
     import torch
     import paper_1710_01839_gb300 as mpg
@@ -131,7 +163,8 @@ def auto_regret_study(shapes, reps=5):
         for c in (auto, rule):
             if c not in cands:
                 cands.append(c)
-        meas = _time_interleaved([run(*c) for c in cands], reps)
+        Cd = torch.empty((Ad.shape[0], m, n), dtype=Ad.dtype, device="cuda")
+        meas = _time_library(kind, bits, m, l, n, Ad, Bd, Cd, cands, reps)
         best = int(np.argmin(meas))
         t_auto, t_rule = meas[cands.index(auto)], meas[cands.index(rule)]
         rows.append({"fmt": fmt if fmt != "mp" else f"mp{bits}", "m": m, "l": l, "n": n, "auto_pick": auto,

@@ -4,11 +4,13 @@ error of the best it times that short list once on the operands (the
 paper's Section 3 idea: predict to prune, time the finalists).  On a fixed
 subset of 24 shapes drawn like the batched workload (m, l, n log-uniform in
 [16, 1024]; DD, QD, 256- and 128-bit), every pick must be within 10 % of the
-fastest configuration timed exhaustively.  Both sides time the steady-state
-cost of a call (calls issued back to back between two events, so the host's
-launch overhead overlaps the device's work as in a loop of calls; the
-exhaustive side takes medians of interleaved windows); a difference below 3
-microseconds, the size of launch jitter, counts as a tie."""
+fastest configuration timed exhaustively.  Both sides use the library's
+timer (calls issued back to back from C between two events, the
+steady-state cost of a call; the exhaustive side takes medians of windows
+interleaved over the candidates): at sizes of a few tens of microseconds a
+timer in Python would measure its own per-call overhead instead.  A
+difference below 3 microseconds, the size of launch jitter, counts as a
+tie."""
 
 import os
 
