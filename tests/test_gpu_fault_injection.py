@@ -120,7 +120,9 @@ def test_batched_plan_allocation_faults():
         probs.append((fmt, dev(A), dev(B), torch.zeros((planes, m, n), dtype=dt, device="cuda")))
     L = mpg.lib()
     for integer_pipe in (False, True):
-        descs = batched.make_descs(probs, integer_pipe=integer_pipe)
+        # explicit tiles: with tile 0 the plan would ask the cost model, whose
+        # own prediction buffers are allocations that fail gracefully
+        descs = batched.make_descs(probs, tiles=[16, 32, 16, 32], integer_pipe=integer_pipe)
         batched.sequential(descs)
         want = [host(c).copy() for _, _, _, c in probs]
         # every allocation the plan makes fails in turn; the plan is not created
