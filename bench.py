@@ -55,7 +55,7 @@ ISSUE_PEAK_GWIPS = 4 * 152 * 2.070
 # Multi-limb thread-instructions per multiply-accumulate (ncu
 # smsp__inst_executed x 32 / MACs of the block kernel k_mp_block on 256^3
 # (2048 bits: 128^3) inputs of the multi-limb workload), by precision in bits.
-MP_INSTR_PER_MAC = {128: 242.7, 256: 403.6, 512: 963.6, 1024: 2610.1, 2048: 8472.3}
+MP_INSTR_PER_MAC = {128: 232.2, 256: 376.7, 512: 963.6, 1024: 2610.1, 2048: 8472.3}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from ncu captures of exactly these configurations (profiles/):
 # (fmt, n, algo, n_min, depth) -> bytes.  Absent => null.

@@ -326,10 +326,8 @@ __device__ __forceinline__ void mp_mul(const MPV<W>& x, const MPV<W>& y, MPV<W>&
 // threads of a warp (whose operands differ in d and sign at random in a
 // GEMM) do not diverge: d is clamped to p + 2 (from there on |y| is below a
 // quarter of x's ulp and the frame below rounds to x, which is RN(x + y) for
-// every larger d as well), y is aligned by the barrel shifter (by a plain
-// funnel shift when d < 32 on every active thread of the warp, a warp-wide
-// decision), and the sum and the difference are one carry chain
-// X + (Y xor mask) + carry-in.
+// every larger d as well), y is aligned by the barrel shifter, and the sum
+// and the difference are one carry chain X + (Y xor mask) + carry-in.
 template <int W>
 __device__ __forceinline__ void mp_add(const MPV<W>& a, const MPV<W>& b, MPV<W>& r, unsigned& status) {
     constexpr int p = 32 * W;
@@ -359,16 +357,7 @@ MP_UNROLL
     X[N - 1] = 0u;
     Y[N - 1] = 0u;
     uint32_t sticky = 0u;
-    if (__all_sync(__activemask(), d < 32)) {
-        // every active thread of the warp aligns within one limb (operands
-        // of similar magnitude): no limb moves, and the guard limb keeps
-        // every shifted-out bit (no sticky)
-MP_UNROLL
-        for (int i = 0; i < N - 1; i++) Y[i] = __funnelshift_r(Y[i], Y[i + 1], d);
-        Y[N - 1] >>= d;
-    } else {
-        shr_sticky<N, W>(Y, d, sticky);   // d <= p + 2: at most W limbs move
-    }
+    shr_sticky<N, W>(Y, d, sticky);   // d <= p + 2: at most W limbs move
     const bool stk = sticky != 0u;
     // sum, or X - Y - stk (the dropped part of y then leaves a positive
     // remainder below S's last bit, kept as sticky) as X + ~Y + 1 - stk
