@@ -88,6 +88,32 @@ int mpgemm_qd(int64_t m, int64_t l, int64_t n, const double* A, const double* B,
 int mpgemm_mp(int64_t m, int64_t l, int64_t n, int prec_bits, const uint32_t* A, const uint32_t* B,
               uint32_t* C, int algo, int n_min, int strassen_depth, void* stream);
 
+/* Which kernel runs the block algorithm (and Strassen's leaves) of
+ * mpgemm_mp at 512, 1024 and 2048 bits (other widths and the simple
+ * algorithm are unaffected):
+ *   MPGEMM_MP_LEAF_THREAD  one thread per element of C, the w limbs of every
+ *                          value in that thread's registers;
+ *   MPGEMM_MP_LEAF_TEAM    a team of w / 8 lanes of a warp per element of C,
+ *                          8 limbs per lane; products by operand scanning with
+ *                          the partial sums passed between lanes by warp
+ *                          shuffles, carries between lanes by a look-ahead on
+ *                          warp ballots;
+ *   MPGEMM_MP_LEAF_DEFAULT the team kernel when the one-thread kernel's
+ *                          grid (16 x 16 elements of C per CTA, times the
+ *                          batch) has at most one CTA for every two SMs of
+ *                          the stream's partition, else the one-thread kernel.
+ * Both kernels keep Eq 1's operation sequence and give the same bits.
+ * Process-wide, not tied to a stream: set it between calls.  Returns the
+ * previous setting, MPGEMM_EINVAL for any other value. */
+typedef enum { MPGEMM_MP_LEAF_DEFAULT = 0, MPGEMM_MP_LEAF_THREAD = 1, MPGEMM_MP_LEAF_TEAM = 2 } mpgemm_mp_leaf;
+int mpgemm_set_mp_leaf(int leaf);
+/* The kernel (MPGEMM_MP_LEAF_THREAD or _TEAM) a block GEMM of `batch`
+ * products of m x n elements at prec_bits uses under the current setting on
+ * a stream of `sms` SMs (mpgemm_stream_sms).  Host arithmetic only;
+ * MPGEMM_EINVAL for prec_bits not a positive multiple of 32, negative sizes,
+ * batch or sms below 1. */
+int mpgemm_mp_leaf_choice(int prec_bits, int64_t m, int64_t n, int64_t batch, int sms);
+
 /* ---------------------------------------------------------------------------
  * Split-precision DD GEMM on the INT8 tensor path (an Ozaki-style scheme; the
  * paper has no counterpart, it is an extension of its DD GEMM):

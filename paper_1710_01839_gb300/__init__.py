@@ -178,6 +178,21 @@ def set_workspace(tensor=None):
         check(lib().mpgemm_set_workspace(ctypes.c_void_p(tensor.data_ptr()), tensor.numel() * tensor.element_size()))
 
 
+MP_LEAVES = {"default": 0, "thread": 1, "team": 2}
+
+
+def set_mp_leaf(leaf):
+    """Select the kernel of multi-limb block GEMMs at 512-2048 bits:
+    "thread" (one thread per output), "team" (W / 8 lanes per output, limbs
+    across lanes) or "default"; returns the previous setting's name
+    (mpgemm_set_mp_leaf)."""
+    if leaf not in MP_LEAVES:
+        raise ValueError(f"leaf must be one of {sorted(MP_LEAVES)}")
+    prev = lib().mpgemm_set_mp_leaf(MP_LEAVES[leaf])
+    check(min(prev, 0))
+    return {v: k for k, v in MP_LEAVES.items()}[prev]
+
+
 def stream_status(stream=None):
     return int(lib().mpgemm_stream_status(_stream_ptr(stream)))
 

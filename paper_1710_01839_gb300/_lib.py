@@ -80,6 +80,8 @@ SIGNATURES = {
     "mpgemm_tune": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _I, _P, _P]),
     "mpgemm_tune_forget": (_I, []),
     "mpgemm_auto_mode": (_I, [_I]),
+    "mpgemm_set_mp_leaf": (_I, [_I]),
+    "mpgemm_mp_leaf_choice": (_I, [_I, _I64, _I64, _I64, _I]),
     "mpgemm_time_config": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _I, _I, _I, _I, _P, _P]),
     "mpgemm_tune_cache_open": (_I, [ctypes.c_char_p]),
     "mpgemm_tune_cache_stats": (_I, [_P, _P, _P, _P]),

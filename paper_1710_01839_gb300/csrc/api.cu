@@ -327,6 +327,6 @@ int mpgemm_selftest_wait_timeout(int limit_ms, void* stream) {
     return mpgemm_stream_status(stream);
 }
 
-int mpgemm_version(void) { return 10000 * 0 + 100 * 1 + 0; }
+int mpgemm_version(void) { return 10000 * 0 + 100 * 2 + 0; }
 
 }  // extern "C"

@@ -85,6 +85,9 @@ static int mp_gemm_w(int algo, int64_t m, int64_t l, int64_t n, int64_t batch, V
         dim3 blk(16, 16);
         dim3 grd(ceil_div(n, 16), ceil_div(m, 16), (unsigned)batch);
         k_mp_simple<W><<<grd, blk, 0, s>>>(m, l, n, A, B, C, status);
+    } else if (mp_team_leaf(W, m, n, batch, s)) {
+        const int rc = mp_gemm_team(W, m, l, n, batch, A, B, C, n_min, status, s);
+        if (rc != MPGEMM_OK) return rc;
     } else {
         unsigned G = n_min > 16 ? (unsigned)(n_min / 16) : 1u;
         dim3 grd(ceil_div(m, 16) * ceil_div(n, 16), (unsigned)batch);

@@ -18,6 +18,13 @@ int ddqd_gemm(int kind, int algo, int64_t m, int64_t l, int64_t n, int64_t batch
 int mp_gemm(int w, int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const uint32_t> A,
             View<const uint32_t> B, View<uint32_t> C, int n_min, cudaStream_t s);
 
+// Multi-limb block GEMM with a team of w / 8 lanes per output (w = 16, 32,
+// 64); mp_team_leaf says whether mp_gemm's block algorithm uses it for a
+// batch of m x n outputs on stream s.
+bool mp_team_leaf(int w, int64_t m, int64_t n, int64_t batch, cudaStream_t s);
+int mp_gemm_team(int w, int64_t m, int64_t l, int64_t n, int64_t batch, View<const uint32_t> A,
+                 View<const uint32_t> B, View<uint32_t> C, int n_min, unsigned* status, cudaStream_t s);
+
 // Elementwise z = x + y (sub: x - y) in a format over a batch of r x c matrices.
 int ddqd_addsub(int kind, int64_t r, int64_t c, int64_t batch, View<double> Z, View<const double> X,
                 View<const double> Y, int sub, cudaStream_t s);

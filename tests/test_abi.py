@@ -71,3 +71,29 @@ def test_host_only_calls(built):
     assert L.mpgemm_peak_run(0, 0, ctypes.byref(ops), None) == -1           # no iterations
     assert L.mpgemm_peak_run(0, (1 << 22) + 1, ctypes.byref(ops), None) == -1   # tcgen05 loop too long
     assert L.mpgemm_peak_run(2, 1, None, None) == -1                        # no ops output
+    # the multi-limb leaf setting is host state: returns the previous value
+    assert L.mpgemm_set_mp_leaf(2) == 0
+    assert L.mpgemm_set_mp_leaf(1) == 2
+    assert L.mpgemm_set_mp_leaf(3) == -1 and L.mpgemm_set_mp_leaf(-1) == -1
+    assert L.mpgemm_set_mp_leaf(0) == 1
+    assert built.set_mp_leaf("team") == "default" and built.set_mp_leaf("default") == "team"
+    import pytest
+    with pytest.raises(ValueError):
+        built.set_mp_leaf("warp")
+    # which multi-limb block kernel a call uses (host arithmetic): the team
+    # kernel at 512-2048 bits when the one-thread grid (16 x 16 per CTA)
+    # has at most one CTA per two SMs
+    choice = L.mpgemm_mp_leaf_choice
+    assert choice(1024, 128, 128, 1, 152) == 2          # 64 CTAs <= 76
+    assert choice(1024, 144, 128, 1, 152) == 2          # 72
+    assert choice(1024, 160, 128, 1, 152) == 1          # 80 > 76
+    assert choice(1024, 64, 64, 4, 152) == 2 and choice(1024, 64, 64, 7, 152) == 1   # 64 and 112 CTAs
+    assert choice(1024, 128, 128, 1, 24) == 1           # a 24-SM partition: 64 > 12
+    assert choice(256, 16, 16, 1, 152) == 1 and choice(4096, 16, 16, 1, 152) == 1   # other widths
+    assert choice(512, 16, 16, 1, 152) == 2 and choice(2048, 1, 1, 1, 152) == 2
+    assert choice(100, 16, 16, 1, 152) == -1 and choice(512, 16, 16, 0, 152) == -1 and choice(512, 1, 1, 1, 0) == -1
+    assert L.mpgemm_set_mp_leaf(1) == 0
+    assert choice(2048, 16, 16, 1, 152) == 1
+    assert L.mpgemm_set_mp_leaf(2) == 1
+    assert choice(2048, 4096, 4096, 1, 152) == 2
+    assert L.mpgemm_set_mp_leaf(0) == 2
