@@ -632,6 +632,22 @@ int mpgemm_profile_read(double* total_ms, int* launches);
 /* Library version as 10000*major + 100*minor + patch. */
 int mpgemm_version(void);
 
+/* The bounds-checked build of this library (libmpgemm_bc.so, the same
+ * sources compiled with -DMPGEMM_BOUNDS_CHECK; a testing tool): every global
+ * read and write of the DD / QD / multi-limb simple, block and Strassen
+ * kernels (operands, result, each Strassen level's operand and product
+ * batches, the integer pipe's limb copies) is checked against the buffer it
+ * belongs to.  An access outside is not made (a load reads 0); it is
+ * counted and the first such address kept.  mpgemm_bounds_read synchronises
+ * the device, returns the count and that address since the last read and
+ * clears them.  mpgemm_selftest_bounds launches one thread that reads one
+ * element inside a 16-word buffer, one past its end and writes one before
+ * its start (the two misses stay inside a larger allocation): a checked
+ * build then counts exactly 2.  Both return MPGEMM_EUNSUPPORTED in the
+ * normal build.  The counter is per device, not per stream. */
+int mpgemm_bounds_read(long long* count, unsigned long long* first_address);
+int mpgemm_selftest_bounds(void* stream);
+
 /* ---------------------------------------------------------------------------
  * Peak-rate microbenchmarks (measurement; the paper has no counterpart): the
  * denominators of the rooflines the benchmark reports, measured on the GPU

@@ -7,6 +7,7 @@ import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libmpgemm.so")
+_LIB_CHECKED_PATH = os.path.join(_HERE, "_build_bc", "libmpgemm_bc.so")
 
 ALGO = {"simple": 0, "block": 1, "strassen": 2, "auto": 3}
 KIND = {"dd": 0, "qd": 1, "mp": 2}
@@ -81,6 +82,8 @@ SIGNATURES = {
     "mpgemm_tune_forget": (_I, []),
     "mpgemm_auto_mode": (_I, [_I]),
     "mpgemm_set_mp_leaf": (_I, [_I]),
+    "mpgemm_bounds_read": (_I, [_P, _P]),
+    "mpgemm_selftest_bounds": (_I, [_P]),
     "mpgemm_mp_leaf_choice": (_I, [_I, _I64, _I64, _I64, _I]),
     "mpgemm_time_config": (_I, [_I, _I, _I64, _I64, _I64, _P, _P, _P, _I, _I, _I, _I, _P, _P]),
     "mpgemm_tune_cache_open": (_I, [ctypes.c_char_p]),
@@ -104,20 +107,38 @@ def lib_path() -> str:
     return _LIB_PATH
 
 
+def _load(path):
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                           f"g.build()'` (the CUDA library is required; there is no CPU path)")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
 def lib():
     """Load libmpgemm.so.  Raises if it was not built (no fallback)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(_LIB_PATH):
-            raise RuntimeError(f"{_LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
-                               f"g.build()'` (the CUDA library is required; there is no CPU path)")
-        L = ctypes.CDLL(_LIB_PATH)
-        for name, (res, args) in SIGNATURES.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = _load(_LIB_PATH)
     return _lib
+
+
+_lib_checked = None
+
+
+def lib_checked():
+    """Load the bounds-checked build, libmpgemm_bc.so (a testing tool: the
+    same C ABI, every global access of the GEMM kernels checked against its
+    buffer; see mpgemm_bounds_read).  It is a separate library with its own
+    state (workspace, status word, tuner)."""
+    global _lib_checked
+    if _lib_checked is None:
+        _lib_checked = _load(_LIB_CHECKED_PATH)
+    return _lib_checked
 
 
 def check_planes(t, planes, dtypes, name, rows=None, cols=None):

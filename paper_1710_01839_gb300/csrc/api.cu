@@ -201,8 +201,10 @@ static int ddqd_entry(int kind, int64_t m, int64_t l, int64_t n, const double* A
         depth = ch.depth;
     }
     if (n_min <= 0) n_min = default_n_min(kind);
-    View<const double> a = planes_view(A, m, l), b = planes_view(B, l, n);
-    View<double> c = planes_view(C, m, n);
+    const size_t eb = sizeof(double) * P;
+    View<const double> a = bounded(planes_view(A, m, l), A, eb * m * l);
+    View<const double> b = bounded(planes_view(B, l, n), B, eb * l * n);
+    View<double> c = bounded(planes_view(C, m, n), C, eb * m * n);
     if (algo == MPGEMM_STRASSEN && depth > 0) return strassen_ddqd(kind, m, l, n, a, b, c, n_min, depth, s);
     return ddqd_gemm(kind, algo == MPGEMM_SIMPLE ? MPGEMM_SIMPLE : MPGEMM_BLOCK, m, l, n, 1, a, b, c, n_min, s);
 }
@@ -227,11 +229,51 @@ static int mp_entry(int64_t m, int64_t l, int64_t n, int prec_bits, const uint32
         depth = ch.depth;
     }
     if (n_min <= 0) n_min = default_n_min(MPGEMM_KIND_MP);
-    View<const uint32_t> a = planes_view(A, m, l), b = planes_view(B, l, n);
-    View<uint32_t> c = planes_view(C, m, n);
+    const size_t eb = sizeof(uint32_t) * (size_t)(2 + w);
+    View<const uint32_t> a = bounded(planes_view(A, m, l), A, eb * m * l);
+    View<const uint32_t> b = bounded(planes_view(B, l, n), B, eb * l * n);
+    View<uint32_t> c = bounded(planes_view(C, m, n), C, eb * m * n);
     if (algo == MPGEMM_STRASSEN && depth > 0) return strassen_mp(w, m, l, n, a, b, c, n_min, depth, s);
     return mp_gemm(w, algo == MPGEMM_SIMPLE ? MPGEMM_SIMPLE : MPGEMM_BLOCK, m, l, n, 1, a, b, c, n_min, s);
 }
+
+#ifdef MPGEMM_BOUNDS_CHECK
+BoundsWord* bounds_word() {
+    static BoundsWord* words[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!words[dev]) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, sizeof(BoundsWord)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(BoundsWord)) != cudaSuccess) return nullptr;
+        words[dev] = static_cast<BoundsWord*>(p);
+    }
+    return words[dev];
+}
+
+// One thread reads element 3 of a 16-word buffer (inside), then element 16
+// and writes element -1 (both outside: not made, counted).
+__global__ void k_selftest_bounds(View<uint32_t> V, uint32_t* out) {
+    out[0] = V.load(V.at(0, 0, 0, 3));
+    out[1] = V.load(V.at(0, 0, 0, 16));
+    V.store(V.at(0, 0, 0, -1), 7u);
+}
+
+static int bounds_selftest(cudaStream_t s) {
+    static uint32_t* buf = nullptr;
+    if (!buf) {
+        void* p = nullptr;
+        MPG_CUDA(cudaMalloc(&p, 32 * sizeof(uint32_t)));
+        MPG_CUDA(cudaMemset(p, 0, 32 * sizeof(uint32_t)));
+        buf = static_cast<uint32_t*>(p);
+    }
+    // the view covers words 8 .. 23 of the allocation: the probes outside it
+    // stay inside the allocation, whether or not the check works
+    View<uint32_t> v = bounded(planes_view(buf + 8, 1, 16), buf + 8, 16 * sizeof(uint32_t));
+    k_selftest_bounds<<<1, 1, 0, s>>>(v, buf + 28);
+    return check_launch();
+}
+#endif
 
 }  // namespace mpg
 
@@ -328,5 +370,33 @@ int mpgemm_selftest_wait_timeout(int limit_ms, void* stream) {
 }
 
 int mpgemm_version(void) { return 10000 * 0 + 100 * 2 + 0; }
+
+int mpgemm_bounds_read(long long* count, unsigned long long* first_address) {
+#ifdef MPGEMM_BOUNDS_CHECK
+    if (!count || !first_address) return MPGEMM_EINVAL;
+    BoundsWord* w = bounds_word();
+    if (!w) return MPGEMM_ECUDA;
+    BoundsWord h{};
+    MPG_CUDA(cudaDeviceSynchronize());
+    MPG_CUDA(cudaMemcpy(&h, w, sizeof h, cudaMemcpyDeviceToHost));
+    MPG_CUDA(cudaMemset(w, 0, sizeof h));
+    *count = (long long)h.count;
+    *first_address = h.first;
+    return MPGEMM_OK;
+#else
+    (void)count;
+    (void)first_address;
+    return MPGEMM_EUNSUPPORTED;
+#endif
+}
+
+int mpgemm_selftest_bounds(void* stream) {
+#ifdef MPGEMM_BOUNDS_CHECK
+    return bounds_selftest((cudaStream_t)stream);
+#else
+    (void)stream;
+    return MPGEMM_EUNSUPPORTED;
+#endif
+}
 
 }  // extern "C"

@@ -15,20 +15,73 @@
 
 namespace mpg {
 
+#ifdef MPGEMM_BOUNDS_CHECK
+// The bounds-checked build (-DMPGEMM_BOUNDS_CHECK, libmpgemm_bc.so): a view
+// also knows the buffer it addresses, [lo, hi), and the GEMM kernels read
+// and write global memory only through View::load / get / store, which
+// check the element against it.  An element outside is not accessed (a load
+// reads 0); the miss is counted in `oob` and the first missed address kept,
+// for mpgemm_bounds_read().  A view without a buffer (lo null) is unchecked.
+struct BoundsWord {
+    unsigned long long count;
+    unsigned long long first;
+};
+BoundsWord* bounds_word();   // this device's counter (device memory)
+#endif
+
 template <class T>
 struct View {
     T* p;
     int64_t ld;  // row stride (elements)
     int64_t ps;  // plane stride (elements)
     int64_t bs;  // batch stride (elements)
+#ifdef MPGEMM_BOUNDS_CHECK
+    const void* lo = nullptr;
+    const void* hi = nullptr;
+    BoundsWord* oob = nullptr;
+#endif
     __host__ __device__ T* at(int64_t z, int q, int64_t i, int64_t j) const {
         return p + z * bs + q * ps + i * ld + j;
+    }
+    // whether element q may be accessed (always, outside the checked build)
+    __device__ __forceinline__ bool ok(const T* q) const {
+#ifdef MPGEMM_BOUNDS_CHECK
+        if (lo && ((const char*)q < (const char*)lo || (const char*)(q + 1) > (const char*)hi)) {
+            if (atomicAdd(&oob->count, 1ull) == 0ull) oob->first = (unsigned long long)(uintptr_t)q;
+            return false;
+        }
+#endif
+        return true;
+    }
+    // read-only load through the non-coherent cache (operands)
+    __device__ __forceinline__ T load(const T* q) const { return ok(q) ? __ldg(q) : T(0); }
+    // plain load (workspace the same kernel sequence writes)
+    __device__ __forceinline__ T get(const T* q) const { return ok(q) ? *q : T(0); }
+    __device__ __forceinline__ void store(T* q, T v) const {
+        if (ok(q)) *q = v;
     }
 };
 
 template <class T>
 __host__ __device__ inline View<T> planes_view(T* p, int64_t rows, int64_t cols) {
     View<T> v{p, cols, rows * cols, 0};
+    return v;
+}
+
+// v restricted to the buffer [base, base + bytes) in the checked build (the
+// view itself elsewhere).
+template <class T>
+inline View<T> bounded(View<T> v, const void* base, size_t bytes) {
+#ifdef MPGEMM_BOUNDS_CHECK
+    v.oob = bounds_word();
+    if (v.oob) {   // no counter (allocation failed): the view stays unchecked
+        v.lo = base;
+        v.hi = (const char*)base + bytes;
+    }
+#else
+    (void)base;
+    (void)bytes;
+#endif
     return v;
 }
 

@@ -35,8 +35,8 @@ __global__ void __launch_bounds__(256) k_simple(int64_t m, int64_t l, int64_t n,
         double a[P], b[P];
 #pragma unroll
         for (int q = 0; q < P; q++) {
-            a[q] = __ldg(pa + q * A.ps + k);
-            b[q] = __ldg(pb + q * B.ps + k * B.ld);
+            a[q] = A.load(pa + q * A.ps + k);
+            b[q] = B.load(pb + q * B.ps + k * B.ld);
         }
         Fmt::mac(acc, a, b);
         if ((k + 1) % Fmt::R == 0) Fmt::renorm(acc);
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_simple(int64_t m, int64_t l, int64_t n,
     double out[P];
     Fmt::finish(acc, out);
 #pragma unroll
-    for (int q = 0; q < P; q++) *C.at(z, q, i, j) = out[q];
+    for (int q = 0; q < P; q++) C.store(C.at(z, q, i, j), out[q]);
 }
 
 // ---------------------------------------------------------------- Eq 2

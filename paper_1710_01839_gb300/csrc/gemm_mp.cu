@@ -26,11 +26,11 @@ __global__ void __launch_bounds__(256) k_mp_simple(int64_t m, int64_t l, int64_t
     mp_set_zero(c, 0u);
     for (int64_t k = 0; k < l; k++) {
         MPV<W> a, b;
-        load_mp(a, A.at(z, 0, i, k), A.ps);
-        load_mp(b, B.at(z, 0, k, j), B.ps);
+        load_mp(a, A, A.at(z, 0, i, k));
+        load_mp(b, B, B.at(z, 0, k, j));
         mp_mac(c, a, b, st);
     }
-    store_mp(c, C.at(z, 0, i, j), C.ps);
+    store_mp(c, C, C.at(z, 0, i, j));
     if (st) atomicOr(status, st);
 }
 
@@ -67,11 +67,11 @@ __global__ void k_mp_addsub(int64_t r, int64_t c, View<uint32_t> Z, View<const u
     if (j >= c) return;
     unsigned st = 0u;
     MPV<W> x, y, s;
-    load_mp(x, X.at(z, 0, i, j), X.ps);
-    load_mp(y, Y.at(z, 0, i, j), Y.ps);
+    load_mp(x, X, X.at(z, 0, i, j));
+    load_mp(y, Y, Y.at(z, 0, i, j));
     if (sub) y.f ^= 1u;
     mp_add<W>(x, y, s, st);
-    store_mp(s, Z.at(z, 0, i, j), Z.ps);
+    store_mp(s, Z, Z.at(z, 0, i, j));
     if (st) atomicOr(status, st);
 }
 

@@ -67,13 +67,13 @@ __global__ void __launch_bounds__(256, team_min_ctas<W>()) k_mp_team(int64_t m, 
             const int q = idx / (BR * KT), rem = idx % (BR * KT);
             const int r = rem / KT, cc = rem % KT;
             const int64_t i = i0 + r, k = k0 + cc;
-            As[cc][r][q < 2 ? q : q + 2] = (i < m && k < l) ? __ldg(A.at(z, q, i, k)) : (q == 1 ? 2u : 0u);
+            As[cc][r][q < 2 ? q : q + 2] = (i < m && k < l) ? A.load(A.at(z, q, i, k)) : (q == 1 ? 2u : 0u);
         }
         for (int idx = threadIdx.x; idx < (2 + W) * KT * BC; idx += 256) {
             const int q = idx / (KT * BC), rem = idx % (KT * BC);
             const int rb = rem / BC, cb = rem % BC;
             const int64_t k = k0 + rb, j = j0 + cb;
-            Bs[rb][cb][q < 2 ? q : q + 2] = (k < l && j < n) ? __ldg(B.at(z, q, k, j)) : (q == 1 ? 2u : 0u);
+            Bs[rb][cb][q < 2 ? q : q + 2] = (k < l && j < n) ? B.load(B.at(z, q, k, j)) : (q == 1 ? 2u : 0u);
         }
         __syncthreads();
         const int kmax = (l - k0) < KT ? (int)(l - k0) : KT;
@@ -93,11 +93,11 @@ __global__ void __launch_bounds__(256, team_min_ctas<W>()) k_mp_team(int64_t m, 
     if (i < m && j < n) {
         uint32_t* p = C.at(z, 0, i, j);
         if (tm.t == 0) {
-            p[0] = (uint32_t)c.e;
-            p[C.ps] = c.f;
+            C.store(p, (uint32_t)c.e);
+            C.store(p + C.ps, c.f);
         }
 #pragma unroll
-        for (int u = 0; u < 8; u++) p[(2 + 8 * tm.t + u) * C.ps] = c.m[u];
+        for (int u = 0; u < 8; u++) C.store(p + (2 + 8 * tm.t + u) * C.ps, c.m[u]);
     }
     if (st) atomicOr(status, st);
 }

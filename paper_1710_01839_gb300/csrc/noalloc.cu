@@ -71,8 +71,10 @@ int mpgemm_dd_strassen_noalloc(int64_t m, int64_t l, int64_t n, const double* A,
     if ((rc = noalloc_scratch(&ws))) return rc;
     PartitionScope pscope(s);   // a partition's stream: its kernels run in its context
     if (n_min <= 0) n_min = default_n_min(MPGEMM_KIND_DD);
-    View<const double> a = planes_view(A, m, l), b = planes_view(B, l, n);
-    View<double> c = planes_view(C, m, n);
+    const size_t eb = 2 * sizeof(double);
+    View<const double> a = bounded(planes_view(A, m, l), A, eb * m * l);
+    View<const double> b = bounded(planes_view(B, l, n), B, eb * l * n);
+    View<double> c = bounded(planes_view(C, m, n), C, eb * m * n);
     return strassen_ddqd_ws(MPGEMM_KIND_DD, m, l, n, a, b, c, n_min, strassen_depth, ws, bytes, s);
 }
 

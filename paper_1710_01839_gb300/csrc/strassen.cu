@@ -52,12 +52,12 @@ struct QDE {
 template <class E>
 __device__ __forceinline__ void ld(const View<const double>& V, int64_t z, int64_t i, int64_t j, double* x) {
 #pragma unroll
-    for (int q = 0; q < E::P; q++) x[q] = *V.at(z, q, i, j);
+    for (int q = 0; q < E::P; q++) x[q] = V.get(V.at(z, q, i, j));
 }
 template <class E>
 __device__ __forceinline__ void st(const View<double>& V, int64_t z, int64_t i, int64_t j, const double* x) {
 #pragma unroll
-    for (int q = 0; q < E::P; q++) *V.at(z, q, i, j) = x[q];
+    for (int q = 0; q < E::P; q++) V.store(V.at(z, q, i, j), x[q]);
 }
 template <class E>
 __device__ __forceinline__ void neg(double* x) {
@@ -141,18 +141,18 @@ __global__ void k_combine(int64_t rows, int64_t cols, int64_t xr, int64_t xc, Vi
 template <int W>
 __device__ __forceinline__ void ldm(const View<const uint32_t>& V, int64_t z, int64_t i, int64_t j, MPV<W>& v) {
     const uint32_t* p = V.at(z, 0, i, j);
-    v.e = (int)p[0];
-    v.f = p[V.ps];
+    v.e = (int)V.get(p);
+    v.f = V.get(p + V.ps);
 #pragma unroll
-    for (int w = 0; w < W; w++) v.m[w] = p[(2 + w) * V.ps];
+    for (int w = 0; w < W; w++) v.m[w] = V.get(p + (2 + w) * V.ps);
 }
 template <int W>
 __device__ __forceinline__ void stm(const View<uint32_t>& V, int64_t z, int64_t i, int64_t j, const MPV<W>& v) {
     uint32_t* p = V.at(z, 0, i, j);
-    p[0] = (uint32_t)v.e;
-    p[V.ps] = v.f;
+    V.store(p, (uint32_t)v.e);
+    V.store(p + V.ps, v.f);
 #pragma unroll
-    for (int w = 0; w < W; w++) p[(2 + w) * V.ps] = v.m[w];
+    for (int w = 0; w < W; w++) V.store(p + (2 + w) * V.ps, v.m[w]);
 }
 
 template <int W>
@@ -265,9 +265,9 @@ size_t strassen_workspace_bytes(size_t eb, int64_t m, int64_t l, int64_t n, int 
 
 // Batched view of `count` contiguous r x c matrices with P planes each.
 template <class T>
-static View<T> batch_view(T* base, int64_t r, int64_t c, int P) {
+static View<T> batch_view(T* base, int64_t r, int64_t c, int P, size_t count) {
     View<T> v{base, c, r * c, (int64_t)P * r * c};
-    return v;
+    return bounded(v, base, sizeof(T) * (size_t)P * (size_t)(r * c) * count);
 }
 
 template <class T>
@@ -288,9 +288,9 @@ static int carve(char* ws, size_t ws_bytes, size_t eb, int P, int64_t m, int64_t
         off += align256(nodes * (size_t)(lk * nk) * eb);
         T* c = reinterpret_cast<T*>(ws + off);
         off += align256(nodes * (size_t)(mk * nk) * eb);
-        L.SA[k] = batch_view(a, mk, lk, P);
-        L.SB[k] = batch_view(b, lk, nk, P);
-        L.PR[k] = batch_view(c, mk, nk, P);
+        L.SA[k] = batch_view(a, mk, lk, P, nodes);
+        L.SB[k] = batch_view(b, lk, nk, P, nodes);
+        L.PR[k] = batch_view(c, mk, nk, P, nodes);
     }
     return off <= ws_bytes ? MPGEMM_OK : MPGEMM_ENOMEM;
 }
@@ -298,6 +298,11 @@ static int carve(char* ws, size_t ws_bytes, size_t eb, int P, int64_t m, int64_t
 template <class T>
 static View<const T> cview(const View<T>& v) {
     View<const T> r{v.p, v.ld, v.ps, v.bs};
+#ifdef MPGEMM_BOUNDS_CHECK
+    r.lo = v.lo;
+    r.hi = v.hi;
+    r.oob = v.oob;
+#endif
     return r;
 }
 

@@ -85,12 +85,12 @@ __device__ __forceinline__ void ddqd_block_tile(int64_t m, int64_t l, int64_t n,
             int64_t i = i0 + r, k = k0 + c;
             bool ok = i < m && k < l;
 #pragma unroll
-            for (int q = 0; q < P; q++) ra[v][q] = ok ? __ldg(A.at(z, q, i, k)) : 0.0;
+            for (int q = 0; q < P; q++) ra[v][q] = ok ? A.load(A.at(z, q, i, k)) : 0.0;
             int rr = idx / BM, cc = idx % BM;        // B panel: KT rows x BM
             int64_t kb = k0 + rr, j = j0 + cc;
             bool okb = kb < l && j < n;
 #pragma unroll
-            for (int q = 0; q < P; q++) rb[v][q] = okb ? __ldg(B.at(z, q, kb, j)) : 0.0;
+            for (int q = 0; q < P; q++) rb[v][q] = okb ? B.load(B.at(z, q, kb, j)) : 0.0;
         }
     };
     auto sstore = [&]() {
@@ -151,25 +151,25 @@ __device__ __forceinline__ void ddqd_block_tile(int64_t m, int64_t l, int64_t n,
             Fmt::finish(acc[r][c], out);
             if (i < m && j < n) {
 #pragma unroll
-                for (int q = 0; q < P; q++) *C.at(z, q, i, j) = out[q];
+                for (int q = 0; q < P; q++) C.store(C.at(z, q, i, j), out[q]);
             }
         }
 }
 
 template <int W>
-__device__ __forceinline__ void load_mp(MPV<W>& v, const uint32_t* p, int64_t ps) {
-    v.e = (int)p[0];
-    v.f = p[ps];
+__device__ __forceinline__ void load_mp(MPV<W>& v, const View<const uint32_t>& V, const uint32_t* p) {
+    v.e = (int)V.load(p);
+    v.f = V.load(p + V.ps);
 MP_UNROLL
-    for (int i = 0; i < W; i++) v.m[i] = p[(2 + i) * ps];
+    for (int i = 0; i < W; i++) v.m[i] = V.load(p + (2 + i) * V.ps);
 }
 
 template <int W>
-__device__ __forceinline__ void store_mp(const MPV<W>& v, uint32_t* p, int64_t ps) {
-    p[0] = (uint32_t)v.e;
-    p[ps] = v.f;
+__device__ __forceinline__ void store_mp(const MPV<W>& v, const View<uint32_t>& V, uint32_t* p) {
+    V.store(p, (uint32_t)v.e);
+    V.store(p + V.ps, v.f);
 MP_UNROLL
-    for (int i = 0; i < W; i++) p[(2 + i) * ps] = v.m[i];
+    for (int i = 0; i < W; i++) V.store(p + (2 + i) * V.ps, v.m[i]);
 }
 
 template <int W>
@@ -248,13 +248,14 @@ __device__ __forceinline__ void mp_block_tile(int64_t m, int64_t l, int64_t n, c
             const int64_t k = k0 + (sA ? ec : er);
             const bool ok = fixed_ok && k < l;
             const uint32_t* src = gbase + (sA ? k : k * B.ld);
+            const View<const uint32_t>& SV = sA ? A : B;
             uint32_t w[OFF + W];
-            w[0] = ok ? __ldg(src) : 0u;
-            w[1] = ok ? __ldg(src + ps) : 2u;   // flags: zero
+            w[0] = ok ? SV.load(src) : 0u;
+            w[1] = ok ? SV.load(src + ps) : 2u;   // flags: zero
             w[2] = 0u;
             w[3] = 0u;
 MP_UNROLL
-            for (int q = 0; q < W; q++) w[OFF + q] = ok ? __ldg(src + (2 + q) * ps) : 0u;
+            for (int q = 0; q < W; q++) w[OFF + q] = ok ? SV.load(src + (2 + q) * ps) : 0u;
 MP_UNROLL
             for (int q = 0; q < OFF + W; q += 4)
                 *reinterpret_cast<uint4*>(sdst + q) = make_uint4(w[q], w[q + 1], w[q + 2], w[q + 3]);
@@ -264,11 +265,11 @@ MP_UNROLL
             int slot = q < 2 ? q : q - 2 + OFF;
             int r = rem / KT, cc = rem % KT;          // A: row r, k = k0 + cc
             int64_t i = i0 + r, k = k0 + cc;
-            uint32_t va = (i < m && k < l) ? __ldg(A.at(z, q, i, k)) : (q == 1 ? 2u : 0u);
+            uint32_t va = (i < m && k < l) ? A.load(A.at(z, q, i, k)) : (q == 1 ? 2u : 0u);
             As[cc][r][slot] = va;
             int rb = rem / BM, cb = rem % BM;         // B: k = k0 + rb, column cb
             int64_t kb = k0 + rb, j = j0 + cb;
-            uint32_t vb = (kb < l && j < n) ? __ldg(B.at(z, q, kb, j)) : (q == 1 ? 2u : 0u);
+            uint32_t vb = (kb < l && j < n) ? B.load(B.at(z, q, kb, j)) : (q == 1 ? 2u : 0u);
             Bs[rb][cb][slot] = vb;
         }
         __syncthreads();
@@ -320,7 +321,7 @@ MP_UNROLL
         __syncthreads();
     }
     int64_t i = i0 + ty, j = j0 + tx;
-    if (i < m && j < n) store_mp(c, C.at(z, 0, i, j), C.ps);
+    if (i < m && j < n) store_mp(c, C, C.at(z, 0, i, j));
 }
 
 }  // namespace mpg

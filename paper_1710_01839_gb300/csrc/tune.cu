@@ -126,15 +126,18 @@ struct Problem {
 int run_once(const Problem& P, int algo, int n_min, int depth, int64_t rows) {
     if (P.kind == MPGEMM_KIND_MP) {
         int w = P.prec_bits / 32;
-        View<const uint32_t> a{(const uint32_t*)P.A, P.l, P.m * P.l, 0};
-        View<const uint32_t> b = planes_view((const uint32_t*)P.B, P.l, P.n);
-        View<uint32_t> c{(uint32_t*)P.C, P.n, P.m * P.n, 0};
+        const size_t eb = sizeof(uint32_t) * (size_t)(2 + w);
+        View<const uint32_t> a = bounded(View<const uint32_t>{(const uint32_t*)P.A, P.l, P.m * P.l, 0}, P.A,
+                                         eb * P.m * P.l);
+        View<const uint32_t> b = bounded(planes_view((const uint32_t*)P.B, P.l, P.n), P.B, eb * P.l * P.n);
+        View<uint32_t> c = bounded(View<uint32_t>{(uint32_t*)P.C, P.n, P.m * P.n, 0}, P.C, eb * P.m * P.n);
         if (algo == MPGEMM_STRASSEN) return strassen_mp(w, P.m, P.l, P.n, a, b, c, n_min, depth, P.s);
         return mp_gemm(w, algo, rows, P.l, P.n, 1, a, b, c, n_min, P.s);
     }
-    View<const double> a{(const double*)P.A, P.l, P.m * P.l, 0};
-    View<const double> b = planes_view((const double*)P.B, P.l, P.n);
-    View<double> c{(double*)P.C, P.n, P.m * P.n, 0};
+    const size_t eb = sizeof(double) * (P.kind == MPGEMM_KIND_DD ? 2 : 4);
+    View<const double> a = bounded(View<const double>{(const double*)P.A, P.l, P.m * P.l, 0}, P.A, eb * P.m * P.l);
+    View<const double> b = bounded(planes_view((const double*)P.B, P.l, P.n), P.B, eb * P.l * P.n);
+    View<double> c = bounded(View<double>{(double*)P.C, P.n, P.m * P.n, 0}, P.C, eb * P.m * P.n);
     if (algo == MPGEMM_STRASSEN) return strassen_ddqd(P.kind, P.m, P.l, P.n, a, b, c, n_min, depth, P.s);
     return ddqd_gemm(P.kind, algo, rows, P.l, P.n, 1, a, b, c, n_min, P.s);
 }

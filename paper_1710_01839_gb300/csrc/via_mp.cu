@@ -134,8 +134,10 @@ static int via_mp_entry(int T, int64_t m, int64_t l, int64_t n, const double* A,
     rc = convert(0, T, w, m * l, A, Am, nullptr, s);
     if (!rc) rc = convert(0, T, w, l * n, B, Bm, nullptr, s);
     if (!rc) {
-        View<const uint32_t> a = planes_view<const uint32_t>(Am, m, l), b = planes_view<const uint32_t>(Bm, l, n);
-        View<uint32_t> c = planes_view(Cm, m, n);
+        const size_t eb = sizeof(uint32_t) * (size_t)(2 + w);
+        View<const uint32_t> a = bounded(planes_view<const uint32_t>(Am, m, l), Am, eb * m * l);
+        View<const uint32_t> b = bounded(planes_view<const uint32_t>(Bm, l, n), Bm, eb * l * n);
+        View<uint32_t> c = bounded(planes_view(Cm, m, n), Cm, eb * m * n);
         if (strassen) {
             const size_t sb = strassen_workspace_bytes(sizeof(uint32_t) * (size_t)(2 + w), m, l, n, depth);
             rc = strassen_mp_ws(w, m, l, n, a, b, c, n_min, depth, rest, sb, s);

@@ -97,3 +97,16 @@ def test_host_only_calls(built):
     assert L.mpgemm_set_mp_leaf(2) == 1
     assert choice(2048, 4096, 4096, 1, 152) == 2
     assert L.mpgemm_set_mp_leaf(0) == 2
+    # the bounds counter exists only in the bounds-checked build
+    assert L.mpgemm_bounds_read(None, None) == -2 and L.mpgemm_selftest_bounds(None) == -2
+
+
+def test_checked_build_exists_and_exports(built):
+    import ctypes
+    from paper_1710_01839_gb300._lib import lib_checked, SIGNATURES
+    Lc = lib_checked()
+    for name in SIGNATURES:
+        assert hasattr(Lc, name), name
+    c, f = ctypes.c_longlong(), ctypes.c_ulonglong()
+    assert Lc.mpgemm_bounds_read(None, ctypes.byref(f)) == -1        # argument check before any device call
+    assert Lc.mpgemm_version() == built.lib().mpgemm_version()
