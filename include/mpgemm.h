@@ -448,7 +448,7 @@ typedef struct {
     double cand_pred_ms[8];      /* T_sample * m / r                              */
     double cand_full_ms[8];      /* measured full time (NaN without VERIFY)       */
     double simple_ms, block_ms;  /* NaN when not run                              */
-    double strassen_ms[4];       /* [d], d = 1..3; NaN when not run               */
+    double strassen_ms[5];       /* [d], d = 1..4; NaN when not run               */
     double tuning_ms;            /* wall time of this call                        */
     int measured;                /* timings taken by this call (not from the cache) */
     int from_cache;              /* 1: the choice came from the tuning cache      */

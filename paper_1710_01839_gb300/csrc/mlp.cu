@@ -274,7 +274,7 @@ static std::vector<Cand> candidates(int kind, int64_t m, int64_t l, int64_t n) {
     c.push_back({MPGEMM_SIMPLE, 16, 0});
     const int tmax = kind == MPGEMM_KIND_DD ? 64 : kind == MPGEMM_KIND_QD ? 32 : 16;
     for (int t = 16; t <= tmax; t *= 2) c.push_back({MPGEMM_BLOCK, t, 0});
-    for (int d = 1; d <= 3; d++) {
+    for (int d = 1; d <= 4; d++) {
         if (strassen_extended(m, d) >> d < 16 || strassen_extended(l, d) >> d < 16 ||
             strassen_extended(n, d) >> d < 16)
             continue;

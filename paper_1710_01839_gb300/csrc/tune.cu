@@ -4,7 +4,7 @@
 //      T_sample * m / r (Fig. 1; the paper's tables imply r = 2 n_min);
 //   2. keep the n_min with the smallest prediction;
 //   3. time the simple algorithm, the block algorithm with that n_min and
-//      Strassen (depths 1..3, leaves at that n_min) and pick the fastest.
+//      Strassen (depths 1..4, leaves at that n_min) and pick the fastest.
 // GPU adaptation of step 1: a reduced-row launch must still fill the machine,
 // so r is at least the rows that give one full wave of CTAs (same per-CTA
 // work as the full run), rounded up to the CTA tile; and the scale factor
@@ -255,7 +255,7 @@ int auto_choice_measured(int kind, int prec_bits, int64_t m, int64_t l, int64_t 
     rep.depth = out->depth;
     rep.best_ms = best_ms;
     rep.simple_ms = rep.block_ms = NAN;
-    for (int d = 0; d < 4; d++) rep.strassen_ms[d] = NAN;
+    for (int d = 0; d < 5; d++) rep.strassen_ms[d] = NAN;
     tune_cache_append_choice(key, &rep);
     return MPGEMM_OK;
 }
@@ -342,7 +342,7 @@ int mpgemm_tune(int kind, int prec_bits, int64_t m, int64_t l, int64_t n, const 
         ch = Choice{MPGEMM_SIMPLE, nm, 0};
         best_ms = rep->simple_ms;
     }
-    for (int d = 1; d <= 3; d++) {
+    for (int d = 1; d <= 4; d++) {
         rep->strassen_ms[d] = NAN;
         // leaves of the zero-extended problem at least 16 on every side
         if (strassen_extended(m, d) >> d < 16 || strassen_extended(l, d) >> d < 16 ||

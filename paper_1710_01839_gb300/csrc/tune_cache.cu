@@ -251,7 +251,7 @@ bool parse_choice(const JObj& o, mpgemm_tune_report* r) {
         !get_arr(o, "cand_sample_ms", (size_t)n_cand, r->cand_sample_ms) ||
         !get_arr(o, "cand_pred_ms", (size_t)n_cand, r->cand_pred_ms) ||
         !get_arr(o, "cand_full_ms", (size_t)n_cand, r->cand_full_ms) || !get_num(o, "simple_ms", &r->simple_ms) ||
-        !get_num(o, "block_ms", &r->block_ms) || !get_arr(o, "strassen_ms", 4, r->strassen_ms))
+        !get_num(o, "block_ms", &r->block_ms) || !get_arr(o, "strassen_ms", 5, r->strassen_ms))
         return false;
     for (int i = 0; i < n_cand; i++) {
         r->cand_n_min[i] = (int)cn[i];
@@ -366,7 +366,7 @@ void tune_cache_append_choice(const TuneKey& k, const mpgemm_tune_report* r) {
     s += ",\"cand_pred_ms\":" + arr_json(r->cand_pred_ms, r->n_cand);
     s += ",\"cand_full_ms\":" + arr_json(r->cand_full_ms, r->n_cand);
     s += ",\"simple_ms\":" + num_json(r->simple_ms) + ",\"block_ms\":" + num_json(r->block_ms);
-    s += ",\"strassen_ms\":" + arr_json(r->strassen_ms, 4) + "}";
+    s += ",\"strassen_ms\":" + arr_json(r->strassen_ms, 5) + "}";
     append_line(c, s);
 }
 

@@ -4,7 +4,7 @@ Section 4 times every algorithm with 1, 2, 4 and 8 OpenMP threads and
 reports, per size and thread count, the fastest algorithm and the block
 size n_min the prediction picked (Tables 1-4).  Here the same procedure
 (mpgemm_tune: predicted n_min from row-sampled runs, then simple, block and
-Strassen depths 1-3 timed) runs on SM partitions holding 1/8, 1/4, 1/2 and
+Strassen depths 1-4 timed) runs on SM partitions holding 1/8, 1/4, 1/2 and
 all of the device's SMs, on square DD, QD and 256-bit problems with the
 inputs of the large DD/QD and multi-limb workloads.
 
@@ -104,12 +104,12 @@ def precision_table(rows):
 
 
 def table(rows):
-    lines = ["| SMs | format | n | fastest | n_min | best ms | GFLOP/s | simple / block / Strassen d=1,2,3 ms |",
+    lines = ["| SMs | format | n | fastest | n_min | best ms | GFLOP/s | simple / block / Strassen d=1,2,3,4 ms |",
              "|---|---|---|---|---|---|---|---|"]
     for r in rows:
         st = r["strassen_ms"]
         others = " / ".join("-" if v is None else f"{v:.3g}"
-                            for v in [r["simple_ms"], r["block_ms"], st.get(1), st.get(2), st.get(3)])
+                            for v in [r["simple_ms"], r["block_ms"], st.get(1), st.get(2), st.get(3), st.get(4)])
         algo = r["algo"] + (f" d={r['depth']}" if r["algo"] == "strassen" else "")
         lines.append(f"| {r['sms']} | {r['fmt']} | {r['n']} | {algo} | {r['n_min']} | {r['best_ms']:.3g} | "
                      f"{r['gflops']:.3g} | {others} |")

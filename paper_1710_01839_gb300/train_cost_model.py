@@ -147,7 +147,7 @@ def auto_regret_study(shapes, reps=5):
         tmax = {"dd": 64, "qd": 32, "mp": 16}[fmt]
         ext = lambda x, d: (x + (1 << d) - 1) >> d << d
         cands = [("simple", 16, 0)] + [("block", t, 0) for t in (16, 32, 64) if t <= tmax]
-        for d in (1, 2, 3):
+        for d in (1, 2, 3, 4):
             if all((ext(x, d) >> d) >= 16 for x in (m, l, n)):
                 cands += [("strassen", t, d) for t in (16, 32, 64) if t <= tmax]
         kind = {"dd": 0, "qd": 1, "mp": 2}[fmt]
@@ -212,7 +212,7 @@ def regret_study(shapes_seed=99, count=12, max_dim=1024):
 
         tmax = {"dd": 64, "qd": 32, "mp": 16}[fmt]
         cands = [("simple", 16, 0)] + [("block", t, 0) for t in (16, 32, 64) if t <= tmax]
-        for d in (1, 2, 3):
+        for d in (1, 2, 3, 4):
             if all(x % (1 << d) == 0 and (x >> d) >= 16 for x in (m, l, n)):
                 cands += [("strassen", t, d) for t in (16, 32, 64) if t <= tmax]
         ch = cm.choice(fmt, m, l, n, prec_bits=bits)      # the library's rule (mpgemm_cost_choice)

@@ -18,7 +18,7 @@ class TuneReport(ctypes.Structure):
                 ("cand_n_min", ctypes.c_int * 8), ("cand_rows", ctypes.c_int64 * 8),
                 ("cand_sample_ms", ctypes.c_double * 8), ("cand_pred_ms", ctypes.c_double * 8),
                 ("cand_full_ms", ctypes.c_double * 8), ("simple_ms", ctypes.c_double),
-                ("block_ms", ctypes.c_double), ("strassen_ms", ctypes.c_double * 4),
+                ("block_ms", ctypes.c_double), ("strassen_ms", ctypes.c_double * 5),
                 ("tuning_ms", ctypes.c_double), ("measured", ctypes.c_int), ("from_cache", ctypes.c_int)]
 
 
@@ -36,7 +36,7 @@ def report_dict(r: TuneReport):
                       "rel_diff": (abs(pred - full) / full) if full else None})
     out = {"algo": ALGO_NAME[r.algo], "n_min": r.n_min, "depth": r.depth, "best_ms": r.best_ms,
            "candidates": cands, "simple_ms": _nan(r.simple_ms), "block_ms": r.block_ms,
-           "strassen_ms": {d: _nan(r.strassen_ms[d]) for d in (1, 2, 3)}, "tuning_ms": r.tuning_ms,
+           "strassen_ms": {d: _nan(r.strassen_ms[d]) for d in (1, 2, 3, 4)}, "tuning_ms": r.tuning_ms,
            "measured": r.measured, "from_cache": bool(r.from_cache)}
     # Section 3's claim: tuning costs 1.6-2.3x more without the prediction.
     # Device time of the procedure with the sampled runs vs. with full runs

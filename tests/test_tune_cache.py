@@ -84,10 +84,10 @@ def test_round_trip_and_auto(tuner, tmp_path):
     path = tmp_path / "tune.jsonl"
     tuner.lib().mpgemm_tune_forget()
     rep, calls = _run(tuner, path)
-    # 6 sampled + 6 full block runs (VERIFY), simple, Strassen d = 1..3 (at
+    # 6 sampled + 6 full block runs (VERIFY), simple, Strassen d = 1..4 (at
     # m = n = 4096 every sample has fewer rows than the full run; the final
     # block run at the chosen n_min is the VERIFY run of the same configuration)
-    assert rep["measured"] == len(calls) == 6 + 6 + 1 + 3
+    assert rep["measured"] == len(calls) == 6 + 6 + 1 + 4
     assert not rep["from_cache"]
     assert (rep["algo"], rep["n_min"], rep["depth"]) == ("strassen", 64, 2)
     lines = [json.loads(x) for x in path.read_text().splitlines()]
@@ -153,7 +153,7 @@ def test_damaged_and_foreign_lines_are_skipped(tuner, tmp_path):
     tuner.cache_open(path)
     try:
         st = tuner.cache_stats()
-        assert st["open"] and st["choices"] == 1 and st["measurements"] == 16
+        assert st["open"] and st["choices"] == 1 and st["measurements"] == 17
         assert st["skipped_lines"] == 4 and st["foreign_records"] == 2
         calls = []
         tuner.set_timer(_counting(calls))
