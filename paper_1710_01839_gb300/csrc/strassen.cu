@@ -38,6 +38,13 @@ static ChildOps b_side_ops() {
     return o;
 }
 
+// The same tables at compile time (side 0: A, 1: B; what 0: qa, 1: qb, 2: op).
+__host__ __device__ constexpr int child_op(int side, int what, int c) {
+    constexpr signed char t[2][3][7] = {{{0, 2, 0, 3, 0, 2, 1}, {3, 3, 0, 0, 1, 0, 3}, {1, 1, 0, 0, 1, 2, 2}},
+                                        {{0, 0, 1, 2, 3, 0, 2}, {3, 0, 3, 0, 0, 1, 3}, {1, 0, 2, 2, 0, 1, 1}}};
+    return t[side][what][c];
+}
+
 // ---------------------------------------------------------------- element ops
 
 struct DDE {
@@ -77,26 +84,33 @@ __device__ __forceinline__ void ld_ext(const View<const double>& V, int64_t p, i
     }
 }
 
-// Children operands: grid (cols/128, rows, parents*7); the parent holds xr x
-// xc elements (2 rows x 2 cols except where zero-extended).
-template <class E>
-__global__ void k_expand(int64_t rows, int64_t cols, int64_t xr, int64_t xc, View<const double> X, View<double> Y,
-                         ChildOps ops) {
+// Children operands: grid (cols/128, rows, parents); the parent holds xr x
+// xc elements (2 rows x 2 cols except where zero-extended).  A thread reads
+// element (i, j) of the parent's four quadrants once and writes it to all
+// seven children.
+template <class E, int SIDE>
+__global__ void k_expand(int64_t rows, int64_t cols, int64_t xr, int64_t xc, View<const double> X, View<double> Y) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = blockIdx.y;
-    int z = blockIdx.z, p = z / 7, c = z % 7;
+    int64_t p = blockIdx.z;
     if (j >= cols) return;
-    int qa = ops.qa[c], qb = ops.qb[c], op = ops.op[c];
-    double x[E::P], y[E::P], r[E::P];
-    ld_ext<E>(X, p, (qa >> 1) * rows + i, (qa & 1) * cols + j, xr, xc, x);
-    if (op == 0) {
-        st<E>(Y, z, i, j, x);
-        return;
+    double Q[4][E::P];
+#pragma unroll
+    for (int q = 0; q < 4; q++) ld_ext<E>(X, p, (q >> 1) * rows + i, (q & 1) * cols + j, xr, xc, Q[q]);
+#pragma unroll
+    for (int c = 0; c < 7; c++) {
+        constexpr int side = SIDE;
+        const int qa = child_op(side, 0, c), qb = child_op(side, 1, c), op = child_op(side, 2, c);
+        if (op == 0) {
+            st<E>(Y, p * 7 + c, i, j, Q[qa]);
+        } else {
+            double y[E::P], r[E::P];
+#pragma unroll
+            for (int q = 0; q < E::P; q++) y[q] = op == 2 ? -Q[qb][q] : Q[qb][q];
+            E::add(Q[qa], y, r);
+            st<E>(Y, p * 7 + c, i, j, r);
+        }
     }
-    ld_ext<E>(X, p, (qb >> 1) * rows + i, (qb & 1) * cols + j, xr, xc, y);
-    if (op == 2) neg<E>(y);
-    E::add(x, y, r);
-    st<E>(Y, z, i, j, r);
 }
 
 // Parent products from children: grid (cols/128, rows, parents); only the
@@ -314,7 +328,6 @@ int strassen_ddqd_ws(int kind, int64_t m, int64_t l, int64_t n, View<const doubl
     Levels<double> L;
     int rc = carve<double>((char*)ws, ws_bytes, eb, P, mq, lq, nq, depth, L);
     if (rc) return rc;
-    const ChildOps ao = a_side_ops(), bo = b_side_ops();
     unsigned parents = 1;
     for (int k = 1; k <= depth; k++) {
         int64_t mk = mq >> k, lk = lq >> k, nk = nq >> k;
@@ -322,13 +335,13 @@ int strassen_ddqd_ws(int kind, int64_t m, int64_t l, int64_t n, View<const doubl
         View<const double> pb = k == 1 ? B : cview(L.SB[k - 1]);
         // level 1 reads the caller's m x l and l x n matrices, deeper levels whole parents
         const int64_t ar = k == 1 ? m : 2 * mk, ac = k == 1 ? l : 2 * lk, bc = k == 1 ? n : 2 * nk;
-        dim3 ga(ceil_div(lk, 128), (unsigned)mk, parents * 7), gb(ceil_div(nk, 128), (unsigned)lk, parents * 7);
+        dim3 ga(ceil_div(lk, 128), (unsigned)mk, parents), gb(ceil_div(nk, 128), (unsigned)lk, parents);
         if (kind == MPGEMM_KIND_DD) {
-            k_expand<DDE><<<ga, 128, 0, s>>>(mk, lk, ar, ac, pa, L.SA[k], ao);
-            k_expand<DDE><<<gb, 128, 0, s>>>(lk, nk, ac, bc, pb, L.SB[k], bo);
+            k_expand<DDE, 0><<<ga, 128, 0, s>>>(mk, lk, ar, ac, pa, L.SA[k]);
+            k_expand<DDE, 1><<<gb, 128, 0, s>>>(lk, nk, ac, bc, pb, L.SB[k]);
         } else {
-            k_expand<QDE><<<ga, 128, 0, s>>>(mk, lk, ar, ac, pa, L.SA[k], ao);
-            k_expand<QDE><<<gb, 128, 0, s>>>(lk, nk, ac, bc, pb, L.SB[k], bo);
+            k_expand<QDE, 0><<<ga, 128, 0, s>>>(mk, lk, ar, ac, pa, L.SA[k]);
+            k_expand<QDE, 1><<<gb, 128, 0, s>>>(lk, nk, ac, bc, pb, L.SB[k]);
         }
         if ((rc = check_launch())) return rc;
         parents *= 7;

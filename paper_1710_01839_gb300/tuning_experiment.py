@@ -4,12 +4,13 @@ is run with MPGEMM_TUNE_VERIFY, which times the block algorithm on the
 reduced-row sample AND in full for every n_min.  From one run:
 
   * with prediction:    device time of the sampled runs + the final timings
-                        (simple, block at the predicted n_min, Strassen 1..3);
+                        (simple, block at the predicted n_min, Strassen 1..4);
   * without prediction: device time of the full block runs for every n_min
                         + the same final timings (the paper's exhaustive
                         alternative; it reports 1.6-2.3x more);
   * the FP32 MLP:       host time of its decision (nothing timed) and the
-                        measured time of its pick against the tuned best;
+                        time of its pick against the tuned best, both with
+                        the library's timer (mpgemm_time_config);
   * the fastest algorithm and, per format, the Strassen threshold: the
     smallest n from which Strassen is the fastest at every larger size
     (Table 2's "threshold" column).
@@ -41,20 +42,6 @@ def _operands(fmt, n, torch, I):
         B = I.mp_random(n, n, w, 1711 + n).view("int32")
     Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     return Ad, Bd, torch.empty_like(Ad)
-
-
-def _time_call(fn, torch, reps=2):
-    fn()
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        fn()
-        b.record()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    return sorted(ts)[len(ts) // 2]
 
 
 def run(formats=("dd", "qd", "mp128", "mp256", "mp1024"), sizes=(128, 256, 512, 1024)):
@@ -91,16 +78,14 @@ def run(formats=("dd", "qd", "mp128", "mp256", "mp1024"), sizes=(128, 256, 512, 
                     t1 = time.perf_counter()
                     mc = costmodel.choice(kind, n, n, n, prec_bits=bits)
                     dec_ms = (time.perf_counter() - t1) * 1e3
-                    if kind == "mp":
-                        call = lambda: mpg.gemm_mp(Ad, Bd, bits, Cd, algo=mc["algo"], n_min=mc["n_min"],
-                                                   depth=mc["depth"])
-                    else:
-                        f = mpg.gemm_dd if kind == "dd" else mpg.gemm_qd
-                        call = lambda: f(Ad, Bd, Cd, algo=mc["algo"], n_min=mc["n_min"], depth=mc["depth"])
-                    t_mlp = _time_call(call, torch)
-                    t_best = _time_call(
-                        (lambda: mpg.gemm_mp(Ad, Bd, bits, Cd, **choice)) if kind == "mp" else
-                        (lambda: (mpg.gemm_dd if kind == "dd" else mpg.gemm_qd)(Ad, Bd, Cd, **choice)), torch)
+                    # both with the library's timer (calls back to back from C, the steady-state
+                    # cost of a call, as MPGEMM_AUTO times): a timer in Python would add its own
+                    # per-call overhead, a large share at these sizes
+                    from paper_1710_01839_gb300.train_cost_model import _time_library
+                    code = {"dd": 0, "qd": 1, "mp": 2}[kind]
+                    t_mlp, t_best = _time_library(
+                        code, bits, n, n, n, Ad, Bd, Cd,
+                        [(mc["algo"], mc["n_min"], mc["depth"]), (choice["algo"], choice["n_min"], choice["depth"])])
                     row["mlp"] = {"choice": {k: mc[k] for k in ("algo", "n_min", "depth")},
                                   "decision_host_ms": dec_ms, "ms": t_mlp, "tuned_best_ms_same_session": t_best,
                                   "regret": t_mlp / t_best - 1}
