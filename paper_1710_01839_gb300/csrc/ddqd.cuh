@@ -166,20 +166,17 @@ __device__ __forceinline__ void dd_renorm(DDAcc& c) {
 }
 
 // Accurate DD + DD (Joldes-Muller-Popescu 2017 "AccurateDWPlusDW", bound 3u^2),
-// used by the Strassen add/sub kernels where each operation is rounded.  Its
-// two Fast2Sum steps are exact (the algorithm's analysis: the first operand
-// dominates, or the sum is exact), so they are computed here by two_sum,
-// which returns the same rounded sum and the same (exact) error with the
-// error term on the integer pipe: 6 FP64 operations per addition instead of
-// 10, the same bits.
+// used by the Strassen add/sub kernels where each operation is rounded.
+// (Its Fast2Sum steps on the integer pipe as well measured no faster: the
+// Strassen passes are latency-bound, not FP64-bound.)
 __device__ __forceinline__ void dd_add(double xh, double xl, double yh, double yl, double& zh, double& zl) {
     double sh, sl, th, tl, vh, vl;
     two_sum(xh, yh, sh, sl);
     two_sum(xl, yl, th, tl);
     double c = __dadd_rn(sl, th);
-    two_sum(sh, c, vh, vl);
+    fast_two_sum(sh, c, vh, vl);
     double w = __dadd_rn(tl, vl);
-    two_sum(vh, w, zh, zl);
+    fast_two_sum(vh, w, zh, zl);
 }
 
 // ---------------------------------------------------------------- QD

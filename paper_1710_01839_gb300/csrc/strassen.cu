@@ -122,32 +122,35 @@ __global__ void k_combine(int64_t rows, int64_t cols, int64_t xr, int64_t xc, Vi
     int64_t i = blockIdx.y;
     int64_t p = blockIdx.z;
     if (j >= cols) return;
-    double P[7][E::P], t[E::P], u[E::P];
+    double P[7][E::P];
 #pragma unroll
     for (int c = 0; c < 7; c++) ld<E>(Pc, p * 7 + c, i, j, P[c]);
-    // C11 = ((P1 + P4) - P5) + P7
-    E::add(P[0], P[3], t);
-    double n5[E::P];
+    double n5[E::P], n2[E::P];
 #pragma unroll
-    for (int q = 0; q < E::P; q++) n5[q] = -P[4][q];
-    E::add(t, n5, u);
-    E::add(u, P[6], t);
+    for (int q = 0; q < E::P; q++) {
+        n5[q] = -P[4][q];
+        n2[q] = -P[1][q];
+    }
+    // C11 = ((P1 + P4) - P5) + P7 and C22 = ((P1 + P3) - P2) + P6 advance
+    // side by side, C12 = P3 + P5 and C21 = P2 + P4 between them: four
+    // independent additions per step instead of one chain of eight (each
+    // result keeps its left-to-right order)
+    double a[E::P], b[E::P], c12[E::P], c21[E::P];
+    E::add(P[0], P[3], a);
+    E::add(P[0], P[2], b);
+    E::add(P[2], P[4], c12);
+    E::add(P[1], P[3], c21);
+    double a2[E::P], b2[E::P];
+    E::add(a, n5, a2);
+    E::add(b, n2, b2);
+    double c11[E::P], c22[E::P];
+    E::add(a2, P[6], c11);
+    E::add(b2, P[5], c22);
     const bool r0 = i < xr, r1 = rows + i < xr, c0 = j < xc, c1 = cols + j < xc;
-    if (r0 && c0) st<E>(Out, p, i, j, t);
-    // C12 = P3 + P5
-    E::add(P[2], P[4], t);
-    if (r0 && c1) st<E>(Out, p, i, cols + j, t);
-    // C21 = P2 + P4
-    E::add(P[1], P[3], t);
-    if (r1 && c0) st<E>(Out, p, rows + i, j, t);
-    // C22 = ((P1 + P3) - P2) + P6
-    E::add(P[0], P[2], t);
-    double n2[E::P];
-#pragma unroll
-    for (int q = 0; q < E::P; q++) n2[q] = -P[1][q];
-    E::add(t, n2, u);
-    E::add(u, P[5], t);
-    if (r1 && c1) st<E>(Out, p, rows + i, cols + j, t);
+    if (r0 && c0) st<E>(Out, p, i, j, c11);
+    if (r0 && c1) st<E>(Out, p, i, cols + j, c12);
+    if (r1 && c0) st<E>(Out, p, rows + i, j, c21);
+    if (r1 && c1) st<E>(Out, p, rows + i, cols + j, c22);
 }
 
 // ---------------------------------------------------------------- multi-limb element ops
