@@ -59,7 +59,8 @@ MP_INSTR_PER_MAC = {128: 232.2, 256: 376.7, 512: 963.6, 1024: 2610.1, 2048: 8472
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from ncu captures of exactly these configurations (profiles/):
 # (fmt, n, algo, n_min, depth) -> bytes.  Absent => null.
-TRAFFIC_BYTES = {("dd", 2048, "strassen", 32, 3): 728.3e6 + 337.8e6}
+TRAFFIC_BYTES = {("dd", 2048, "strassen", 32, 3): 728.3e6 + 337.8e6,
+                 ("dd", 2048, "strassen", 32, 4): 1.268e9 + 0.600e9}
 
 
 def parse():
@@ -678,10 +679,10 @@ def workload_name(fmt, n, prec=256):
 # ---------------------------------------------------------------- reference arm (the oracle)
 
 # The configuration the reference arm times: what the Section 3 tuner picks
-# on GB300 at the benchmark's sizes (Strassen depth 3 in every measured
-# format; the oracle's n_min only blocks its CPU loops, the arithmetic of
-# every c_ij is the same at any n_min).
-REF_ALGO, REF_N_MIN, REF_DEPTH = "strassen", 32, 3
+# on GB300 for the benchmark's DD 2048^3 workload (Strassen depth 4, n_min
+# 32; the oracle's n_min only blocks its CPU loops, the arithmetic of every
+# c_ij is the same at any n_min).
+REF_ALGO, REF_N_MIN, REF_DEPTH = "strassen", 32, 4
 REF_ARM_MAX_S = 300.0   # whole products for every step only while the run stays within this estimate
 
 

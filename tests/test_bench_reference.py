@@ -28,7 +28,7 @@ def test_reference_arm_line(fmt):
     assert d["dtype"] == ("u32" if fmt == "mp" else "f64")
     assert "m=l=n=64" in d["config"]["workload"]
     # the configuration the GPU arm's tuner picks at the benchmark sizes: the whole Strassen product
-    assert (d["config"]["algo"], d["config"]["strassen_depth"]) == ("strassen", 3)
+    assert (d["config"]["algo"], d["config"]["strassen_depth"]) == ("strassen", 4)
     assert "whole product" in d["cpu_baseline"]["sample"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]

@@ -6,7 +6,7 @@ it belongs to, an access outside is not made and is counted
 (both stay inside a larger allocation, so nothing outside any allocation is
 touched even without the check); then every algorithm, at sizes that are
 multiples of no tile (1 x 1 x 1, primes, ragged; Strassen's zero extension
-at depths 1-3), the one-thread and the warp-cooperative multi-limb kernels
+at depths 1-4), the one-thread and the warp-cooperative multi-limb kernels
 and DD / QD on the integer pipe make no access outside their buffers and
 give the same bits as the normal build."""
 
@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 mpg = pytest.importorskip("paper_1710_01839_gb300")
 
 SHAPES = [(1, 1, 1), (2, 3, 5), (17, 31, 13), (37, 53, 29), (65, 33, 47)]
-CONFIGS = [(0, 16, 0), (1, 16, 0), (1, 32, 0), (1, 64, 0), (2, 16, 1), (2, 16, 2), (2, 16, 3)]
+CONFIGS = [(0, 16, 0), (1, 16, 0), (1, 32, 0), (1, 64, 0), (2, 16, 1), (2, 16, 2), (2, 16, 3), (2, 16, 4)]
 
 
 @pytest.fixture(scope="module")

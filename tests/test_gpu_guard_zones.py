@@ -5,7 +5,7 @@ at ragged sizes (not multiples of any tile, Strassen's zero extension at
 work).  A write past a buffer changes a guard zone; a read past an operand
 brings NaN or the pattern into the result, which then differs from the same
 call on plain buffers.  Both are checked for DD / QD (simple, block, every
-tile, Strassen depths 1-3), multi-limb (128 / 256 / 1024 bits), split
+tile, Strassen depths 1-4), multi-limb (128 / 256 / 1024 bits), split
 precision (int8 and FP8 digits, DD and QD), DD / QD on the integer pipe and
 a batched plan."""
 
@@ -84,10 +84,10 @@ def test_dd_qd_all_algorithms(fmt, m, l, n):
     A, B = _dd_like(P, m, l, 5), _dd_like(P, l, n, 6)
     Ag, Bg = Guarded((P, m, l), torch.float64, torch.from_numpy(A)), Guarded((P, l, n), torch.float64, torch.from_numpy(B))
     Ap, Bp = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    ws = _workspace(max(mpg.workspace_size(fmt, m, l, n, algo="strassen", depth=d) for d in (1, 2, 3)))
+    ws = _workspace(max(mpg.workspace_size(fmt, m, l, n, algo="strassen", depth=d) for d in (1, 2, 3, 4)))
     tiles = (16, 32, 64) if fmt == "dd" else (16, 32)
     configs = [("simple", 16, 0)] + [("block", t, 0) for t in tiles] + [("strassen", t, d) for t in tiles[:2]
-                                                                         for d in (1, 2, 3)]
+                                                                         for d in (1, 2, 3, 4)]
     for algo, nm, d in configs:
         Cg = Guarded((P, m, n), torch.float64)
         f(Ag.t, Bg.t, Cg.t, algo=algo, n_min=nm, depth=d)

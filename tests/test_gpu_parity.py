@@ -212,7 +212,7 @@ def test_mp_cancellation_and_zeros():
 
 # ---------------------------------------------------------------- Strassen
 
-@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("depth", [1, 2, 3, 4])
 @pytest.mark.parametrize("fmt", ["dd", "qd", "mp128"])
 def test_strassen_integers_bit_exact(fmt, depth):
     m, l, n = 64, 48, 40
@@ -230,7 +230,7 @@ def test_strassen_integers_bit_exact(fmt, depth):
     assert np.array_equal(C, want)
 
 
-@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("depth", [1, 2, 3, 4])
 def test_dd_strassen_bound(depth):
     n = 256
     A, B = I.dd_random(n, n, 700), I.dd_random(n, n, 701)
@@ -254,7 +254,7 @@ def test_qd_strassen_bound(depth):
     assert np.max(err) <= 2.0**-200 * n * amax * bmax
 
 
-@pytest.mark.parametrize("depth", [1, 2])
+@pytest.mark.parametrize("depth", [1, 2, 3, 4])
 def test_mp_strassen_bit_exact_vs_oracle(depth):
     w, n = 4, 32
     A, B = I.mp_random(n, n, w, 710 + depth), I.mp_random(n, n, w, 720 + depth)
@@ -266,7 +266,7 @@ def test_mp_strassen_bit_exact_vs_oracle(depth):
 # Sizes that 2^depth does not divide: A and B are zero-extended to the next
 # multiple of 2^depth (the oracle makes the same reading), so integer
 # products stay exact and the multi-limb result is the oracle's bit for bit.
-@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("depth", [1, 2, 3, 4])
 @pytest.mark.parametrize("fmt", ["dd", "qd", "mp128"])
 def test_strassen_odd_sizes_integers_bit_exact(fmt, depth):
     m, l, n = 67, 45, 37
@@ -382,24 +382,27 @@ def test_paper_matrices_dd_closed_form():
 
 # ---------------------------------------------------------------- the bench's own launch configurations
 
-def test_dd_bench_configuration_sampled():
+@pytest.mark.parametrize("depth", [3, 4])
+def test_dd_bench_configuration_sampled(depth):
     """DD 2048^3 with the bench's inputs and its tuned launch (Strassen depth
-    3, n_min 32): sampled entries against the exact product, Strassen bound."""
+    4, n_min 32; depth 3 the earlier choice): sampled entries against the
+    exact product, Strassen bound."""
     n = 2048
     A = I.dd_random(n, n, I.seed_for(1, 0), exp_spread=20)
     B = I.dd_random(n, n, I.seed_for(1, 1), exp_spread=20)
-    C = host(mpg.gemm_dd(dev(A), dev(B), algo="strassen", n_min=32, depth=3))
+    C = host(mpg.gemm_dd(dev(A), dev(B), algo="strassen", n_min=32, depth=depth))
     ii, jj = sample_indices(n, n, 384, seed=2048)
     err, _ = oracle.exact_check(A, B, C, ii, jj)
     amax, bmax = np.max(np.abs(A[0] + A[1])), np.max(np.abs(B[0] + B[1]))
     assert np.max(err) <= 2.0**-96 * n * amax * bmax
 
 
-def test_qd_bench_configuration_sampled():
+@pytest.mark.parametrize("depth", [3, 4])
+def test_qd_bench_configuration_sampled(depth):
     n = 1024
     A = I.qd_random(n, n, I.seed_for(1, 0), exp_spread=20)
     B = I.qd_random(n, n, I.seed_for(1, 1), exp_spread=20)
-    C = host(mpg.gemm_qd(dev(A), dev(B), algo="strassen", n_min=16, depth=3))
+    C = host(mpg.gemm_qd(dev(A), dev(B), algo="strassen", n_min=16, depth=depth))
     ii, jj = sample_indices(n, n, 128, seed=1024)
     err, _ = oracle.exact_check(A, B, C, ii, jj)
     assert np.max(err) <= 2.0**-200 * n * np.max(np.abs(A[0])) * np.max(np.abs(B[0]))
@@ -458,8 +461,8 @@ def test_strassen_error_margins_at_bench_sizes(capsys):
     rows = []
     for fmt, n, f, bound, cases in (
             ("dd", 2048, mpg.gemm_dd, 2.0**-96, [("block", 32, 0), ("strassen", 32, 1), ("strassen", 32, 2),
-                                                   ("strassen", 32, 3)]),
-            ("qd", 1024, mpg.gemm_qd, 2.0**-200, [("block", 16, 0), ("strassen", 16, 3)])):
+                                                   ("strassen", 32, 3), ("strassen", 32, 4)]),
+            ("qd", 1024, mpg.gemm_qd, 2.0**-200, [("block", 16, 0), ("strassen", 16, 3), ("strassen", 16, 4)])):
         gen = I.dd_random if fmt == "dd" else I.qd_random
         A, B = gen(n, n, I.seed_for(1, 0), exp_spread=20), gen(n, n, I.seed_for(1, 1), exp_spread=20)
         Ad, Bd = dev(A), dev(B)

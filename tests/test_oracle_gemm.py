@@ -3,7 +3,7 @@
 * Eq 2 (block, in-place accumulation over K blocks) is bit-identical to
   Eq 1 (simple) for every format, ragged sizes included.
 * Eq 3 (Strassen) is bit-identical to Eq 1 on small integer matrices, where
-  every intermediate is exact, at depths 1-3 in every format.
+  every intermediate is exact, at depths 1-4 in every format.
 * DD and QD results lie within 4 l 2^-104 |A||B| (DD) and 4 l 2^-208 |A||B|
   (QD) of the exact product, computed with Fractions; DD Strassen within
   2^-96 l max|A| max|B|.
@@ -65,7 +65,7 @@ def test_block_equals_simple_ragged(fmt):
 
 # ---------------------------------------------------------------- Strassen == simple on integers
 
-@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("depth", [1, 2, 3, 4])
 @pytest.mark.parametrize("fmt", ["dd", "qd", "mp128"])
 def test_strassen_equals_simple_on_integers(fmt, depth):
     m, l, n = 16, 24, 8
@@ -90,7 +90,7 @@ def test_strassen_equals_simple_on_integers(fmt, depth):
 # Dimensions that 2^depth does not divide run on zero-extended matrices: on
 # integer matrices every intermediate is still exact, so the result is the
 # exact product, bit-identical to Eq 1, at any depth.
-@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("depth", [1, 2, 3, 4])
 @pytest.mark.parametrize("fmt", ["dd", "qd", "mp128"])
 @pytest.mark.parametrize("m,l,n", [(13, 21, 7), (1, 5, 3), (9, 8, 17)])
 def test_strassen_odd_dimensions_equal_simple_on_integers(fmt, depth, m, l, n):
