@@ -240,11 +240,11 @@ def split_precision_extra(args, stream):
                         "frac": int_ops / (oz_kms * 1e-3) / 1e12 / s8_peak,
                         "kernel": f"k_ozaki_levels, {pairs} slice pairs x 2 n^2 l int8 ops", "kernel_ms": oz_kms,
                         "kernel_share": oz_kms / oz_ms}}
-    for name, algo, nm, d in (("plain_dd_block", "block", 64, 0), ("plain_dd_strassen3", "strassen", 32, 3)):
+    for name, algo, nm, d in (("plain_dd_block", "block", 64, 0), ("plain_dd_strassen4", "strassen", 32, 4)):
         ms, _ = timed_calls(lambda: mpg.gemm_dd(Ad, Bd, Cd, algo=algo, n_min=nm, depth=d), stream, reps, flush)
         out[name + "_gflops"] = flops / (ms * 1e-3) / 1e9
         out[name + "_ms"] = ms
-    out["speedup_vs_best_plain_dd"] = min(out["plain_dd_block_ms"], out["plain_dd_strassen3_ms"]) / oz_ms
+    out["speedup_vs_best_plain_dd"] = min(out["plain_dd_block_ms"], out["plain_dd_strassen4_ms"]) / oz_ms
     # FP8 digits: balanced base-32, e4m3 tcgen05 MMAs with exact f32 accumulation in tensor memory
     S8 = args.ozaki_fp8_slices
 
@@ -258,7 +258,7 @@ def split_precision_extra(args, stream):
     f8_flops = 2.0 * n * n * lp * pairs8
     out["fp8"] = {"slices": S8, "gflops": flops / (f8_ms * 1e-3) / 1e9, "ms": f8_ms,
                   "speedup_vs_int8": oz_ms / f8_ms,
-                  "speedup_vs_best_plain_dd": min(out["plain_dd_block_ms"], out["plain_dd_strassen3_ms"]) / f8_ms,
+                  "speedup_vs_best_plain_dd": min(out["plain_dd_block_ms"], out["plain_dd_strassen4_ms"]) / f8_ms,
                   "roofline": tc_roofline(f8_flops, f8_kms, f"k_levels_tc (tcgen05 kind::f8f6f4), {pairs8} slice "
                                                             "pairs x 2 n^2 l", f8_ms)}
     return out
@@ -327,12 +327,12 @@ def qd_split_extra(args, stream):
            "qd_split_gflops": flops / (sp_ms * 1e-3) / 1e9, "qd_split_ms": sp_ms,
            "roofline": tc_roofline(tc_flops, sp_kms, f"k_levels_tc (tcgen05 kind::f8f6f4), {S * (S + 1) // 2} "
                                                      "slice pairs x 2 n^2 l", sp_ms)}
-    for name, algo, nm, d in (("plain_qd_block", "block", 32, 0), ("plain_qd_strassen3", "strassen", 16, 3)):
+    for name, algo, nm, d in (("plain_qd_block", "block", 32, 0), ("plain_qd_strassen4", "strassen", 16, 4)):
         ms, _ = timed_calls(lambda: mpg.gemm_qd(Ad, Bd, Cd, algo=algo, n_min=nm, depth=d), stream, args.extra_reps,
                             flush)
         out[name + "_gflops"] = flops / (ms * 1e-3) / 1e9
         out[name + "_ms"] = ms
-    out["speedup_vs_best_plain_qd"] = min(out["plain_qd_block_ms"], out["plain_qd_strassen3_ms"]) / sp_ms
+    out["speedup_vs_best_plain_qd"] = min(out["plain_qd_block_ms"], out["plain_qd_strassen4_ms"]) / sp_ms
     return out
 
 
@@ -901,7 +901,7 @@ def main():
         pextra = paper_matrices_extra(args, stream)
         if qextra is not None and "qd" in vextra:
             vextra["qd"]["speedup_vs_fp64_pipe"] = vextra["qd"]["gflops"] / max(qextra["plain_qd_block_gflops"],
-                                                                                qextra["plain_qd_strassen3_gflops"])
+                                                                                qextra["plain_qd_strassen4_gflops"])
         bextra = batched_extra(args, stream)
 
     if dist:
@@ -929,7 +929,7 @@ def main():
         summary["dd_split_4096"] = {
             "int8_gflops": extras["ozaki_gflops"], "fp8_gflops": f8["gflops"],
             "plain_dd_block_gflops": extras["plain_dd_block_gflops"],
-            "plain_dd_strassen3_gflops": extras["plain_dd_strassen3_gflops"],
+            "plain_dd_strassen4_gflops": extras["plain_dd_strassen4_gflops"],
             "fp8_speedup_vs_best_plain_dd": f8["speedup_vs_best_plain_dd"],
             "int8_speedup_vs_best_plain_dd": extras["speedup_vs_best_plain_dd"],
             "fp8_level_kernel_frac": f8["roofline"]["frac"], "int8_level_kernel_frac": extras["roofline"]["frac"]}
