@@ -29,7 +29,9 @@
 
 namespace mpg {
 
-enum TileKind : int { T_DD16 = 0, T_DD32 = 1, T_QD16 = 2, T_QD32 = 3, T_MP256 = 4, T_MP128 = 5 };
+// T_MP128 and T_MP256C: the integer pipe's images of DD / QD operands (similar magnitudes:
+// the add's alignment shortcut); T_MP256: the caller's 256-bit operands.
+enum TileKind : int { T_DD16 = 0, T_DD32 = 1, T_QD16 = 2, T_QD32 = 3, T_MP256 = 4, T_MP128 = 5, T_MP256C = 6 };
 
 struct DevDesc {
     int tk;
@@ -67,14 +69,16 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
         const Work w = work[it];
         const DevDesc d = descs[w.desc];
         const int64_t i0 = (int64_t)w.tm * d.tile, j0 = (int64_t)w.tn * d.tile;
-        if (d.tk == T_MP256 || d.tk == T_MP128) {
+        if (d.tk == T_MP256 || d.tk == T_MP128 || d.tk == T_MP256C) {
             View<const uint32_t> a = planes_view((const uint32_t*)d.A, d.m, d.l);
             View<const uint32_t> b = planes_view((const uint32_t*)d.B, d.l, d.n);
             View<uint32_t> c = planes_view((uint32_t*)d.C, d.m, d.n);
             if (d.tk == T_MP256)
                 mp_block_tile<8, 8>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
+            else if (d.tk == T_MP256C)
+                mp_block_tile<8, 8, true>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
             else
-                mp_block_tile<4, 8>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
+                mp_block_tile<4, 8, true>(d.m, d.l, d.n, a, b, c, 0, i0, j0, reinterpret_cast<uint32_t*>(sm), st);
         } else if constexpr (!MP_ONLY) {
             View<const double> a = planes_view((const double*)d.A, d.m, d.l);
             View<const double> b = planes_view((const double*)d.B, d.l, d.n);
@@ -249,7 +253,7 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
         }
         int tk;
         if (d.engine == 1) {
-            tk = d.kind == MPGEMM_KIND_DD ? T_MP128 : T_MP256;
+            tk = d.kind == MPGEMM_KIND_DD ? T_MP128 : T_MP256C;
         } else if (int rc = desc_tile_kind(d, tile, &tk)) {
             delete P;
             return rc;
@@ -317,7 +321,7 @@ int mpgemm_batched_plan(const mpgemm_desc* descs, int count, mpgemm_plan* out) {
     int sms = 0, occ = 0;
     if (!rc && (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device)) != cudaSuccess) fail(e);
     P->mp_only = count > 0;
-    for (int i = 0; i < count; i++) P->mp_only &= dd[i].tk == T_MP128 || dd[i].tk == T_MP256;
+    for (int i = 0; i < count; i++) P->mp_only &= dd[i].tk == T_MP128 || dd[i].tk == T_MP256 || dd[i].tk == T_MP256C;
     if (!rc && (e = P->mp_only ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<true>, 256, 0)
                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<false>, 256, 0)) !=
                    cudaSuccess)

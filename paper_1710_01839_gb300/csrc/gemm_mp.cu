@@ -14,7 +14,7 @@
 
 namespace mpg {
 
-template <int W>
+template <int W, bool CLOSE>
 __global__ void __launch_bounds__(256) k_mp_simple(int64_t m, int64_t l, int64_t n, View<const uint32_t> A,
                                                    View<const uint32_t> B, View<uint32_t> C, unsigned* status) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) k_mp_simple(int64_t m, int64_t l, int64_t
         MPV<W> a, b;
         load_mp(a, A, A.at(z, 0, i, k));
         load_mp(b, B, B.at(z, 0, k, j));
-        mp_mac(c, a, b, st);
+        mp_mac<W, CLOSE>(c, a, b, st);
     }
     store_mp(c, C, C.at(z, 0, i, j));
     if (st) atomicOr(status, st);
@@ -44,7 +44,7 @@ constexpr int mp_block_min_ctas() {
 
 // CTA = 16 x 16 outputs (mp_block_tile); CTA order follows the super-tile
 // raster with group G.
-template <int W, int KT>
+template <int W, int KT, bool CLOSE>
 __global__ void __launch_bounds__(256, mp_block_min_ctas<W>()) k_mp_block(int64_t m, int64_t l, int64_t n, View<const uint32_t> A,
                                                   View<const uint32_t> B, View<uint32_t> C, unsigned G,
                                                   unsigned* status) {
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256, mp_block_min_ctas<W>()) k_mp_block(int64_
     unsigned tm, tn;
     raster(blockIdx.x, tiles_m, tiles_n, G, tm, tn);
     unsigned st = 0u;
-    mp_block_tile<W, KT>(m, l, n, A, B, C, blockIdx.y, (int64_t)tm * BM, (int64_t)tn * BM, sm, st);
+    mp_block_tile<W, KT, CLOSE>(m, l, n, A, B, C, blockIdx.y, (int64_t)tm * BM, (int64_t)tn * BM, sm, st);
     if (st) atomicOr(status, st);
 }
 
@@ -75,24 +75,43 @@ __global__ void k_mp_addsub(int64_t r, int64_t c, View<uint32_t> Z, View<const u
     if (st) atomicOr(status, st);
 }
 
+// Operands of similar magnitude (set by the integer pipe's DD / QD
+// conversions around their GEMMs): the kernels with mp_add's alignment
+// shortcut (widths 2 to 16, the integer pipe's).
+static thread_local bool t_close_operands = false;
+
+CloseOperandsScope::CloseOperandsScope() : prev_(t_close_operands) { t_close_operands = true; }
+CloseOperandsScope::~CloseOperandsScope() { t_close_operands = prev_; }
+
+template <int W, bool CLOSE>
+static void launch_mp(int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const uint32_t> A,
+                      View<const uint32_t> B, View<uint32_t> C, int n_min, unsigned* status, cudaStream_t s) {
+    if (algo == MPGEMM_SIMPLE) {
+        dim3 blk(16, 16);
+        dim3 grd(ceil_div(n, 16), ceil_div(m, 16), (unsigned)batch);
+        k_mp_simple<W, CLOSE><<<grd, blk, 0, s>>>(m, l, n, A, B, C, status);
+    } else {
+        unsigned G = n_min > 16 ? (unsigned)(n_min / 16) : 1u;
+        dim3 grd(ceil_div(m, 16) * ceil_div(n, 16), (unsigned)batch);
+        constexpr int KT = W >= 16 ? 4 : 8;
+        k_mp_block<W, KT, CLOSE><<<grd, 256, 0, s>>>(m, l, n, A, B, C, G, status);
+    }
+}
+
 template <int W>
 static int mp_gemm_w(int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const uint32_t> A,
                      View<const uint32_t> B, View<uint32_t> C, int n_min, cudaStream_t s) {
     unsigned* status = device_status_ptr();
     if (!status) return MPGEMM_ECUDA;
     ProfScope ps(s);
-    if (algo == MPGEMM_SIMPLE) {
-        dim3 blk(16, 16);
-        dim3 grd(ceil_div(n, 16), ceil_div(m, 16), (unsigned)batch);
-        k_mp_simple<W><<<grd, blk, 0, s>>>(m, l, n, A, B, C, status);
-    } else if (mp_team_leaf(W, m, n, batch, s)) {
+    if (algo != MPGEMM_SIMPLE && mp_team_leaf(W, m, n, batch, s)) {
         const int rc = mp_gemm_team(W, m, l, n, batch, A, B, C, n_min, status, s);
         if (rc != MPGEMM_OK) return rc;
+    } else if constexpr (W >= 2 && W <= 16) {
+        if (t_close_operands) launch_mp<W, true>(algo, m, l, n, batch, A, B, C, n_min, status, s);
+        else launch_mp<W, false>(algo, m, l, n, batch, A, B, C, n_min, status, s);
     } else {
-        unsigned G = n_min > 16 ? (unsigned)(n_min / 16) : 1u;
-        dim3 grd(ceil_div(m, 16) * ceil_div(n, 16), (unsigned)batch);
-        constexpr int KT = W >= 16 ? 4 : 8;
-        k_mp_block<W, KT><<<grd, 256, 0, s>>>(m, l, n, A, B, C, G, status);
+        launch_mp<W, false>(algo, m, l, n, batch, A, B, C, n_min, status, s);
     }
     return check_launch();
 }

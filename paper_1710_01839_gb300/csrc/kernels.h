@@ -14,6 +14,20 @@ namespace mpg {
 int ddqd_gemm(int kind, int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const double> A,
               View<const double> B, View<double> C, int n_min, cudaStream_t s);
 
+// While alive, multi-limb GEMMs issued from this host thread expect
+// operands of similar magnitude (the integer pipe's images of DD / QD
+// numbers) and use the add's alignment shortcut for them.
+class CloseOperandsScope {
+   public:
+    CloseOperandsScope();
+    ~CloseOperandsScope();
+    CloseOperandsScope(const CloseOperandsScope&) = delete;
+    CloseOperandsScope& operator=(const CloseOperandsScope&) = delete;
+
+   private:
+    bool prev_;
+};
+
 // Multi-limb simple / block, w limbs per mantissa.
 int mp_gemm(int w, int algo, int64_t m, int64_t l, int64_t n, int64_t batch, View<const uint32_t> A,
             View<const uint32_t> B, View<uint32_t> C, int n_min, cudaStream_t s);

@@ -328,7 +328,12 @@ __device__ __forceinline__ void mp_mul(const MPV<W>& x, const MPV<W>& y, MPV<W>&
 // quarter of x's ulp and the frame below rounds to x, which is RN(x + y) for
 // every larger d as well), y is aligned by the barrel shifter, and the sum
 // and the difference are one carry chain X + (Y xor mask) + carry-in.
-template <int W>
+// CLOSE: the operands are expected to be of similar magnitude (multi-limb
+// images of DD / QD numbers); then when every active thread of the warp has
+// d < 32 (a warp-wide decision, so no divergence) a plain funnel shift
+// aligns y.  With exponents spread over a wide range the vote seldom
+// succeeds and costs more than it saves, so the default leaves it out.
+template <int W, bool CLOSE = false>
 __device__ __forceinline__ void mp_add(const MPV<W>& a, const MPV<W>& b, MPV<W>& r, unsigned& status) {
     constexpr int p = 32 * W;
     constexpr int N = W + 2;   // [guard, M (W limbs), carry]
@@ -357,7 +362,18 @@ MP_UNROLL
     X[N - 1] = 0u;
     Y[N - 1] = 0u;
     uint32_t sticky = 0u;
-    shr_sticky<N, W>(Y, d, sticky);   // d <= p + 2: at most W limbs move
+    if constexpr (CLOSE) {
+        if (__all_sync(__activemask(), d < 32)) {
+            // no limb moves, and the guard limb keeps every shifted-out bit
+MP_UNROLL
+            for (int i = 0; i < N - 1; i++) Y[i] = __funnelshift_r(Y[i], Y[i + 1], d);
+            Y[N - 1] >>= d;
+        } else {
+            shr_sticky<N, W>(Y, d, sticky);   // d <= p + 2: at most W limbs move
+        }
+    } else {
+        shr_sticky<N, W>(Y, d, sticky);   // d <= p + 2: at most W limbs move
+    }
     const bool stk = sticky != 0u;
     // sum, or X - Y - stk (the dropped part of y then leaves a positive
     // remainder below S's last bit, kept as sticky) as X + ~Y + 1 - stk

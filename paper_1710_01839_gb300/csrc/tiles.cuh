@@ -172,12 +172,12 @@ MP_UNROLL
     for (int i = 0; i < W; i++) V.store(p + (2 + i) * V.ps, v.m[i]);
 }
 
-template <int W>
+template <int W, bool CLOSE = false>
 __device__ __forceinline__ void mp_mac(MPV<W>& c, const MPV<W>& a, const MPV<W>& b, unsigned& st) {
     MPV<W> t;
     mp_mul<W>(a, b, t, st);
     MPV<W> s;
-    mp_add<W>(c, t, s, st);
+    mp_add<W, CLOSE>(c, t, s, st);
     c = s;
 }
 
@@ -202,8 +202,9 @@ __host__ __device__ constexpr int mp_tile_words() {
 // One 16 x 16 block of C (one output per thread, 256 threads) with A rows and
 // B columns staged KT elements deep through shared memory `sm`
 // (mp_tile_words<W, KT>() words, 16-byte aligned) as [k][row][word];
-// device-side flags are ORed into `st`.
-template <int W, int KT>
+// device-side flags are ORed into `st`.  CLOSE: mp_add's alignment shortcut
+// for operands of similar magnitude.
+template <int W, int KT, bool CLOSE = false>
 __device__ __forceinline__ void mp_block_tile(int64_t m, int64_t l, int64_t n, const View<const uint32_t>& A,
                                               const View<const uint32_t>& B, const View<uint32_t>& C, int64_t z,
                                               int64_t i0, int64_t j0, uint32_t* sm, unsigned& st) {
@@ -315,7 +316,7 @@ MP_UNROLL
                 mp_mul<W>(a, b, t, st);
             }
             MPV<W> s;
-            mp_add<W>(c, t, s, st);
+            mp_add<W, CLOSE>(c, t, s, st);
             c = s;
         }
         __syncthreads();

@@ -134,6 +134,7 @@ static int via_mp_entry(int T, int64_t m, int64_t l, int64_t n, const double* A,
     rc = convert(0, T, w, m * l, A, Am, nullptr, s);
     if (!rc) rc = convert(0, T, w, l * n, B, Bm, nullptr, s);
     if (!rc) {
+        CloseOperandsScope close;   // images of DD / QD numbers: operands of similar magnitude
         const size_t eb = sizeof(uint32_t) * (size_t)(2 + w);
         View<const uint32_t> a = bounded(planes_view<const uint32_t>(Am, m, l), Am, eb * m * l);
         View<const uint32_t> b = bounded(planes_view<const uint32_t>(Bm, l, n), Bm, eb * l * n);
