@@ -517,10 +517,13 @@ int mpgemm_fault_fired(void);
    bit for every pair of doubles.  Device pointers (out: 3 count doubles);
    asynchronous on stream; MPGEMM_EINVAL for bad arguments. */
 int mpgemm_selftest_two_sum(int64_t count, const double* a, const double* b, double* out, void* stream);
-/* Self-test of the DD kernel's product error term: out[i] = RN(a[i] b[i]),
-   out[count + i] = its rounding error as the kernel computes it (the
-   integer-pipe form) and out[2 count + i] = fma(a[i], b[i], -out[i]).  The
-   two error planes are equal bit for bit for every pair of doubles. */
+/* Self-test of the DD kernel's TwoProd (the product and its rounding error
+   on the integer pipe): out[i] = RN(a[i] b[i]) and out[count + i] = its
+   error as the kernel computes them, out[2 count + i] = fma(a[i], b[i],
+   -p) with p the FP64 product.  out[i] equals the IEEE product (NaN for NaN)
+   and the two error planes are equal bit for bit for every pair of doubles.
+   Device pointers (out: 3 count doubles); asynchronous on stream;
+   MPGEMM_EINVAL for bad arguments. */
 int mpgemm_selftest_two_prod(int64_t count, const double* a, const double* b, double* out, void* stream);
 
 /* ---------------------------------------------------------------------------

@@ -4,12 +4,13 @@
 //
 // The multiply-accumulate of the GEMM (Eq 1's c <- c + a_ik b_kj) uses a
 // deferred-renormalisation accumulator instead of a full DD add per step:
-//   DD:  state (s, t).  p = RN(ah bh) and its exact error e from one FMA,
-//        the two cross products accumulated into t with two more FMAs, then
+//   DD:  state (s, t).  p = RN(ah bh) and its exact error e (TwoProd),
+//        the two cross products accumulated into t with two FMAs, then
 //        (s, r) = TwoSum(s, p) and t <- t + (e + r).  Every DD_RENORM steps
-//        (s, t) = TwoSum(s, t).  6 FP64 operations per step: the error
-//        terms of the product and of the exponent-ordered TwoSum below run
-//        on the integer pipe (the library DD add + multiply pair costs 27).
+//        (s, t) = TwoSum(s, t).  5 FP64 operations per step: TwoProd (the
+//        product and its error) and the error term of the exponent-ordered
+//        TwoSum run on the integer pipe (the library DD add + multiply pair
+//        costs 27).
 //        Worst-case error after l steps: about (DD_RENORM + 3) l u^2 sum|a||b|
 //        plus O(u^2) per product, inside the required 16 l u^2 |A||B|
 //        (= 4 l 2^-104 |A||B|) for DD_RENORM = 8.
@@ -75,31 +76,44 @@ __device__ __forceinline__ double fast_two_sum_err(double x, double y, double s)
         (long long)((ri < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)F << 52) | (mant & MM)));
 }
 
-// The rounding error e = a b - p of p = RN(a b), exactly (what
-// fma(a, b, -p) returns), computed on the integer pipe: with normal a, b, p
-// the mantissa product Ma Mb (106 bits) and p's mantissa scaled to the same
-// unit (Mp 2^k, k = 52 or 53) differ by at most half an ulp of p, 2^52
-// units, so the difference is the low 64 bits of Ma Mb minus Mp 2^k modulo
-// 2^64, and e is assembled from it without rounding.  Zero, subnormal,
-// infinite or NaN operands or product and a subnormal e take the FMA.
-// Bit-identical to fma(a, b, -p) (checked by mpgemm_selftest_two_prod).
-__device__ __forceinline__ double two_prod_err(double a, double b, double p) {
+// TwoProd: p = RN(a b) and e = a b - p exactly (what fma(a, b, -p)
+// returns), both on the integer pipe from one 106-bit mantissa product
+// P = Ma Mb = hi 2^64 + lo, 2^104 <= P < 2^106.  With sh = 52 or 53 (P below
+// or above 2^105), p's mantissa is q = RNE(P / 2^sh), 2^52 <= q <= 2^53 (q =
+// 2^53 carries into the exponent field when the fields are packed as
+// (E - 1) 2^52 + q), and e = P - q 2^sh, |e| <= 2^(sh-1), is the difference
+// of the low 64 bits taken modulo 2^64; e is representable and its double
+// is assembled from that integer without rounding.  Zero, subnormal,
+// infinite or NaN operands, a product outside the normal range and a
+// subnormal e take __dmul_rn and the FMA.  Bit-identical to the FP64 pair (checked against the host's IEEE product
+// and the device FMA by mpgemm_selftest_two_prod).
+__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) {
     const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
     const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
-    const unsigned long long bp = (unsigned long long)__double_as_longlong(p);
-    const int Ea = (int)((ba >> 52) & 0x7ff), Eb = (int)((bb >> 52) & 0x7ff), Ep = (int)((bp >> 52) & 0x7ff);
-    if (Ea == 0 || Eb == 0 || Ep == 0 || Ea == 0x7ff || Eb == 0x7ff || Ep == 0x7ff) return __fma_rn(a, b, -p);
+    const int Ea = (int)((ba >> 52) & 0x7ff), Eb = (int)((bb >> 52) & 0x7ff);
     constexpr unsigned long long MM = (1ull << 52) - 1ull, H = 1ull << 52;
-    const unsigned long long Ma = (ba & MM) | H, Mb = (bb & MM) | H, Mp = (bp & MM) | H;
-    const int k = Ep - Ea - Eb + 1075;                     // 52, or 53 when p carried into the next binade
-    const long long eu = (long long)(Ma * Mb - (Mp << k)); // (|a b| - |p|) / 2^(Ea + Eb - 2150)
-    if (eu == 0) return 0.0;
+    const unsigned long long Ma = (ba & MM) | H, Mb = (bb & MM) | H;
+    const unsigned long long lo = Ma * Mb, hi = __umul64hi(Ma, Mb);
+    const int top = (int)(hi >> 41);                       // 1 when P >= 2^105
+    const int sh = 52 + top;
+    unsigned long long q = (hi << (12 - top)) | (lo >> sh);
+    const unsigned long long rem = lo & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+    const int Ep = Ea + Eb - 1023 + top;                  // p's field before a rounding carry
+    const long long eu = (long long)(lo - (q << sh));     // e / 2^(Ea + Eb - 2150)
     const unsigned long long m = eu < 0 ? 0ull - (unsigned long long)eu : (unsigned long long)eu;
     const int lz = __clzll((long long)m);                  // >= 11: |eu| <= 2^52
-    const int F = Ea + Eb - 1064 - lz;                      // exponent field of e
-    if (F <= 0) return __fma_rn(a, b, -p);
-    const unsigned long long sgn = ((ba ^ bb) >> 63) ^ (eu < 0 ? 1ull : 0ull);
-    return __longlong_as_double((long long)((sgn << 63) | ((unsigned long long)F << 52) | ((m << (lz - 11)) & MM)));
+    const int F = Ea + Eb - 1064 - lz;                     // e's field
+    if (Ea == 0 || Eb == 0 || Ea == 0x7ff || Eb == 0x7ff || Ep < 1 || Ep > 0x7fd || (eu != 0 && F <= 0)) {
+        p = __dmul_rn(a, b);
+        e = __fma_rn(a, b, -p);
+        return;
+    }
+    const unsigned long long sgn = (ba ^ bb) & (1ull << 63);
+    p = __longlong_as_double((long long)(sgn | (((unsigned long long)(Ep - 1) << 52) + q)));
+    e = eu == 0 ? 0.0
+                : __longlong_as_double((long long)((sgn ^ (eu < 0 ? (1ull << 63) : 0ull)) |
+                                                   ((unsigned long long)F << 52) | ((m << (lz - 11)) & MM)));
 }
 
 // TwoSum: s = RN(a + b), e = a + b - s exactly, for any a, b.  Computed as
@@ -148,8 +162,8 @@ __device__ __forceinline__ void dd_zero(DDAcc& c) {
 }
 
 __device__ __forceinline__ void dd_mac(DDAcc& c, double ah, double al, double bh, double bl) {
-    double p = __dmul_rn(ah, bh);
-    double e = two_prod_err(ah, bh, p);   // exact error of p, on the integer pipe
+    double p, e;
+    two_prod(ah, bh, p, e);             // p = RN(ah bh) and its exact error, on the integer pipe
     double t = __fma_rn(ah, bl, c.t);   // cross products straight into the low part
     t = __fma_rn(al, bh, t);
     double s, r;

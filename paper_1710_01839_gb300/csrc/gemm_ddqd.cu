@@ -112,15 +112,16 @@ __global__ void k_selftest_two_sum(int64_t count, const double* a, const double*
     out[2 * count + i] = e2;
 }
 
-// The product error term on the integer pipe against fma(a, b, -p)
-// (mpgemm_selftest_two_prod).
+// The DD MAC's product and its error on the integer pipe, with the FP64
+// error fma(a, b, -RN(a b)) beside them (mpgemm_selftest_two_prod).
 __global__ void k_selftest_two_prod(int64_t count, const double* a, const double* b, double* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    const double p = __dmul_rn(a[i], b[i]);
+    double p, e;
+    two_prod(a[i], b[i], p, e);
     out[i] = p;
-    out[count + i] = two_prod_err(a[i], b[i], p);
-    out[2 * count + i] = __fma_rn(a[i], b[i], -p);
+    out[count + i] = e;
+    out[2 * count + i] = __fma_rn(a[i], b[i], -__dmul_rn(a[i], b[i]));
 }
 
 }  // namespace mpg

@@ -4,7 +4,11 @@ doubles (mpgemm_selftest_two_sum runs both on the device).  Pairs: random
 doubles over the whole exponent range, and crafted ones (equal exponents,
 cancellation, powers of two, exponent gaps around 54, zeros of both signs,
 subnormals, infinities, NaN, overflow), plus the accumulator / product
-pairs of a DD multiply-accumulate."""
+pairs of a DD multiply-accumulate.  The DD MAC's TwoProd (product and
+error, both on the integer pipe; mpgemm_selftest_two_prod) must give the
+host's IEEE product (numpy's float64 multiply) and the device FMA's error
+bit for bit on the same kinds of pairs, plus products that round up into
+the next binade, ties and products at the edges of the normal range."""
 
 import numpy as np
 import pytest
@@ -100,19 +104,66 @@ def _run_prod(a, b):
     return o[0], o[1], o[2]
 
 
+def _check_prod(a, b):
+    """p == the host's IEEE product (both NaN where it is NaN) and the
+    integer-pipe error == fma(a, b, -p), bit for bit."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    p, e_int, e_fma = _run_prod(a, b)
+    with np.errstate(all="ignore"):
+        want = a * b
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(p), nan)
+    assert np.array_equal(_bits(p[~nan]), _bits(want[~nan]))
+    assert np.array_equal(_bits(e_int), _bits(e_fma))
+    return p, e_int
+
+
 def test_product_error_random_pairs():
     # the DD kernel's product error term on the integer pipe == fma(a, b, -p)
     rng = np.random.default_rng(77)
     n = 1 << 20
     bits = rng.integers(0, 2**63, size=(2, n), dtype=np.uint64) | (rng.integers(0, 2, size=(2, n), dtype=np.uint64) << np.uint64(63))
     a, b = bits[0].view(np.float64), bits[1].view(np.float64)
-    p, e_int, e_fma = _run_prod(a, b)
-    assert np.array_equal(_bits(e_int), _bits(e_fma))
+    _check_prod(a, b)
     # products near 1 (all carries and roundings of the mantissa product)
     a = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n) * np.ldexp(1.0, rng.integers(-500, 500, n))
     b = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n) * np.ldexp(1.0, rng.integers(-500, 500, n))
-    p, e_int, e_fma = _run_prod(a, b)
-    assert np.array_equal(_bits(e_int), _bits(e_fma))
+    _check_prod(a, b)
+    # products at the edges of the normal range (overflow, underflow into
+    # subnormals and below, subnormal errors)
+    a = rng.uniform(1, 2, n) * np.ldexp(1.0, rng.integers(-1022, 1024, n))
+    b = rng.uniform(1, 2, n) * np.ldexp(1.0, rng.integers(-1022, 1024, n))
+    near = np.abs(np.log2(np.abs(a)) + np.log2(np.abs(b)))
+    assert (near > 1000).sum() > 1000
+    _check_prod(a, b)
+
+
+def test_product_roundings():
+    # mantissa products one unit either side of a binade (x y just below
+    # 2^105 or 2^106: many round up into the next binade, a carry into the
+    # exponent field) and exact ties at both product widths, rounding up and
+    # down to even
+    rng = np.random.default_rng(78)
+    xs, ys = [], []
+    for _ in range(20000):
+        x = int(rng.integers(1 << 52, 1 << 53))
+        for top in (106, 105):
+            y = ((1 << top) - 1) // x
+            if (1 << 52) <= y < (1 << 53):
+                xs.append(x); ys.append(y)
+    ties = [(3 << 51, (1 << 52) + k) for k in range(1, 400, 2)]                  # P < 2^105
+    ties += [(7 << 50, (5 << 50) + 4 + 8 * j) for j in range(200)]               # P >= 2^105
+    for x, y in ties:
+        P = x * y
+        sh = 53 if P >> 105 else 52
+        assert P % (1 << sh) == 1 << (sh - 1)                                       # an exact tie
+    xs += [x for x, _ in ties]
+    ys += [y for _, y in ties]
+    a = np.array([np.ldexp(float(v), -52) for v in xs]) * rng.choice([-1.0, 1.0], len(xs))
+    b = np.array([np.ldexp(float(v), -52) for v in ys]) * rng.choice([-1.0, 1.0], len(ys))
+    p, e = _check_prod(a, b)
+    assert ((np.abs(p) == 2.0) | (np.abs(p) == 4.0)).sum() > 100   # roundings into the next binade
 
 
 def test_product_error_crafted_pairs():
@@ -124,5 +175,4 @@ def test_product_error_crafted_pairs():
             np.ldexp(1.0, 512), np.inf, np.nan, 1.0 / 3.0, np.ldexp(1.0 - u, 1), 1e-300, 1e300]
     vals = np.array(vals + [-v for v in vals])
     a, b = np.meshgrid(vals, vals, indexing="ij")
-    p, e_int, e_fma = _run_prod(a.ravel(), b.ravel())
-    assert np.array_equal(_bits(e_int), _bits(e_fma))
+    _check_prod(a.ravel(), b.ravel())
