@@ -45,8 +45,9 @@ METRIC = "DD/QD GEMM GFLOP/s (2mnl/t) & roofline %; Ozaki vs plain DD at ≤2^-1
 # term except in the QD MAC's nine order-2 TwoSums: 1 FP64 operation per
 # TwoSum, 3 for those nine; the DD MAC's product and its error run there too):
 #   DD: 2 DFMA + TwoSum (1) + 2 DADD = 5, plus a 1-op TwoSum every 8 steps
-#   QD: 62 per step plus a 5-op renormalisation every 4 steps
-FP64_OPS_PER_MAC = {"dd": 5.0 + 1.0 / 8.0, "qd": 62.0 + 5.0 / 4.0}
+#   QD: 50 per step (its six order-0..2 products through TwoProd on the
+#       integer pipe) plus a 5-op renormalisation every 4 steps
+FP64_OPS_PER_MAC = {"dd": 5.0 + 1.0 / 8.0, "qd": 50.0 + 5.0 / 4.0}
 # FP64 pipe: 2 operations / clock / SM (measured 1.91 DFMA/clk/SM at 2.07 GHz by
 # a dependent-chain-free DFMA loop) x 152 SMs x 2070 MHz maximum SM clock.
 FP64_PEAK_GOPS = 2 * 152 * 2.070

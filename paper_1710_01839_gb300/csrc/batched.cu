@@ -97,14 +97,14 @@ __global__ void __launch_bounds__(256) k_batched(const DevDesc* __restrict__ des
 }
 
 // Relative cost of one multiply-accumulate, for ordering work items only:
-// time per MAC of each tile kind on GB300 in units where a DD MAC is 7.1
-// (about its FP64 operations: DD 6.1 - 7.1 and QD 63.25 at 82 - 89 % of the FP64 pipe;
-// the 128- and 256-bit multi-limb MACs issue 265 and 417 instructions at
-// about 44 % of the issue rate).
+// time per MAC of each tile kind on GB300 in units where a 128-bit
+// multi-limb MAC is 8.3 (DD 5.1 and QD 51.25 FP64 operations at 81 - 88 % of
+// the FP64 pipe; the 128- and 256-bit multi-limb MACs issue 232 and 377
+// instructions at about 43 % of the issue rate).
 static double mac_cost(int tk) {
     switch (tk) {
-        case T_DD16: case T_DD32: return 7.1;
-        case T_QD16: case T_QD32: return 68.5;
+        case T_DD16: case T_DD32: return 6.4;
+        case T_QD16: case T_QD32: return 63.5;
         case T_MP128: return 8.3;
         default: return 13.5;
     }

@@ -19,9 +19,9 @@
 //        every term of order <= 2 enters its level through TwoSum, its
 //        rounding error going one level down; order-3 terms are added
 //        plainly into s3 (their errors are order 4).  Every QD_RENORM steps
-//        the levels are renormalised.  63.25 FP64 operations per step (the
-//        TwoSum errors of orders 0 and 1 and of the renormalisation on the
-//        integer pipe).  Worst case about
+//        the levels are renormalised.  51.25 FP64 operations per step (the
+//        six products of orders 0-2 through TwoProd, and the TwoSum errors of
+//        orders 0 and 1 and of the renormalisation, on the integer pipe).  Worst case about
 //        (10 QD_RENORM + 10) l u^4 sum|a||b|, inside 4 l 2^-208 = 64 l u^4.
 #pragma once
 
@@ -76,44 +76,73 @@ __device__ __forceinline__ double fast_two_sum_err(double x, double y, double s)
         (long long)((ri < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)F << 52) | (mant & MM)));
 }
 
-// TwoProd: p = RN(a b) and e = a b - p exactly (what fma(a, b, -p)
-// returns), both on the integer pipe from one 106-bit mantissa product
-// P = Ma Mb = hi 2^64 + lo, 2^104 <= P < 2^106.  With sh = 52 or 53 (P below
-// or above 2^105), p's mantissa is q = RNE(P / 2^sh), 2^52 <= q <= 2^53 (q =
-// 2^53 carries into the exponent field when the fields are packed as
-// (E - 1) 2^52 + q), and e = P - q 2^sh, |e| <= 2^(sh-1), is the difference
-// of the low 64 bits taken modulo 2^64; e is representable and its double
-// is assembled from that integer without rounding.  Zero, subnormal,
-// infinite or NaN operands, a product outside the normal range and a
-// subnormal e take __dmul_rn and the FMA.  Bit-identical to the FP64 pair (checked against the host's IEEE product
-// and the device FMA by mpgemm_selftest_two_prod).
-__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) {
-    const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
-    const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
-    const int Ea = (int)((ba >> 52) & 0x7ff), Eb = (int)((bb >> 52) & 0x7ff);
-    constexpr unsigned long long MM = (1ull << 52) - 1ull, H = 1ull << 52;
-    const unsigned long long Ma = (ba & MM) | H, Mb = (bb & MM) | H;
-    const unsigned long long lo = Ma * Mb, hi = __umul64hi(Ma, Mb);
-    const int top = (int)(hi >> 41);                       // 1 when P >= 2^105
-    const int sh = 52 + top;
-    unsigned long long q = (hi << (12 - top)) | (lo >> sh);
-    const unsigned long long rem = lo & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
-    const int Ep = Ea + Eb - 1023 + top;                  // p's field before a rounding carry
-    const long long eu = (long long)(lo - (q << sh));     // e / 2^(Ea + Eb - 2150)
+// TwoProd on the integer pipe: p = RN(a b) and the exact error e = a b - p
+// as the signed integer eu times 2^ge, from one 106-bit mantissa product
+// P = Ma Mb (four 32 x 32-bit products of the 21- and 32-bit halves).  P is
+// shifted left by sh = 0 or 1 into [2^105, 2^106); p's mantissa is
+// q = RNE(P / 2^53) (guard bit 52, sticky bits 0-51, ties to even),
+// 2^52 <= q <= 2^53 (q = 2^53 carries into the exponent field when the
+// fields are packed as (E - 1) 2^52 + q), and e = P - q 2^53 = rem - up 2^53
+// (rem = P mod 2^53, up = the rounding increment), |e| <= 2^52 units of
+// 2^(Ea + Eb - 2150 - sh).  Returns false (p and e unspecified) for zero,
+// subnormal, infinite or NaN operands and for exponent fields summing
+// outside [1129, 3067] (products below 2^-917, or that may reach 2^1023):
+// there the caller takes the FP64 operations.
+__device__ __forceinline__ bool two_prod_i(double a, double b, double& p, long long& eu, int& ge) {
+    const unsigned ah = (unsigned)__double2hiint(a), al = (unsigned)__double2loint(a);
+    const unsigned bh = (unsigned)__double2hiint(b), bl = (unsigned)__double2loint(b);
+    const int Ea = (int)((ah >> 20) & 0x7ffu), Eb = (int)((bh >> 20) & 0x7ffu);
+    const bool ok = (unsigned)(Ea - 1) < 0x7feu && (unsigned)(Eb - 1) < 0x7feu && (unsigned)(Ea + Eb - 1129) <= 1938u;
+    const unsigned a1 = (ah & 0xfffffu) | 0x100000u, b1 = (bh & 0xfffffu) | 0x100000u;
+    const unsigned long long p00 = (unsigned long long)al * bl;
+    const unsigned long long mid = (unsigned long long)al * b1 + (unsigned long long)a1 * bl;   // < 2^54
+    const unsigned long long t = (p00 >> 32) + (mid & 0xffffffffull);
+    const unsigned long long u = (unsigned long long)a1 * b1 + (mid >> 32) + (t >> 32);        // P / 2^64
+    unsigned w0 = (unsigned)p00, w1 = (unsigned)t, w2 = (unsigned)u, w3 = (unsigned)(u >> 32);
+    const int top = (int)(w3 >> 9);                          // bit 105 of P
+    const int sh = 1 - top;
+    w3 = __funnelshift_l(w2, w3, sh);
+    w2 = __funnelshift_l(w1, w2, sh);
+    w1 = __funnelshift_l(w0, w1, sh);
+    w0 <<= sh;
+    const unsigned qlo = __funnelshift_r(w1, w2, 21), qhi = __funnelshift_r(w2, w3, 21);
+    const unsigned up = (w1 >> 20) & (((w1 & 0xfffffu) | w0) != 0u ? 1u : qlo) & 1u;
+    const unsigned long long q = (((unsigned long long)qhi << 32) | qlo) + up;
+    const int Ep = Ea + Eb - 1023 + top;                     // p's field before a rounding carry
+    const unsigned sgn = (ah ^ bh) & 0x80000000u;
+    p = __hiloint2double((int)(sgn | (((unsigned)(Ep - 1) << 20) + (unsigned)(q >> 32))), (int)(unsigned)q);
+    const long long v = (long long)((((unsigned long long)(w1 & 0x1fffffu) << 32) | w0) - ((unsigned long long)up << 53));
+    eu = sgn ? -v : v;
+    ge = Ea + Eb - 2150 - sh;
+    return ok;
+}
+
+// The double of the exact integer value eu 2^ge with |eu| <= 2^53 (no
+// rounding needed); false for a subnormal result.
+__device__ __forceinline__ bool exact_to_double(long long eu, int ge, double& e) {
+    if (eu == 0) {
+        e = 0.0;
+        return true;
+    }
     const unsigned long long m = eu < 0 ? 0ull - (unsigned long long)eu : (unsigned long long)eu;
-    const int lz = __clzll((long long)m);                  // >= 11: |eu| <= 2^52
-    const int F = Ea + Eb - 1064 - lz;                     // e's field
-    if (Ea == 0 || Eb == 0 || Ea == 0x7ff || Eb == 0x7ff || Ep < 1 || Ep > 0x7fd || (eu != 0 && F <= 0)) {
+    const int lz = __clzll((long long)m);                    // >= 10
+    const int F = 63 - lz + ge + 1023;
+    const unsigned long long mant = m << (lz - 11 >= 0 ? lz - 11 : 0) >> (lz - 11 >= 0 ? 0 : 11 - lz);
+    e = __longlong_as_double((long long)((eu < 0 ? (1ull << 63) : 0ull) + ((unsigned long long)(F - 1) << 52) + mant));
+    return F > 0;
+}
+
+// TwoProd: p = RN(a b) and e = a b - p exactly, both on the integer pipe
+// (two_prod_i), the FP64 pair __dmul_rn / fma(a, b, -p) outside its range
+// and for a subnormal e.  Bit-identical to the FP64 pair (checked against
+// the host's IEEE product and the device FMA by mpgemm_selftest_two_prod).
+__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) {
+    long long eu;
+    int ge;
+    if (!(two_prod_i(a, b, p, eu, ge) && exact_to_double(eu, ge, e))) {
         p = __dmul_rn(a, b);
         e = __fma_rn(a, b, -p);
-        return;
     }
-    const unsigned long long sgn = (ba ^ bb) & (1ull << 63);
-    p = __longlong_as_double((long long)(sgn | (((unsigned long long)(Ep - 1) << 52) + q)));
-    e = eu == 0 ? 0.0
-                : __longlong_as_double((long long)((sgn ^ (eu < 0 ? (1ull << 63) : 0ull)) |
-                                                   ((unsigned long long)F << 52) | ((m << (lz - 11)) & MM)));
 }
 
 // TwoSum: s = RN(a + b), e = a + b - s exactly, for any a, b.  Computed as
@@ -228,8 +257,8 @@ __device__ __forceinline__ void qd_finish(QDAcc& c) {
 __device__ __forceinline__ void qd_mac(QDAcc& c, const double a[4], const double b[4]) {
     double p, e, s, r;
     // order 0
-    p = __dmul_rn(a[0], b[0]);
-    double e00 = __fma_rn(a[0], b[0], -p);
+    double e00;
+    two_prod(a[0], b[0], p, e00);
     two_sum(c.s0, p, s, r);
     c.s0 = s;
     // order 1: r, e00, a0 b1, a1 b0 (into s1; errors -> order 2 terms)
@@ -238,12 +267,12 @@ __device__ __forceinline__ void qd_mac(QDAcc& c, const double a[4], const double
     c.s1 = s;
     two_sum(c.s1, e00, s, l2b);
     c.s1 = s;
-    p = __dmul_rn(a[0], b[1]);
-    double e01 = __fma_rn(a[0], b[1], -p);
+    double e01;
+    two_prod(a[0], b[1], p, e01);
     two_sum(c.s1, p, s, l2c);
     c.s1 = s;
-    p = __dmul_rn(a[1], b[0]);
-    double e10 = __fma_rn(a[1], b[0], -p);
+    double e10;
+    two_prod(a[1], b[0], p, e10);
     two_sum(c.s1, p, s, l2d);
     c.s1 = s;
     // order 2: l2a..l2d, e01, e10, a0 b2, a1 b1, a2 b0 (into s2; errors -> s3).
@@ -257,14 +286,11 @@ __device__ __forceinline__ void qd_mac(QDAcc& c, const double a[4], const double
     two_sum_fp64(c.s2, l2d, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
     two_sum_fp64(c.s2, e01, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
     two_sum_fp64(c.s2, e10, s, r); c.s2 = s; t3 = __dadd_rn(t3, r);
-    p = __dmul_rn(a[0], b[2]);
-    e = __fma_rn(a[0], b[2], -p);
+    two_prod(a[0], b[2], p, e);
     two_sum_fp64(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
-    p = __dmul_rn(a[1], b[1]);
-    e = __fma_rn(a[1], b[1], -p);
+    two_prod(a[1], b[1], p, e);
     two_sum_fp64(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
-    p = __dmul_rn(a[2], b[0]);
-    e = __fma_rn(a[2], b[0], -p);
+    two_prod(a[2], b[0], p, e);
     two_sum_fp64(c.s2, p, s, r); c.s2 = s; t3 = __dadd_rn(t3, __dadd_rn(r, e));
     // order 3: a0 b3 + a1 b2 + a2 b1 + a3 b0, plainly
     double q = __dmul_rn(a[3], b[0]);

@@ -4,12 +4,12 @@
 //
 // Why: on GB300 the FP64 pipe delivers 2 operations per clock per SM
 // (629 G op/s), while the integer pipes issue 128 thread-instructions per
-// clock per SM.  A DD multiply-accumulate costs 6.1 FP64 operations (its
-// error terms already on the integer pipe) and a QD one 63.25; a 128-bit
-// multi-limb one about 265 integer instructions and a 256-bit one about 417,
-// so the multi-limb path runs DD about 1.3x and QD about 7.6x faster, with
-// every operation rounded to p >= 128 / 256 bits (far inside the DD and QD
-// error bounds).
+// clock per SM.  A DD multiply-accumulate costs 5.1 FP64 operations (its
+// product and error terms already on the integer pipe) and a QD one 51.25;
+// a 128-bit multi-limb one about 232 integer instructions and a 256-bit one
+// about 377, so the multi-limb path runs DD about 1.15x and QD about 6.5x
+// faster, with every operation rounded to p >= 128 / 256 bits (far inside
+// the DD and QD error bounds).
 //
 // Conversions (the definitions the oracle restates):
 //   to p bits:   c = +0; for t = 0..T-1: c = RN_p(c + x_t), x_t taken exactly

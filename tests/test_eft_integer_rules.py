@@ -6,10 +6,14 @@ e(x) - e(y) <= 54, s not below y's binade): x, y, s are integer multiples
 of ulp(y) and |x + y - s| <= ulp(s)/2 < 2^55 ulp(y), so (x + y - s)/ulp(y)
 equals the sum of the three scaled mantissas taken modulo 2^64.
 
-Product error (a, b, p = RN(a b) normal): the mantissa product Ma Mb and p's
-mantissa scaled to the same unit (Mp 2^k, k = 52 or 53) differ by at most
-2^52 units, so their difference is the low 64 bits of Ma Mb minus Mp 2^k
-modulo 2^64.
+TwoProd (a, b normal, exponent fields summing to 1129..3067, i.e. products
+from 2^-917 up to below 2^1023): P = Ma Mb from four
+32 x 32-bit products of the mantissas' 21- and 32-bit halves, shifted left
+by 0 or 1 into [2^105, 2^106); p's mantissa is P / 2^53 rounded to nearest
+even from the guard bit 52 and the sticky bits 0-51 (a carry to 2^53 goes
+into the exponent field by packing (E - 1) 2^52 + q), and e = P - q 2^53 =
+(P mod 2^53) - up 2^53, |e| <= 2^52 units.  The model below follows the
+kernel's 32-bit words and funnel shifts step by step.
 
 Each function returns None where the kernels take the FP64 formula instead.
 """
@@ -76,25 +80,62 @@ def two_sum_err_int(x, y, s):
     return assemble(ri, Ey)
 
 
-def two_prod_err_int(a, b, p):
-    ba, bb, bp = bits(a), bits(b), bits(p)
-    Ea, Eb, Ep = (ba >> 52) & 0x7FF, (bb >> 52) & 0x7FF, (bp >> 52) & 0x7FF
-    if 0 in (Ea, Eb, Ep) or 0x7FF in (Ea, Eb, Ep):
-        return None
-    Ma, Mb, Mp = (ba & MM) | (1 << 52), (bb & MM) | (1 << 52), (bp & MM) | (1 << 52)
-    k = Ep - Ea - Eb + 1075
-    assert k in (52, 53)
-    eu = to_signed(Ma * Mb - (Mp << k))
-    assert abs(eu) <= 1 << 52
+M32 = (1 << 32) - 1
+
+
+def _funnel_l(lo, hi, n):
+    return ((((hi << 32) | lo) << n) >> 32) & M32
+
+
+def _funnel_r(lo, hi, n):
+    return (((hi << 32) | lo) >> n) & M32
+
+
+def exact_to_double(eu, ge):
+    """The double eu 2^ge (|eu| <= 2^53, no rounding), None if subnormal."""
     if eu == 0:
         return 0.0
     m = abs(eu)
     lz = 64 - m.bit_length()
-    F = Ea + Eb - 1064 - lz
+    F = 63 - lz + ge + 1023
     if F <= 0:
         return None
-    sgn = ((ba ^ bb) >> 63) ^ (1 if eu < 0 else 0)
-    return from_bits((sgn << 63) | (F << 52) | ((m << (lz - 11)) & MM))
+    mant = m << (lz - 11) if lz >= 11 else m >> (11 - lz)
+    return from_bits(((1 << 63) if eu < 0 else 0) + ((F - 1) << 52) + mant)
+
+
+def two_prod_int(a, b):
+    """(p, e) as the kernel's integer-pipe TwoProd computes them, or None
+    where it takes __dmul_rn and the FMA."""
+    ba, bb = bits(a), bits(b)
+    ah, al, bh, bl = ba >> 32, ba & M32, bb >> 32, bb & M32
+    Ea, Eb = (ah >> 20) & 0x7FF, (bh >> 20) & 0x7FF
+    if not (1 <= Ea <= 0x7FE and 1 <= Eb <= 0x7FE and 1129 <= Ea + Eb <= 3067):
+        return None
+    a1, b1 = (ah & 0xFFFFF) | 0x100000, (bh & 0xFFFFF) | 0x100000
+    p00 = al * bl
+    mid = al * b1 + a1 * bl
+    assert mid < 1 << 54
+    t = (p00 >> 32) + (mid & M32)
+    u = a1 * b1 + (mid >> 32) + (t >> 32)
+    w0, w1, w2, w3 = p00 & M32, t & M32, u & M32, u >> 32
+    assert (w3 << 96 | w2 << 64 | w1 << 32 | w0) == ((ba & MM) | 1 << 52) * ((bb & MM) | 1 << 52)
+    top = w3 >> 9
+    sh = 1 - top
+    w3, w2, w1, w0 = _funnel_l(w2, w3, sh), _funnel_l(w1, w2, sh), _funnel_l(w0, w1, sh), (w0 << sh) & M32
+    qlo, qhi = _funnel_r(w1, w2, 21), _funnel_r(w2, w3, 21)
+    up = (w1 >> 20) & (1 if ((w1 & 0xFFFFF) | w0) else qlo) & 1
+    q = ((qhi << 32) | qlo) + up
+    Ep = Ea + Eb - 1023 + top
+    sgn = (ah ^ bh) & 0x80000000
+    phi = sgn | ((((Ep - 1) << 20) + (q >> 32)) & M32)
+    p = from_bits((phi << 32) | (q & M32))
+    v = to_signed((((w1 & 0x1FFFFF) << 32) | w0) - (up << 53))
+    assert abs(v) <= 1 << 52
+    e = exact_to_double(-v if sgn else v, Ea + Eb - 2150 - sh)
+    if e is None:
+        return None
+    return p, e
 
 
 def _ordered(a, b):
@@ -144,23 +185,49 @@ def test_two_sum_rule_edge_cases():
     assert routed > 0      # zeros, subnormals and infinities take the FP64 formula
 
 
+def _check_two_prod(a, b):
+    r = two_prod_int(a, b)
+    if r is None:
+        return False
+    p, e = r
+    assert bits(p) == bits(a * b)                          # the IEEE product, bit for bit
+    assert Fraction(a) * Fraction(b) == Fraction(p) + Fraction(e)
+    return True
+
+
 def test_two_prod_rule_is_the_exact_error():
     rng = np.random.default_rng(5)
     a_s, b_s = _doubles(rng, 5000, -500, 500), _doubles(rng, 5000, -500, 500)
     for a, b in zip(a_s, b_s):
-        p = a * b
-        e = two_prod_err_int(a, b, p)
-        if e is None:                              # e below the normal range: the FMA
-            assert abs(p) < 2.0 ** -960
-            continue
-        assert Fraction(a) * Fraction(b) == Fraction(p) + Fraction(e)
-    # products that round up into the next binade (k = 53) and exact ones
+        if not _check_two_prod(a, b):                  # outside [2^-917, 2^1022): FP64
+            assert abs(a * b) < 2.0 ** -915
+    # products near the range's edges (exponent fields summing to 1129..3067:
+    # products from 2^-917, and below 2^1023)
+    for a, b, want in ((2.0 ** -458, 2.0 ** -459, True), (2.0 ** -459, 2.0 ** -459, False),
+                       (2.0 ** 511, 2.0 ** 510, True), (1.5 * 2.0 ** 511, 1.5 * 2.0 ** 510, True),
+                       (1.99 * 2.0 ** 511, 1.99 * 2.0 ** 510, True), (2.0 ** 511, 2.0 ** 511, False)):
+        assert _check_two_prod(a, b) == want
+        assert 2.0 ** -917 <= abs(a * b) < 2.0 ** 1023 or not want
+    # products that round up into the next binade, exact ones, and ties
     u = 2.0 ** -53
     for a, b in ((1 + 2 * u, 2 - 2 * u), (math.sqrt(2.0), math.sqrt(2.0)), (2 - 2 * u, 2 - 2 * u), (3.0, 0.5),
                  (1.0, 1.0), (-1.5, 1 + 4 * u)):
-        p = a * b
-        e = two_prod_err_int(a, b, p)
-        assert Fraction(a) * Fraction(b) == Fraction(p) + Fraction(e)
-    # underflowing or overflowing products are routed to the FMA
-    assert two_prod_err_int(2.0 ** -600, 2.0 ** -600, 2.0 ** -600 * 2.0 ** -600) is None
-    assert two_prod_err_int(2.0 ** 600, 2.0 ** 600, math.inf) is None
+        assert _check_two_prod(a, b)
+    for k in range(1, 200, 2):       # P < 2^105, P mod 2^52 = 2^51: ties, both parities of q
+        assert _check_two_prod(1.5, 1 + k * 2 * u)
+    for j in range(100):             # P >= 2^105, P mod 2^53 = 2^52
+        assert _check_two_prod(1.75, ((5 << 50) + 4 + 8 * j) * 2.0 ** -52)
+    carried = 0
+    for _ in range(3000):
+        x = int(rng.integers(1 << 52, 1 << 53))
+        for top in (106, 105):
+            y = ((1 << top) - 1) // x
+            if (1 << 52) <= y < (1 << 53):
+                a, b = x * 2.0 ** -52, y * 2.0 ** -52
+                assert _check_two_prod(a, b)
+                carried += a * b in (2.0, 4.0)
+    assert carried > 100
+    # zeros, subnormals, infinities, NaN and out-of-range products take FP64
+    for a, b in ((0.0, 1.0), (2.0 ** -1074, 1.0), (math.inf, 1.0), (math.nan, 1.0), (2.0 ** -600, 2.0 ** -600),
+                 (2.0 ** 600, 2.0 ** 600)):
+        assert two_prod_int(a, b) is None

@@ -176,3 +176,4 @@ def test_product_error_crafted_pairs():
     vals = np.array(vals + [-v for v in vals])
     a, b = np.meshgrid(vals, vals, indexing="ij")
     _check_prod(a.ravel(), b.ravel())
+
