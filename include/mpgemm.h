@@ -525,6 +525,14 @@ int mpgemm_selftest_two_sum(int64_t count, const double* a, const double* b, dou
    Device pointers (out: 3 count doubles); asynchronous on stream;
    MPGEMM_EINVAL for bad arguments. */
 int mpgemm_selftest_two_prod(int64_t count, const double* a, const double* b, double* out, void* stream);
+/* Self-test of the DD multiply-accumulate step: in = 6 planes of count
+   doubles [s, t, ah, al, bh, bl] (accumulator and operands); out = 8 planes:
+   [s, t] after the kernels' MAC (TwoProd and TwoSum's error term on the
+   integer pipe), [s, t] after the same steps with every error term from
+   FP64 operations, then both after one more renormalisation.  The two
+   forms are equal bit for bit for every input (NaN as NaN).  Device
+   pointers; asynchronous on stream; MPGEMM_EINVAL for bad arguments. */
+int mpgemm_selftest_dd_mac(int64_t count, const double* in, double* out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Precision selection from an accuracy target (the paper's outlook: choose

@@ -100,6 +100,7 @@ SIGNATURES = {
     "mpgemm_mp_to_terms": (_I, [_I, _I64, _I, _P, _P, _P]),
     "mpgemm_selftest_two_sum": (_I, [_I64, _P, _P, _P, _P]),
     "mpgemm_selftest_two_prod": (_I, [_I64, _P, _P, _P, _P]),
+    "mpgemm_selftest_dd_mac": (_I, [_I64, _P, _P, _P]),
 }
 
 

@@ -201,6 +201,19 @@ __device__ __forceinline__ void dd_mac(DDAcc& c, double ah, double al, double bh
     c.t = __dadd_rn(t, __dadd_rn(e, r));
 }
 
+// The DD MAC with every error term from FP64 operations (the reference of
+// mpgemm_selftest_dd_mac).
+__device__ __forceinline__ void dd_mac_fp64(DDAcc& c, double ah, double al, double bh, double bl) {
+    const double p = __dmul_rn(ah, bh);
+    const double e = __fma_rn(ah, bh, -p);
+    double t = __fma_rn(ah, bl, c.t);
+    t = __fma_rn(al, bh, t);
+    double s, r;
+    two_sum_fp64(c.s, p, s, r);
+    c.s = s;
+    c.t = __dadd_rn(t, __dadd_rn(e, r));
+}
+
 __device__ __forceinline__ void dd_renorm(DDAcc& c) {
     double s, t;
     two_sum(c.s, c.t, s, t);

@@ -124,7 +124,40 @@ __global__ void k_selftest_two_prod(int64_t count, const double* a, const double
     out[2 * count + i] = __fma_rn(a[i], b[i], -__dmul_rn(a[i], b[i]));
 }
 
+// The DD MAC (TwoProd and TwoSum's error on the integer pipe) and its
+// all-FP64 form on the same steps (mpgemm_selftest_dd_mac): in = [s, t,
+// ah, al, bh, bl] planes, out = [s, t] of dd_mac then of dd_mac_fp64, then
+// [s, t] after one more renormalisation (dd_renorm and two_sum_fp64).
+__global__ void k_selftest_dd_mac(int64_t count, const double* in, double* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double* v = in + i;
+    DDAcc c{v[0], v[count]}, f{v[0], v[count]};
+    dd_mac(c, v[2 * count], v[3 * count], v[4 * count], v[5 * count]);
+    dd_mac_fp64(f, v[2 * count], v[3 * count], v[4 * count], v[5 * count]);
+    out[i] = c.s;
+    out[count + i] = c.t;
+    out[2 * count + i] = f.s;
+    out[3 * count + i] = f.t;
+    dd_renorm(c);
+    double s, t;
+    two_sum_fp64(f.s, f.t, s, t);
+    out[4 * count + i] = c.s;
+    out[5 * count + i] = c.t;
+    out[6 * count + i] = s;
+    out[7 * count + i] = t;
+}
+
 }  // namespace mpg
+
+extern "C" int mpgemm_selftest_dd_mac(int64_t count, const double* in, double* out, void* stream) {
+    if (count < 0 || (count && (!in || !out))) return MPGEMM_EINVAL;
+    if (count == 0) return MPGEMM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    mpg::PartitionScope pscope(st);
+    mpg::k_selftest_dd_mac<<<mpg::ceil_div(count, 256), 256, 0, st>>>(count, in, out);
+    return mpg::check_launch();
+}
 
 extern "C" int mpgemm_selftest_two_prod(int64_t count, const double* a, const double* b, double* out,
                                         void* stream) {

@@ -28,7 +28,9 @@ namespace mpg {
 
 __device__ __forceinline__ int expo_of(double x) {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    if ((b << 1) == 0ull) return INT_MIN;   // +-0 (integer test: no FP64 instruction)
+    // +-0, tested on the 32-bit halves (a test on the 64-bit pattern can
+    // become an FP64 compare, which takes the slow FP64 pipe)
+    if ((((unsigned)__double2hiint(x) << 1) | (unsigned)__double2loint(x)) == 0u) return INT_MIN;
     int E = (int)((b >> 52) & 0x7ff);
     if (E == 0) {   // subnormal: 0.m * 2^-1022, leading one of m decides
         unsigned long long mant = b & ((1ull << 52) - 1);

@@ -107,7 +107,7 @@ double split_ms(int digit_bits, int S, int64_t m, int64_t l, int64_t n, int term
 // frexp exponent of a nonzero double from its bits (INT_MIN for +-0).
 __device__ __forceinline__ int sel_expo(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    if ((b << 1) == 0ull) return INT_MIN;
+    if ((((unsigned)__double2hiint(x) << 1) | (unsigned)__double2loint(x)) == 0u) return INT_MIN;
     const int E = (int)((b >> 52) & 0x7ff);
     if (E == 0) return -1022 - (__clzll(b & ((1ull << 52) - 1)) - 12);
     return E - 1022;
