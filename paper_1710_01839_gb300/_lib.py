@@ -101,6 +101,7 @@ SIGNATURES = {
     "mpgemm_selftest_two_sum": (_I, [_I64, _P, _P, _P, _P]),
     "mpgemm_selftest_two_prod": (_I, [_I64, _P, _P, _P, _P]),
     "mpgemm_selftest_dd_mac": (_I, [_I64, _P, _P, _P]),
+    "mpgemm_selftest_dd_add": (_I, [_I64, _P, _P, _P]),
 }
 
 

@@ -222,9 +222,11 @@ __device__ __forceinline__ void dd_renorm(DDAcc& c) {
 }
 
 // Accurate DD + DD (Joldes-Muller-Popescu 2017 "AccurateDWPlusDW", bound 3u^2),
-// used by the Strassen add/sub kernels where each operation is rounded.
-// (Its Fast2Sum steps on the integer pipe as well measured no faster: the
-// Strassen passes are latency-bound, not FP64-bound.)
+// the rounding of each of the Strassen passes' sums and differences.  The
+// passes compute it as dd_add_int (below: 6 FP64 operations) and use this
+// form only for the operands that dd_add_int flags; here the TwoSums' FP64
+// fallbacks, which the compiler predicates rather than branches around,
+// bring the count to 12-18 FP64 instructions per addition (ncu), not 10.
 __device__ __forceinline__ void dd_add(double xh, double xl, double yh, double yl, double& zh, double& zl) {
     double sh, sl, th, tl, vh, vl;
     two_sum(xh, yh, sh, sl);
@@ -233,6 +235,110 @@ __device__ __forceinline__ void dd_add(double xh, double xl, double yh, double y
     fast_two_sum(sh, c, vh, vl);
     double w = __dadd_rn(tl, vl);
     fast_two_sum(vh, w, zh, zl);
+}
+
+// ---------------------------------------------------------------- DD add, error terms on the integer pipe
+
+__device__ __forceinline__ bool is_zero_bits(unsigned hi, unsigned lo) { return ((hi << 1) | lo) == 0u; }
+
+// The rounding error r = x + y - s of s = RN(x + y) for x whose exponent
+// field is at least y's, with no FP64 operation: the integer rule of
+// fast_two_sum_err, and zeros handled exactly as the FP64 formula
+// y - (s - x) treats them (y = +-0 gives r = y; s = +-0 with y != 0, i.e.
+// x = -y, gives +0).  Where that formula would be needed instead (x or s
+// infinite or NaN, y subnormal, r subnormal) `rare` is set and the value
+// returned is unspecified: the caller recomputes with FP64 formulas.
+// Zero tests use the 32-bit halves (a test on the 64-bit pattern can
+// become an FP64 compare).
+__device__ __forceinline__ double sum_err_int(double x, double y, double s, bool& rare) {
+    const unsigned xh = (unsigned)__double2hiint(x), yh = (unsigned)__double2hiint(y);
+    const unsigned sh = (unsigned)__double2hiint(s);
+    const int Ex = (int)((xh >> 20) & 0x7ffu), Ey = (int)((yh >> 20) & 0x7ffu), Es = (int)((sh >> 20) & 0x7ffu);
+    if (Ex == 0x7ff || Es == 0x7ff) {
+        rare = true;
+        return 0.0;
+    }
+    if (Ey == 0) {
+        if (is_zero_bits(yh, (unsigned)__double2loint(y))) return y;
+        rare = true;                                         // subnormal y
+        return 0.0;
+    }
+    const int dxy = Ex - Ey;
+    if (dxy > 54) return y;
+    if (Es < Ey) return 0.0;                                 // exact sum (s = +-0 included)
+    constexpr unsigned long long MM = (1ull << 52) - 1ull, H = 1ull << 52;
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long by = (unsigned long long)__double_as_longlong(y);
+    const unsigned long long bs = (unsigned long long)__double_as_longlong(s);
+    unsigned long long X = ((bx & MM) | H) << dxy;          // x / ulp(y) mod 2^64
+    unsigned long long Y = (by & MM) | H;                   // y / ulp(y)
+    unsigned long long S = ((bs & MM) | H) << (Es - Ey);    // s / ulp(y) mod 2^64
+    if (xh >> 31) X = 0ull - X;
+    if (yh >> 31) Y = 0ull - Y;
+    if (sh >> 31) S = 0ull - S;
+    const long long ri = (long long)(X + Y - S);            // r / ulp(y), exact
+    if (ri == 0) return 0.0;
+    const unsigned long long m = ri < 0 ? 0ull - (unsigned long long)ri : (unsigned long long)ri;
+    const int lz = __clzll((long long)m);
+    const int F = Ey + 11 - lz;                             // exponent field of r
+    if (F <= 0) {
+        rare = true;                                         // subnormal r
+        return 0.0;
+    }
+    const unsigned long long mant = lz >= 11 ? m << (lz - 11) : m >> (11 - lz);
+    return __longlong_as_double(
+        (long long)((ri < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)F << 52) | (mant & MM)));
+}
+
+// TwoSum (operands ordered by exponent field, then Fast2Sum) with the error
+// from sum_err_int: one FP64 operation; where `rare` stays false, s and e
+// are those of two_sum bit for bit.
+__device__ __forceinline__ void two_sum_int(double a, double b, double& s, double& e, bool& rare) {
+    const int ea = __double2hiint(a) & 0x7ff00000, eb = __double2hiint(b) & 0x7ff00000;
+    const bool sw = eb > ea;
+    const double x = sw ? b : a, y = sw ? a : b;
+    s = __dadd_rn(x, y);
+    e = sum_err_int(x, y, s, rare);
+}
+
+// Dekker's Fast2Sum in the given operand order, error from sum_err_int: one
+// FP64 operation.  Where e(a) >= e(b) the FP64 form b - (s - a) is exact and
+// equals it; for a = +-0 (and finite b) that form gives +0; any other
+// a with a smaller exponent field than b's (where the FP64 form need not be
+// exact), or an infinite or NaN b, sets `rare`.  Where `rare` stays false,
+// s and e are those of fast_two_sum bit for bit.
+__device__ __forceinline__ void fast_two_sum_int(double a, double b, double& s, double& e, bool& rare) {
+    const unsigned ah = (unsigned)__double2hiint(a), bh = (unsigned)__double2hiint(b);
+    const int Ea = (int)((ah >> 20) & 0x7ffu), Eb = (int)((bh >> 20) & 0x7ffu);
+    s = __dadd_rn(a, b);
+    if (Ea >= Eb) {
+        e = sum_err_int(a, b, s, rare);
+    } else {
+        e = 0.0;
+        if (Eb == 0x7ff || !is_zero_bits(ah, (unsigned)__double2loint(a))) rare = true;
+    }
+}
+
+// The accurate DD + DD of dd_add with all four error terms on the integer
+// pipe: 6 FP64 operations instead of 10.  Bit for bit dd_add's result
+// wherever `rare` stays false (checked by mpgemm_selftest_dd_add); the
+// caller recomputes with dd_add where it is set (infinite, NaN or subnormal
+// values, and Fast2Sum operands out of exponent order, which only a near
+// cancellation of the high parts produces).
+__device__ __forceinline__ void dd_add_int(double xh, double xl, double yh, double yl, double& zh, double& zl,
+                                           bool& rare) {
+    double sh, sl, th, tl, vh, vl;
+    two_sum_int(xh, yh, sh, sl, rare);
+    two_sum_int(xl, yl, th, tl, rare);
+    const double c = __dadd_rn(sl, th);
+    fast_two_sum_int(sh, c, vh, vl, rare);
+    const double w = __dadd_rn(tl, vl);
+    fast_two_sum_int(vh, w, zh, zl, rare);
+}
+
+// -x by its sign bit (no FP64 operation).
+__device__ __forceinline__ double neg_bits(double x) {
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
 // ---------------------------------------------------------------- QD

@@ -148,6 +148,26 @@ __global__ void k_selftest_dd_mac(int64_t count, const double* in, double* out) 
     out[7 * count + i] = t;
 }
 
+// The Strassen passes' DD addition with every error term on the integer pipe
+// and dd_add (FP64 error terms) on the same operands
+// (mpgemm_selftest_dd_add): in = [xh, xl, yh, yl] planes, out = [zh, zl] of
+// dd_add_int, [zh, zl] of dd_add, and 1.0 where dd_add_int set `rare` (the
+// passes recompute those with dd_add), else 0.0.
+__global__ void k_selftest_dd_add(int64_t count, const double* in, double* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double* v = in + i;
+    double zh, zl, fh, fl;
+    bool rare = false;
+    dd_add_int(v[0], v[count], v[2 * count], v[3 * count], zh, zl, rare);
+    dd_add(v[0], v[count], v[2 * count], v[3 * count], fh, fl);
+    out[i] = zh;
+    out[count + i] = zl;
+    out[2 * count + i] = fh;
+    out[3 * count + i] = fl;
+    out[4 * count + i] = rare ? 1.0 : 0.0;
+}
+
 }  // namespace mpg
 
 extern "C" int mpgemm_selftest_dd_mac(int64_t count, const double* in, double* out, void* stream) {
@@ -156,6 +176,15 @@ extern "C" int mpgemm_selftest_dd_mac(int64_t count, const double* in, double* o
     cudaStream_t st = (cudaStream_t)stream;
     mpg::PartitionScope pscope(st);
     mpg::k_selftest_dd_mac<<<mpg::ceil_div(count, 256), 256, 0, st>>>(count, in, out);
+    return mpg::check_launch();
+}
+
+extern "C" int mpgemm_selftest_dd_add(int64_t count, const double* in, double* out, void* stream) {
+    if (count < 0 || (count && (!in || !out))) return MPGEMM_EINVAL;
+    if (count == 0) return MPGEMM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    mpg::PartitionScope pscope(st);
+    mpg::k_selftest_dd_add<<<mpg::ceil_div(count, 256), 256, 0, st>>>(count, in, out);
     return mpg::check_launch();
 }
 

@@ -47,13 +47,23 @@ __host__ __device__ constexpr int child_op(int side, int what, int c) {
 
 // ---------------------------------------------------------------- element ops
 
+// add: the sum rounded in the format (FP64 error terms); add_int: the same
+// sum where `rare` stays false, with fewer FP64 operations (DD: every error
+// term on the integer pipe, 6 FP64 operations instead of 10; QD: add
+// itself); neg_int: -x for add_int's operands.
 struct DDE {
     static constexpr int P = 2;
     __device__ static void add(const double* x, const double* y, double* z) { dd_add(x[0], x[1], y[0], y[1], z[0], z[1]); }
+    __device__ static void add_int(const double* x, const double* y, double* z, bool& rare) {
+        dd_add_int(x[0], x[1], y[0], y[1], z[0], z[1], rare);
+    }
+    __device__ static double neg_int(double v) { return neg_bits(v); }
 };
 struct QDE {
     static constexpr int P = 4;
     __device__ static void add(const double* x, const double* y, double* z) { qd_add(x, y, z); }
+    __device__ static void add_int(const double* x, const double* y, double* z, bool&) { qd_add(x, y, z); }
+    __device__ static double neg_int(double v) { return -v; }
 };
 
 template <class E>
@@ -87,34 +97,83 @@ __device__ __forceinline__ void ld_ext(const View<const double>& V, int64_t p, i
 // Children operands: grid (cols/128, rows, parents); the parent holds xr x
 // xc elements (2 rows x 2 cols except where zero-extended).  A thread reads
 // element (i, j) of the parent's four quadrants once and writes it to all
-// seven children.
+// seven children.  The sums are formed with add_int; a thread whose sums
+// met a rare case forms them again with add and overwrites its children
+// (the same thread's later stores win), so every child holds add's result.
 template <class E, int SIDE>
 __global__ void k_expand(int64_t rows, int64_t cols, int64_t xr, int64_t xc, View<const double> X, View<double> Y) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = blockIdx.y;
     int64_t p = blockIdx.z;
     if (j >= cols) return;
+    constexpr int side = SIDE;
     double Q[4][E::P];
 #pragma unroll
     for (int q = 0; q < 4; q++) ld_ext<E>(X, p, (q >> 1) * rows + i, (q & 1) * cols + j, xr, xc, Q[q]);
+    bool rare = false;
 #pragma unroll
     for (int c = 0; c < 7; c++) {
-        constexpr int side = SIDE;
         const int qa = child_op(side, 0, c), qb = child_op(side, 1, c), op = child_op(side, 2, c);
         if (op == 0) {
             st<E>(Y, p * 7 + c, i, j, Q[qa]);
         } else {
             double y[E::P], r[E::P];
 #pragma unroll
-            for (int q = 0; q < E::P; q++) y[q] = op == 2 ? -Q[qb][q] : Q[qb][q];
-            E::add(Q[qa], y, r);
+            for (int q = 0; q < E::P; q++) y[q] = op == 2 ? E::neg_int(Q[qb][q]) : Q[qb][q];
+            E::add_int(Q[qa], y, r, rare);
             st<E>(Y, p * 7 + c, i, j, r);
+        }
+    }
+    if (rare) {
+#pragma unroll
+        for (int c = 0; c < 7; c++) {
+            const int qa = child_op(side, 0, c), qb = child_op(side, 1, c), op = child_op(side, 2, c);
+            if (op != 0) {
+                double y[E::P], r[E::P];
+#pragma unroll
+                for (int q = 0; q < E::P; q++) y[q] = op == 2 ? -Q[qb][q] : Q[qb][q];
+                E::add(Q[qa], y, r);
+                st<E>(Y, p * 7 + c, i, j, r);
+            }
         }
     }
 }
 
+// The four quadrants of a parent element from its seven children (Eq 3):
+// C11 = ((P1 + P4) - P5) + P7 and C22 = ((P1 + P3) - P2) + P6 advance side
+// by side, C12 = P3 + P5 and C21 = P2 + P4 between them: four independent
+// additions per step instead of one chain of eight (each result keeps its
+// left-to-right order).  INT: add_int and neg_int (`rare` set where add is
+// needed), else add.
+template <class E, bool INT>
+__device__ __forceinline__ void assemble(const double (&P)[7][E::P], double* c11, double* c12, double* c21,
+                                         double* c22, bool& rare) {
+    double n5[E::P], n2[E::P];
+#pragma unroll
+    for (int q = 0; q < E::P; q++) {
+        n5[q] = INT ? E::neg_int(P[4][q]) : -P[4][q];
+        n2[q] = INT ? E::neg_int(P[1][q]) : -P[1][q];
+    }
+    auto add = [&](const double* x, const double* y, double* z) {
+        if (INT) E::add_int(x, y, z, rare);
+        else E::add(x, y, z);
+    };
+    double a[E::P], b[E::P];
+    add(P[0], P[3], a);
+    add(P[0], P[2], b);
+    add(P[2], P[4], c12);
+    add(P[1], P[3], c21);
+    double a2[E::P], b2[E::P];
+    add(a, n5, a2);
+    add(b, n2, b2);
+    add(a2, P[6], c11);
+    add(b2, P[5], c22);
+}
+
 // Parent products from children: grid (cols/128, rows, parents); only the
-// first xr rows and xc columns of the parent are written.
+// first xr rows and xc columns of the parent are written.  The quadrants
+// are assembled with add_int; a thread that met a rare case reads its
+// children again, assembles with add and overwrites its outputs.
 template <class E>
 __global__ void k_combine(int64_t rows, int64_t cols, int64_t xr, int64_t xc, View<const double> Pc,
                           View<double> Out) {
@@ -125,32 +184,23 @@ __global__ void k_combine(int64_t rows, int64_t cols, int64_t xr, int64_t xc, Vi
     double P[7][E::P];
 #pragma unroll
     for (int c = 0; c < 7; c++) ld<E>(Pc, p * 7 + c, i, j, P[c]);
-    double n5[E::P], n2[E::P];
-#pragma unroll
-    for (int q = 0; q < E::P; q++) {
-        n5[q] = -P[4][q];
-        n2[q] = -P[1][q];
-    }
-    // C11 = ((P1 + P4) - P5) + P7 and C22 = ((P1 + P3) - P2) + P6 advance
-    // side by side, C12 = P3 + P5 and C21 = P2 + P4 between them: four
-    // independent additions per step instead of one chain of eight (each
-    // result keeps its left-to-right order)
-    double a[E::P], b[E::P], c12[E::P], c21[E::P];
-    E::add(P[0], P[3], a);
-    E::add(P[0], P[2], b);
-    E::add(P[2], P[4], c12);
-    E::add(P[1], P[3], c21);
-    double a2[E::P], b2[E::P];
-    E::add(a, n5, a2);
-    E::add(b, n2, b2);
-    double c11[E::P], c22[E::P];
-    E::add(a2, P[6], c11);
-    E::add(b2, P[5], c22);
+    double c11[E::P], c12[E::P], c21[E::P], c22[E::P];
+    bool rare = false;
+    assemble<E, true>(P, c11, c12, c21, c22, rare);
     const bool r0 = i < xr, r1 = rows + i < xr, c0 = j < xc, c1 = cols + j < xc;
     if (r0 && c0) st<E>(Out, p, i, j, c11);
     if (r0 && c1) st<E>(Out, p, i, cols + j, c12);
     if (r1 && c0) st<E>(Out, p, rows + i, j, c21);
     if (r1 && c1) st<E>(Out, p, rows + i, cols + j, c22);
+    if (rare) {
+#pragma unroll
+        for (int c = 0; c < 7; c++) ld<E>(Pc, p * 7 + c, i, j, P[c]);
+        assemble<E, false>(P, c11, c12, c21, c22, rare);
+        if (r0 && c0) st<E>(Out, p, i, j, c11);
+        if (r0 && c1) st<E>(Out, p, i, cols + j, c12);
+        if (r1 && c0) st<E>(Out, p, rows + i, j, c21);
+        if (r1 && c1) st<E>(Out, p, rows + i, cols + j, c22);
+    }
 }
 
 // ---------------------------------------------------------------- multi-limb element ops

@@ -231,3 +231,145 @@ def test_two_prod_rule_is_the_exact_error():
     for a, b in ((0.0, 1.0), (2.0 ** -1074, 1.0), (math.inf, 1.0), (math.nan, 1.0), (2.0 ** -600, 2.0 ** -600),
                  (2.0 ** 600, 2.0 ** 600)):
         assert two_prod_int(a, b) is None
+
+
+# ---------------------------------------------------------------- the Strassen passes' DD addition
+#
+# Every error term on the integer pipe (sum_err_int / two_sum_int /
+# fast_two_sum_int / dd_add_int of the device header), with no FP64
+# fallback: zeros are exact (y = +-0 gives r = y, s = +-0 with y != 0 gives
+# +0, as y - (s - x) does), and the cases that need the FP64 formula set a
+# flag instead (the passes then recompute the element with FP64 error terms).
+
+def sum_err_total(x, y, s):
+    """(r, rare) for x with exponent field >= y's, s = RN(x + y)."""
+    bx, by, bs = bits(x), bits(y), bits(s)
+    Ex, Ey, Es = (bx >> 52) & 0x7FF, (by >> 52) & 0x7FF, (bs >> 52) & 0x7FF
+    if Ex == 0x7FF or Es == 0x7FF:
+        return None, True
+    if Ey == 0:
+        return (y, False) if (by << 1) & M64 == 0 else (None, True)
+    dxy = Ex - Ey
+    if dxy > 54:
+        return y, False
+    if Es < Ey:
+        return 0.0, False
+    X = (((bx & MM) | (1 << 52)) << dxy) & M64
+    Y = (by & MM) | (1 << 52)
+    S = (((bs & MM) | (1 << 52)) << (Es - Ey)) & M64
+    if bx >> 63:
+        X = -X
+    if by >> 63:
+        Y = -Y
+    if bs >> 63:
+        S = -S
+    ri = to_signed(X + Y - S)
+    if ri == 0:
+        return 0.0, False
+    r = assemble(ri, Ey)
+    return (None, True) if r is None else (r, False)
+
+
+def two_sum_int_model(a, b):
+    x, y = _ordered(a, b)
+    s = x + y
+    e, rare = sum_err_total(x, y, s)
+    return s, e, rare
+
+
+def fast_two_sum_int_model(a, b):
+    s = a + b
+    Ea, Eb = (bits(a) >> 52) & 0x7FF, (bits(b) >> 52) & 0x7FF
+    if Ea >= Eb:
+        e, rare = sum_err_total(a, b, s)
+        return s, e, rare
+    return s, 0.0, Eb == 0x7FF or (bits(a) << 1) & M64 != 0
+
+
+def dd_add_int_model(xh, xl, yh, yl):
+    sh, sl, r1 = two_sum_int_model(xh, yh)
+    th, tl, r2 = two_sum_int_model(xl, yl)
+    if r1 or r2:
+        return None
+    c = sl + th
+    vh, vl, r3 = fast_two_sum_int_model(sh, c)
+    if r3:
+        return None
+    w = tl + vl
+    zh, zl, r4 = fast_two_sum_int_model(vh, w)
+    return None if r4 else (zh, zl)
+
+
+def dd_add_fp64(xh, xl, yh, yl):
+    """The kernels' dd_add with FP64 error terms: TwoSum as Fast2Sum after
+    ordering by exponent field, then the accurate double-word steps."""
+    def two_sum(a, b):
+        x, y = _ordered(a, b)
+        s = x + y
+        return s, y - (s - x)
+
+    def fast_two_sum(a, b):
+        s = a + b
+        return s, b - (s - a)
+
+    sh, sl = two_sum(xh, yh)
+    th, tl = two_sum(xl, yl)
+    vh, vl = fast_two_sum(sh, sl + th)
+    return fast_two_sum(vh, tl + vl)
+
+
+def _same(p, q):
+    return all(bits(a) == bits(b) for a, b in zip(p, q))
+
+
+def test_dd_add_int_rule_on_dd_pairs():
+    rng = np.random.default_rng(71)
+    n = 4000
+    hi = rng.uniform(-1, 1, (4, n)) * np.ldexp(1.0, rng.integers(-20, 21, (4, n)))
+    lo = np.ldexp(hi, -53) * rng.uniform(-1, 1, (4, n))
+    for i in range(n):
+        xh, yh = float(hi[0, i]), float(hi[1, i])
+        xl, yl = float(lo[0, i]), float(lo[1, i])
+        for sgn in (1.0, -1.0):
+            z = dd_add_int_model(xh, xl, sgn * yh, sgn * yl)
+            assert z is not None                    # none of these is rare
+            assert _same(z, dd_add_fp64(xh, xl, sgn * yh, sgn * yl))
+
+
+def test_dd_add_int_rule_on_cancellations():
+    rng = np.random.default_rng(72)
+    flagged = 0
+    for k in range(-3, 4):
+        for _ in range(400):
+            xh = float(rng.uniform(-1, 1)) * 2.0 ** int(rng.integers(-30, 30))
+            xl = math.ldexp(xh, -53) * float(rng.uniform(-1, 1))
+            yh = -(xh + k * math.ulp(xh))
+            yl = -xl * float(rng.uniform(0.25, 4)) * float(rng.choice([-1, 1]))
+            z = dd_add_int_model(xh, xl, yh, yl)
+            if z is None:
+                flagged += 1
+                continue
+            assert _same(z, dd_add_fp64(xh, xl, yh, yl))
+            # the exact sum's error: the accurate addition's bound 3u^2 |x + y|
+            exact = Fraction(xh) + Fraction(xl) + Fraction(yh) + Fraction(yl)
+            assert abs(Fraction(z[0]) + Fraction(z[1]) - exact) <= 3 * Fraction(2) ** -106 * abs(exact)
+    assert flagged < 7 * 400
+
+
+def test_dd_add_int_rule_special_values():
+    u = 2.0 ** -53
+    vals = [0.0, -0.0, 1.0, -1.0, 1 + 2 * u, u, 2.0 ** -1074, 2.0 ** -1022, 1.7976931348623157e308, math.inf,
+            -math.inf, math.nan, 2.0 ** -1000, 3.0]
+    unflagged = 0
+    for xh in vals:
+        for xl in vals:
+            for yh in vals:
+                for yl in vals:
+                    z = dd_add_int_model(xh, xl, yh, yl)
+                    if not all(math.isfinite(v) for v in (xh, xl, yh, yl)):
+                        assert z is None            # every infinity and NaN is flagged
+                    if z is None:
+                        continue
+                    unflagged += 1
+                    assert _same(z, dd_add_fp64(xh, xl, yh, yl))
+    assert unflagged > 5000
