@@ -58,10 +58,10 @@ ISSUE_PEAK_GWIPS = 4 * 152 * 2.070
 # (2048 bits: 128^3) inputs of the multi-limb workload), by precision in bits.
 MP_INSTR_PER_MAC = {128: 232.2, 256: 376.7, 512: 963.6, 1024: 2610.1, 2048: 8472.3}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from ncu captures of exactly these configurations (profiles/):
-# (fmt, n, algo, n_min, depth) -> bytes.  Absent => null.
-TRAFFIC_BYTES = {("dd", 2048, "strassen", 32, 3): 728.3e6 + 337.8e6,
-                 ("dd", 2048, "strassen", 32, 4): 1.268e9 + 0.600e9}
+# kernel from ncu captures of exactly these configurations (profiles/),
+# taken with the leaf kernel as it is now (entries of earlier forms of the
+# kernel are dropped): (fmt, n, algo, n_min, depth) -> bytes.  Absent => null.
+TRAFFIC_BYTES = {("dd", 2048, "strassen", 16, 4): 1.267e9 + 0.605e9}
 
 
 def parse():
