@@ -537,10 +537,11 @@ int mpgemm_selftest_dd_mac(int64_t count, const double* in, double* out, void* s
    (Eq 3's sums and differences, each rounded in DD by the accurate
    double-word addition of Joldes, Muller and Popescu 2017): in = 4 planes
    of count doubles [xh, xl, yh, yl]; out = 5 planes: [zh, zl] as the passes
-   compute it first (all four error terms on the integer pipe), [zh, zl]
-   with the error terms from FP64 operations, and 1.0 where the first form
-   flagged the operands as rare (infinite, NaN or subnormal values, or
-   Fast2Sum operands out of exponent order), else 0.0.  Where the flag is
+   compute it first (three of its four error terms on the integer pipe),
+   [zh, zl] with every error term from FP64 operations, and 1.0 where the
+   first form flagged the operands as rare (infinite, NaN or subnormal
+   values, or the last Fast2Sum's operands out of exponent order), else
+   0.0.  Where the flag is
    0.0 the two results are equal bit for bit; the passes recompute flagged
    elements with the FP64 form.  Device pointers; asynchronous on stream;
    MPGEMM_EINVAL for bad arguments. */

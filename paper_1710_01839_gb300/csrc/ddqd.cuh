@@ -319,19 +319,23 @@ __device__ __forceinline__ void fast_two_sum_int(double a, double b, double& s, 
     }
 }
 
-// The accurate DD + DD of dd_add with all four error terms on the integer
-// pipe: 6 FP64 operations instead of 10.  Bit for bit dd_add's result
-// wherever `rare` stays false (checked by mpgemm_selftest_dd_add); the
-// caller recomputes with dd_add where it is set (infinite, NaN or subnormal
-// values, and Fast2Sum operands out of exponent order, which only a near
-// cancellation of the high parts produces).
+// The accurate DD + DD of dd_add with three of its four error terms on the
+// integer pipe (the two TwoSums' and the last Fast2Sum's): 8 FP64
+// operations instead of 10.  The first Fast2Sum keeps dd_add's FP64 formula
+// (the same bits by construction, whatever the operands' exponent order),
+// which balances the FP64 and integer pipes of the Strassen passes (all
+// four on the integer pipe: 6 FP64 operations, integer-issue bound).  Bit
+// for bit dd_add's result wherever `rare` stays false (checked by
+// mpgemm_selftest_dd_add); the caller recomputes with dd_add where it is set
+// (infinite, NaN or subnormal values, and a last Fast2Sum whose operands
+// are out of exponent order).
 __device__ __forceinline__ void dd_add_int(double xh, double xl, double yh, double yl, double& zh, double& zl,
                                            bool& rare) {
     double sh, sl, th, tl, vh, vl;
     two_sum_int(xh, yh, sh, sl, rare);
     two_sum_int(xl, yl, th, tl, rare);
     const double c = __dadd_rn(sl, th);
-    fast_two_sum_int(sh, c, vh, vl, rare);
+    fast_two_sum(sh, c, vh, vl);
     const double w = __dadd_rn(tl, vl);
     fast_two_sum_int(vh, w, zh, zl, rare);
 }

@@ -48,9 +48,9 @@ __host__ __device__ constexpr int child_op(int side, int what, int c) {
 // ---------------------------------------------------------------- element ops
 
 // add: the sum rounded in the format (FP64 error terms); add_int: the same
-// sum where `rare` stays false, with fewer FP64 operations (DD: every error
-// term on the integer pipe, 6 FP64 operations instead of 10; QD: add
-// itself); neg_int: -x for add_int's operands.
+// sum where `rare` stays false, with fewer FP64 operations (DD: three of the
+// four error terms on the integer pipe, 8 FP64 operations instead of 10;
+// QD: add itself); neg_int: -x for add_int's operands.
 struct DDE {
     static constexpr int P = 2;
     __device__ static void add(const double* x, const double* y, double* z) { dd_add(x[0], x[1], y[0], y[1], z[0], z[1]); }

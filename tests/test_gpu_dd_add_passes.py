@@ -1,8 +1,9 @@
 """The Strassen operand and assembly passes (Eq 3's sums and differences,
-each rounded in DD) compute the accurate double-word addition with its four
-error terms on the integer pipe and recompute, with the FP64 error terms,
-every element whose operands the integer form flags as rare (infinite, NaN
-or subnormal values, Fast2Sum operands out of exponent order).  Checked
+each rounded in DD) compute the accurate double-word addition with three of
+its four error terms on the integer pipe and recompute, with the FP64 error
+terms, every element whose operands the integer form flags as rare
+(infinite, NaN or subnormal values, the last Fast2Sum's operands out of
+exponent order).  Checked
 here through mpgemm_selftest_dd_add:
   - unflagged results equal the FP64 form bit for bit, on the benchmark's
     operand pairs (none flagged there), near cancellations of the high
