@@ -223,7 +223,7 @@ __device__ __forceinline__ void dd_renorm(DDAcc& c) {
 
 // Accurate DD + DD (Joldes-Muller-Popescu 2017 "AccurateDWPlusDW", bound 3u^2),
 // the rounding of each of the Strassen passes' sums and differences.  The
-// passes compute it as dd_add_int (below: 6 FP64 operations) and use this
+// passes compute it as dd_add_int (below: 8 FP64 operations) and use this
 // form only for the operands that dd_add_int flags; here the TwoSums' FP64
 // fallbacks, which the compiler predicates rather than branches around,
 // bring the count to 12-18 FP64 instructions per addition (ncu), not 10.
