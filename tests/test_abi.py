@@ -99,6 +99,20 @@ def test_host_only_calls(built):
     assert L.mpgemm_set_mp_leaf(0) == 2
     # the bounds counter exists only in the bounds-checked build
     assert L.mpgemm_bounds_read(None, None) == -2 and L.mpgemm_selftest_bounds(None) == -2
+    # the arithmetic self-tests check their arguments before any CUDA call:
+    # a negative count or missing buffers are refused, an empty one is a no-op
+    buf = ctypes.c_void_p(8)                 # never dereferenced: refused or count 0
+    for name in ("mpgemm_selftest_two_sum", "mpgemm_selftest_two_prod"):
+        f = getattr(L, name)
+        assert f(-1, buf, buf, buf, None) == -1, name
+        assert f(4, None, buf, buf, None) == -1 and f(4, buf, None, buf, None) == -1, name
+        assert f(4, buf, buf, None, None) == -1, name
+        assert f(0, None, None, None, None) == 0, name
+    for name in ("mpgemm_selftest_dd_mac", "mpgemm_selftest_dd_add"):
+        f = getattr(L, name)
+        assert f(-1, buf, buf, None) == -1, name
+        assert f(4, None, buf, None) == -1 and f(4, buf, None, None) == -1, name
+        assert f(0, None, None, None) == 0, name
 
 
 def test_checked_build_exists_and_exports(built):
